@@ -1,0 +1,312 @@
+#!/usr/bin/env python3
+"""Benchmark of the Power-psi hot path on GB300.
+
+One step = the whole path on one synthetic graph: psi_graph_create (validate, renumber,
+sort + merge duplicates, CSR, sigma/c/d, tile schedule), psi_solve (Power-psi to
+eps = 1e-8 on the psi-tolerance eps_t/N, FP32 series + FP64 refinement, final psi) and
+psi_topk (k = 100).  Default workload: R-MAT scale 25 (N = 2^25), edge factor 16,
+(a, b, c) = (.57, .19, .19), random relabel, lambda, mu ~ LogNormal(0, 1.5) clipped to
+[1e-3, 1e3] -- a synthetic stand-in for the paper's social graphs.
+
+``value`` is the seconds per step with inputs resident in HBM; ``e2e`` is the same step
+through the C ABI from pinned host buffers (H2D of edges and rates, D2H of the top-k inside
+the timed region).  ``--impl reference`` times the FP64 CPU oracle on the host cores
+instead.  Multi-GPU runs are replicas (one independent graph per rank, weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Power-ψ time-to-L1<1e-8 and GTEPS/iter at N=2^25; % of HBM peak"
+FALLBACK_HBM_GBS = 6800.0
+# DRAM bytes per launch of the FP32 series step (k_spmv + fix-up) from one ncu capture,
+# valid only while the kernel sources hash to `sha`.
+NCU_TRAFFIC = {"sha": None, "bytes_per_launch": None, "note": ""}
+KERNEL_SOURCES = ["paper_2206_09960_gb300/csrc/spmv.cuh", "paper_2206_09960_gb300/csrc/common.cuh"]
+CPU_SAMPLE_SCALE = 20
+
+
+def kernel_sha() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.dev)], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_sample_seconds(seed: int, eps: float):
+    """Full oracle solve (canonicalise + build A, B + Algorithm 2 + ranking) of a smaller
+    graph with the same recipe; returns (seconds, draws of the sample, threads)."""
+    import oracle
+    import psigen
+
+    w = psigen.workload("rmat", seed=seed, scale=CPU_SAMPLE_SCALE)
+    t = time.perf_counter()
+    out = oracle.solve(w["n"], w["follower"], w["leader"], w["lam"], w["mu"], eps=eps, tol_mode=oracle.TOL_PSI)
+    oracle.topk(out["psi"], 100)
+    return time.perf_counter() - t, int(w["follower"].size), oracle.num_threads()
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    draws_full = 16 << args.scale
+    times = []
+    threads = 1
+    for i in range(args.warmup + args.steps):
+        sec, draws, threads = cpu_sample_seconds(args.seed, args.eps)
+        if i >= args.warmup:
+            times.append(sec * draws_full / draws)
+    v = statistics.mean(times)
+    sample = (f"full FP64 oracle solve (canonicalise, explicit A/B, Algorithm 2 to eps={args.eps:g} on eps_t/N, "
+              f"top-100) of R-MAT scale {CPU_SAMPLE_SCALE} (same recipe), time x {draws_full // draws} "
+              f"(edge-draw ratio to scale {args.scale})")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args, None),
+            "cpu_baseline": {"value": v, "unit": "s", "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(args, stats):
+    cfg = {"workload": f"rmat_scale{args.scale}_ef16_a.57_b.19_c.19_relabel_lognormal1.5",
+           "n": 1 << args.scale, "edge_draws": 16 << args.scale, "eps": args.eps,
+           "tolerance": "eps_t/N (psi tolerance, B_norm=1)", "precision": "fp32 terms, fp64 iterate and residual",
+           "topk": 100, "l2": "inputs larger than L2 (edge list 8 B x draws)", "parallelism": "replicas"}
+    if stats:
+        cfg["m_unique"] = stats["m_unique"]
+        cfg["n_rows"] = stats["n_rows"]
+        cfg["n_gathered"] = stats["n_gathered"]
+    return cfg
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--scale", type=int, default=25)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--eps", type=float, default=1e-8)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import numpy as np
+    import torch
+
+    import psigen
+    import paper_2206_09960_gb300 as psi
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    psi.load(build_if_missing=False)
+
+    # one independent graph per rank (replicas)
+    seed = args.seed + rank
+    n = 1 << args.scale
+    m0 = 16 << args.scale
+    f_h = torch.empty(m0, dtype=torch.int32).pin_memory()
+    l_h = torch.empty(m0, dtype=torch.int32).pin_memory()
+    psigen.rmat_graph(args.scale, 16, *psigen.RMAT_ABC, seed, relabel=True, out=(f_h.numpy(), l_h.numpy()))
+    lam_h = torch.from_numpy(psigen.lognormal_rates(n, 0.0, 1.5, 1e-3, 1e3, seed, psigen.STREAM_LAMBDA)).pin_memory()
+    mu_h = torch.from_numpy(psigen.lognormal_rates(n, 0.0, 1.5, 1e-3, 1e3, seed, psigen.STREAM_MU)).pin_memory()
+    f_d, l_d, lam_d, mu_d = (x.cuda() for x in (f_h, l_h, lam_h, mu_h))
+    ids_d = torch.empty(100, dtype=torch.int32, device="cuda")
+    vals_d = torch.empty(100, dtype=torch.float64, device="cuda")
+    ids_h = torch.empty(100, dtype=torch.int32).pin_memory()
+    vals_h = torch.empty(100, dtype=torch.float64).pin_memory()
+    stream = torch.cuda.current_stream()
+
+    def step(inputs, ids, vals, profile=False):
+        with psi.Graph(n, *inputs, profile=profile, stream=stream) as g:
+            info = g.solve(args.eps, 100000)
+            g.topk(100, ids, vals)
+            return info, g.stats()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if ws == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    dev_in = (f_d, l_d, lam_d, mu_d)
+    host_in = (f_h, l_h, lam_h, mu_h)
+    for _ in range(args.warmup):
+        step(dev_in, ids_d, vals_d)
+
+    # ---- timed region: inputs resident in HBM
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    launches0 = psi.psi_kernel_launches()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    infos, stats = [], None
+    for _ in range(args.steps):
+        info, stats = step(dev_in, ids_d, vals_d, profile=True)
+        infos.append(info)
+    e1.record(stream)
+    barrier()
+    launches = psi.psi_kernel_launches() - launches0
+    clk = clocks.stop()
+    step_s = max_over_ranks(e0.elapsed_time(e1) / 1e3 / args.steps)
+
+    # ---- end to end from pinned host buffers (H2D of inputs and D2H of the ranking inside)
+    e2e = None
+    if not args.no_e2e:
+        step(host_in, ids_h, vals_h)
+        barrier()
+        t0 = time.perf_counter()
+        h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        h0.record(stream)
+        for _ in range(args.steps):
+            step(host_in, ids_h, vals_h)
+        h1.record(stream)
+        barrier()
+        wall = (time.perf_counter() - t0) / args.steps
+        e2e_s = max_over_ranks(max(h0.elapsed_time(h1) / 1e3 / args.steps, wall))
+        e2e = {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(2 * 4 * m0 + 2 * 8 * n),
+               "d2h_bytes_per_step": int(100 * (4 + 8))}
+
+    # ---- roofline of the dominant kernel: the FP32 series step (sparse product + fix-up)
+    iters = statistics.mean(i["iters"] for i in infos)
+    spmv_launches = sum(i["spmv_timed"] for i in infos)
+    spmv_ms = sum(i["spmv_ms"] for i in infos)
+    avg_launch_s = spmv_ms / 1e3 / max(spmv_launches, 1)
+    m_u, n_rows, n_g = stats["m_unique"], stats["n_rows"], stats["n_gathered"]
+    alg_bytes = 4 * m_u + 32 * n_rows + 4 * n_g
+    peak, peak_kind = measured_peaks()
+    achieved = alg_bytes / avg_launch_s / 1e9
+    traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["sha"] == kernel_sha() else None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "peak_kind": peak_kind,
+                "kernel": "k_spmv<float,EpiSeries> + k_fixup (FP32 series step of Eq. 13)",
+                "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_launch_s * 1e3,
+                "launches_timed": spmv_launches}
+    solve_s = statistics.mean(i["ms"] for i in infos) / 1e3
+    build_s = stats["build_ms"] / 1e3
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        sec, draws, threads = cpu_sample_seconds(args.seed, args.eps)
+        cpu = {"value": sec * m0 / draws, "unit": "s", "cores": threads, "kind": "oracle",
+               "sample": f"full FP64 oracle solve of R-MAT scale {CPU_SAMPLE_SCALE} (same recipe, eps={args.eps:g} "
+                         f"on eps_t/N, top-100) took {sec:.2f} s; scaled by the edge-draw ratio {m0 // draws}"}
+
+    line = {"metric": METRIC, "value": step_s, "unit": "s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(args, stats),
+            "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "roofline": roofline, "cpu_baseline": cpu,
+            "time_to_eps_s": solve_s, "build_s": build_s, "iters": iters,
+            "refinements": statistics.mean(i["refinements"] for i in infos),
+            "gteps_per_iter": m_u / avg_launch_s / 1e9,
+            "hbm_frac_per_iter_4M_32N": (4 * m_u + 32 * n) / avg_launch_s / 1e9 / peak,
+            "gap_psi_bound": infos[-1]["gap_psi_bound"], "gap_scaled": infos[-1]["gap_scaled"],
+            "psi_sum": infos[-1]["psi_sum"], "problems_per_s": ws / step_s}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

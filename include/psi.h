@@ -1,0 +1,188 @@
+/*
+ * psi.h -- C ABI of the GB300 Power-psi solver (libpsi_gb300.so).
+ *
+ * Computes the psi-score of every user of a follower graph (Arhachoui, Bautista,
+ * Danisch, Giovanidis, "A Fast Algorithm for Ranking Users by their Influence in Online
+ * Social Platforms", ASONAM 2022):
+ *
+ *   psi^T = (1/N) [ (sum_{t>=0} c^T A^t) B + d^T ]                        (Eq. 12)
+ *
+ * with, for user j following user i (L(j) = leaders of j):
+ *   a_ji = mu_i / sigma_j,  b_ji = lambda_i / sigma_j,  sigma_j = sum_{l in L(j)} (lambda_l + mu_l),
+ *   c_j = mu_j / (lambda_j + mu_j),  d_j = lambda_j / (lambda_j + mu_j)   (Sec. II, Eqs. 6-7).
+ *
+ * The series is evaluated by Power-psi (Algorithm 2): s_0 = c, s_t^T = s_{t-1}^T A + c^T
+ * (Eq. 14), gap eps_t = ||s_t - s_{t-1}||_1 (Eq. 15), stop when the scaled gap <= eps
+ * (Eq. 16), then psi^T = (s_t^T B + d^T) / N.
+ *
+ * Conventions for every call:
+ *   * Every function returns a psi_status; none aborts, traps or exits.  On failure a
+ *     message is available from psi_last_error() (thread-local, valid until the next
+ *     call on the same thread).
+ *   * Array arguments may be host or device pointers (detected per call).  Inputs are
+ *     copied and never retained; the caller keeps ownership of everything it passes.
+ *   * Work is queued on the CUDA stream given in psi_options.stream (NULL = the legacy
+ *     default stream).  psi_graph_create, psi_solve, psi_scores, psi_topk and
+ *     psi_get_iterate return after their results are complete (they synchronise that
+ *     stream once at the end, plus a few small status reads on the way).
+ *   * User ids are 0-based int32; n < 2^31 and the edge count m < 2^31 - 1.
+ *   * A graph handle may be used by one host thread at a time.
+ */
+#ifndef PSI_GB300_H
+#define PSI_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct psi_graph psi_graph; /* opaque; owns all of its device memory */
+
+typedef enum psi_status {
+  PSI_OK = 0,
+  PSI_ERR_INVALID_ARG = 1,     /* null pointer, negative size, unknown option, k out of range */
+  PSI_ERR_OUT_OF_RANGE_ID = 2, /* an edge endpoint outside [0, n) */
+  PSI_ERR_SELF_LOOP = 3,       /* a user follows itself and self_loops == PSI_REJECT */
+  PSI_ERR_BAD_RATE = 4,        /* lambda or mu NaN, infinite or negative, or lambda + mu == 0 */
+  PSI_ERR_OOM = 5,             /* the allocator returned NULL */
+  PSI_ERR_CUDA = 6,            /* a CUDA runtime error (message in psi_last_error) */
+  PSI_ERR_NOT_CONVERGED = 7,   /* max_iter reached; the last iterate and psi stay readable */
+  PSI_ERR_TIMEOUT = 8,         /* a bounded device-side wait gave up */
+  PSI_ERR_NOT_SOLVED = 9       /* scores asked for before a solve produced them */
+} psi_status;
+
+/* psi_options.precision */
+enum {
+  PSI_FP32 = 0,        /* Algorithm 2 literally, iterate stored and summed in FP32;
+                          stalls near the FP32 rounding floor for tight eps */
+  PSI_FP32_REFINE = 1, /* default: the series of Eq. 13 with FP32 terms summed into an
+                          FP64 iterate, then FP64 residual steps near eps (see psi_solve) */
+  PSI_FP64 = 2         /* Algorithm 2 literally in FP64 */
+};
+/* psi_options.tol_mode: scale applied to eps_t before the test of Eq. 16 */
+enum {
+  PSI_TOL_PSI = 0,   /* default: B_norm * eps_t / N, a bound on ||psi_t - psi_{t-1}||_1 (Eq. 19) */
+  PSI_TOL_S_ABS = 1  /* B_norm * eps_t, the paper's s-tolerance */
+};
+/* psi_options.bnorm_mode: the B_norm of Algorithm 2 */
+enum {
+  PSI_BNORM_NONE = 0, /* default: 1 (>= ||B||_inf, so the more conservative test) */
+  PSI_BNORM_INF = 1   /* ||B||_inf = max_j sum_i b_ji */
+};
+/* psi_options.self_loops (the model has no self-loops, Eq. 5) */
+enum { PSI_REJECT = 0, PSI_DROP = 1 };
+
+/* Optional device allocator.  alloc returns device memory of `bytes` usable on
+ * `stream` (or NULL on failure); free releases it.  Default: cudaMallocAsync /
+ * cudaFreeAsync on the options' stream. */
+typedef struct psi_allocator {
+  void* (*alloc)(size_t bytes, void* stream, void* ctx);
+  void (*free)(void* ptr, size_t bytes, void* stream, void* ctx);
+  void* ctx;
+} psi_allocator;
+
+typedef struct psi_options {
+  int32_t precision;   /* PSI_FP32 | PSI_FP32_REFINE | PSI_FP64 */
+  int32_t tol_mode;    /* PSI_TOL_PSI | PSI_TOL_S_ABS */
+  int32_t bnorm_mode;  /* PSI_BNORM_NONE | PSI_BNORM_INF */
+  int32_t self_loops;  /* PSI_REJECT | PSI_DROP */
+  int32_t reorder;     /* 1 (default): number users internally by class and in-degree so
+                          the gathered iterate is compact in L2; 0: keep the input order
+                          within each class.  Results do not depend on it beyond rounding. */
+  int32_t profile;     /* 1: time every sparse product with CUDA events (psi_solve_info) */
+  void* stream;        /* cudaStream_t to queue all work on */
+  const psi_allocator* allocator; /* NULL: cudaMallocAsync on stream */
+} psi_options;
+
+/* Fills the defaults listed above. */
+void psi_options_default(psi_options* opt);
+
+typedef struct psi_solve_info {
+  int32_t iters;          /* power-iteration steps t performed (each yields s_t) */
+  int32_t converged;      /* 1 if the scaled gap met eps */
+  int32_t refinements;    /* FP64 residual steps taken (PSI_FP32_REFINE) */
+  int32_t spmv_launches;  /* sparse products run (iterations + final psi product) */
+  double gap_s_l1;        /* eps_t = ||s_t - s_{t-1}||_1 of the last step */
+  double gap_scaled;      /* the value compared with eps (tol_mode, bnorm_mode) */
+  double gap_psi_bound;   /* eps_t * ||B||_inf / N, bounds ||psi_t - psi_{t-1}||_1 (Eq. 19) */
+  double psi_sum;         /* sum_i psi_i (FP64); 1 when every user has a leader */
+  double ms;              /* wall time of the solve on the stream (CUDA events) */
+  double spmv_ms;         /* profile == 1: summed duration of the main-precision steps (FP32
+                             series or FP32/FP64 Algorithm 2 steps): sparse product + fix-up */
+  int32_t spmv_timed;     /* profile == 1: number of steps in spmv_ms */
+  int32_t refine_timed;   /* profile == 1: number of FP64 refinement steps in refine_ms */
+  double refine_ms;       /* profile == 1: summed duration of the FP64 refinement steps */
+} psi_solve_info;
+
+typedef struct psi_graph_stats {
+  int64_t n;              /* users */
+  int64_t m_input;        /* edges passed in */
+  int64_t m_unique;       /* distinct follow edges after self-loop handling and merging */
+  int64_t n_rows;         /* users with at least one follower (rows of the iteration) */
+  int64_t n_gathered;     /* users with at least one leader (entries of the gathered iterate) */
+  int64_t max_followers;  /* largest row */
+  double bnorm_inf;       /* ||B||_inf */
+  double rho_inf;         /* max_j sum_{l in L(j)} mu_l / sigma_j (< 1: contraction rate bound) */
+  double build_ms;        /* wall time of psi_graph_create on the stream */
+  int64_t device_bytes;   /* device memory held by the handle */
+} psi_graph_stats;
+
+/*
+ * Build the operator of Sec. II from an edge list.  Edge k: user follower[k] follows user
+ * leader[k] (Sec. II).  Duplicate edges are merged (L(j) is a set); self-loops are
+ * rejected or dropped per opt->self_loops.  lambda[i], mu[i]: posting and re-posting rates
+ * of user i (n entries, FP64).  opt may be NULL (defaults).  m may be 0.
+ * Errors: INVALID_ARG, OUT_OF_RANGE_ID, SELF_LOOP, BAD_RATE, OOM, CUDA; *out is NULL then.
+ */
+psi_status psi_graph_create(int64_t n, int64_t m, const int32_t* follower, const int32_t* leader,
+                            const double* lambda, const double* mu, const psi_options* opt,
+                            psi_graph** out);
+
+/*
+ * Power-psi (Algorithm 2) to tolerance eps with at most max_iter steps, then psi.
+ * init_s (nullable, n FP64 values, host or device) replaces s_0 = c (warm start or
+ * resume; the fixed point does not change).  Returns OK or NOT_CONVERGED (psi is then
+ * computed from the last iterate).  info may be NULL.
+ * PSI_FP32_REFINE: the terms c^T A^t of Eq. 13 are formed in FP32 and summed into an
+ * FP64 s; when their gap meets eps, one FP64 step s <- s A + c is taken and its gap is
+ * the one tested (repeating the FP32 series from its residual if needed), so the
+ * returned gap is an FP64 gap of Algorithm 2.
+ */
+psi_status psi_solve(psi_graph* g, double eps, int32_t max_iter, const double* init_s,
+                     psi_solve_info* info);
+
+/* psi of every user (n FP64 values, host or device), in input user ids. */
+psi_status psi_scores(const psi_graph* g, double* psi_out);
+
+/*
+ * The k highest psi (descending; equal psi by ascending user id): ids_out[k] int32 and
+ * vals_out[k] FP64, host or device (vals_out may be NULL).  1 <= k <= min(n, 65536);
+ * larger k is INVALID_ARG.
+ */
+psi_status psi_topk(const psi_graph* g, int32_t k, int32_t* ids_out, double* vals_out);
+
+/* The last iterate s_t (n FP64 values, input user ids): resume or warm-start source. */
+psi_status psi_get_iterate(const psi_graph* g, double* s_out);
+
+/* Sizes and norms of the built operator. */
+psi_status psi_graph_get_stats(const psi_graph* g, psi_graph_stats* stats);
+
+/* Releases the handle and its device memory (NULL is ignored). */
+void psi_graph_destroy(psi_graph* g);
+
+const char* psi_status_string(psi_status s);
+const char* psi_last_error(void);
+
+/* Number of CUDA kernels this library has launched in this process (instrumentation). */
+int64_t psi_kernel_launches(void);
+
+/* Library version (major*10000 + minor*100 + patch). */
+int32_t psi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PSI_GB300_H */

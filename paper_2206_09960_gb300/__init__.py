@@ -1,0 +1,151 @@
+"""GB300 Power-psi: psi-score ranking of every user of a follower graph.
+
+The computation (graph build, Power-psi iteration, psi, ranking) runs in the CUDA library
+``libpsi_gb300.so`` behind the C ABI of ``include/psi.h``.  This package marshals
+arguments: numpy arrays or torch tensors (host or device) go in as pointers, device
+memory comes from torch's caching allocator through the library's allocator hook, and
+work is queued on torch's current CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _binding as B
+from ._binding import (PsiError, psi_get_iterate, psi_graph_create, psi_graph_destroy,  # noqa: F401
+                       psi_graph_get_stats, psi_kernel_launches, psi_options_default, psi_scores, psi_solve,
+                       psi_topk, psi_version)
+
+__all__ = ["Graph", "PsiError", "psi_graph_create", "psi_solve", "psi_scores", "psi_topk",
+           "psi_get_iterate", "psi_graph_get_stats", "psi_graph_destroy", "psi_options_default",
+           "psi_kernel_launches", "psi_version", "load"]
+
+load = B.load
+
+
+def _ptr(x):
+    """Pointer of a numpy array or torch tensor (contiguous)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        assert x.flags.c_contiguous
+        return ctypes.c_void_p(x.ctypes.data)
+    assert x.is_contiguous()
+    return ctypes.c_void_p(x.data_ptr())
+
+
+class _TorchAllocator:
+    """psi_allocator backed by torch.cuda.caching_allocator_alloc/delete."""
+
+    def __init__(self, device):
+        import torch
+
+        self._torch = torch
+        self._device = device
+
+        def _alloc(nbytes, stream, ctx):
+            try:
+                return int(torch.cuda.caching_allocator_alloc(int(nbytes), self._device, int(stream or 0)))
+            except Exception:
+                return None
+
+        def _free(ptr, nbytes, stream, ctx):
+            try:
+                torch.cuda.caching_allocator_delete(int(ptr))
+            except Exception:
+                pass
+
+        self._a = B.ALLOC_FN(_alloc)
+        self._f = B.FREE_FN(_free)
+        self.struct = B.psi_allocator(self._a, self._f, None)
+
+
+class Graph:
+    """One follower graph on the GPU.
+
+    ``follower[k]`` follows ``leader[k]`` (int32, host or device); ``lam``/``mu`` are FP64
+    per-user rates.  Options mirror ``psi_options`` (precision ``fp32 | fp32_refine | fp64``,
+    tol_mode ``psi | s_abs``, bnorm_mode ``none | inf``, self_loops ``reject | drop``).
+    """
+
+    def __init__(self, n, follower, leader, lam, mu, precision="fp32_refine", tol_mode="psi",
+                 bnorm_mode="none", self_loops="reject", reorder=True, profile=False, stream=None,
+                 allocator="torch"):
+        import torch
+
+        B.load()
+        self.n = int(n)
+        self._keep = [follower, leader, lam, mu]
+        opt = psi_options_default()
+        opt.precision = B.PRECISION[precision]
+        opt.tol_mode = B.TOL_MODE[tol_mode]
+        opt.bnorm_mode = B.BNORM_MODE[bnorm_mode]
+        opt.self_loops = B.SELF_LOOPS[self_loops]
+        opt.reorder = 1 if reorder else 0
+        opt.profile = 1 if profile else 0
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        opt.stream = ctypes.c_void_p(stream.cuda_stream)
+        self._alloc = None
+        if allocator == "torch":
+            self._alloc = _TorchAllocator(torch.cuda.current_device())
+            opt.allocator = ctypes.pointer(self._alloc.struct)
+        self._opt = opt
+        m = int(follower.shape[0]) if follower is not None else 0
+        self._h = psi_graph_create(self.n, m, _ptr(follower), _ptr(leader), _ptr(lam), _ptr(mu), opt)
+        self._keep = None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            psi_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def solve(self, eps, max_iter=10000, init_s=None) -> dict:
+        st, info = psi_solve(self._h, eps, max_iter, _ptr(init_s))
+        out = info.as_dict()
+        out["status"] = B.status_name(st)
+        return out
+
+    def scores(self, out=None):
+        """psi of every user (FP64) into ``out`` (tensor/array, host or device) or a new CUDA tensor."""
+        import torch
+
+        if out is None:
+            out = torch.empty(self.n, dtype=torch.float64, device="cuda")
+        psi_scores(self._h, _ptr(out))
+        return out
+
+    def iterate(self, out=None):
+        import torch
+
+        if out is None:
+            out = torch.empty(self.n, dtype=torch.float64, device="cuda")
+        psi_get_iterate(self._h, _ptr(out))
+        return out
+
+    def topk(self, k, ids=None, vals=None):
+        import torch
+
+        if ids is None:
+            ids = torch.empty(k, dtype=torch.int32, device="cuda")
+        if vals is None:
+            vals = torch.empty(k, dtype=torch.float64, device="cuda")
+        psi_topk(self._h, k, _ptr(ids), _ptr(vals))
+        return ids, vals
+
+    def stats(self) -> dict:
+        return psi_graph_get_stats(self._h).as_dict()

@@ -1,0 +1,505 @@
+// build.cu -- the operator of Sec. II built on the device from an edge list.
+//
+//  1. validate ids, self-loops and rates; count (raw) in- and out-degrees;
+//  2. renumber users by class (X: followers and leaders, R: followers only, U: leaders
+//     only, Z: isolated) and, within a class, by decreasing degree, so rows form one range
+//     [0, nX+nR) and the gathered users one compact L2-friendly range;
+//  3. sort the renumbered (leader, follower) pairs (stable LSD radix), merge duplicates
+//     (L(j) is a set), and cut the transposed CSR: row i = followers of leader i;
+//  4. regroup the unique edges by follower (stable radix on the follower id) and form,
+//     for every follower j, sigma_j = sum_{l in L(j)} (lambda_l + mu_l) and
+//     beta_j = sum_{l in L(j)} lambda_l in FP64 (the denominators of a_ji, b_ji);
+//  5. per-user constants c, d, 1/sigma in FP64 and FP32; ||B||_inf = max_j beta_j/sigma_j;
+//  6. the merge-path tile schedule of the sparse product.
+#include <cmath>
+
+#include "primitives.cuh"
+#include "solve.cuh"
+
+namespace psi {
+
+namespace {
+
+enum : uint32_t { kErrId = 1u, kErrSelf = 2u, kErrRate = 4u };
+
+int grid_for(int64_t n, int threads = 256) {
+  int64_t g = ceil_div(n > 0 ? n : 1, threads);
+  int64_t cap = num_sms() * 16;
+  return (int)(g < cap ? g : cap);
+}
+
+#define GRID_STRIDE(i, n) \
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
+
+// lambda, mu finite, >= 0 and lambda + mu > 0 (the model needs c, d defined)
+__global__ void k_check_rates(const double* __restrict__ lam, const double* __restrict__ mu, int64_t n,
+                              uint32_t* err) {
+  uint32_t bad = 0;
+  GRID_STRIDE(i, n) {
+    double x = lam[i], y = mu[i];
+    if (!(isfinite(x) && isfinite(y) && x >= 0.0 && y >= 0.0 && x + y > 0.0)) bad = kErrRate;
+  }
+  if (bad) atomicOr(err, bad);
+}
+
+__global__ void k_edges(const int32_t* __restrict__ f, const int32_t* __restrict__ l, int64_t m, int64_t n,
+                        int drop_self, uint32_t* in_deg, uint32_t* out_deg, uint32_t* err) {
+  uint32_t bits = 0;
+  GRID_STRIDE(e, m) {
+    int32_t a = f[e], b = l[e];
+    if (a < 0 || a >= n || b < 0 || b >= n) { bits |= kErrId; continue; }
+    if (a == b) { if (!drop_self) bits |= kErrSelf; continue; }
+    atomicAdd(&out_deg[a], 1u);
+    atomicAdd(&in_deg[b], 1u);
+  }
+  if (bits) atomicOr(err, bits);
+}
+
+// key = class (2 bits) | rank (23 bits); value = user id.  A stable sort gives ties by id.
+__global__ void k_node_keys(const uint32_t* __restrict__ in_deg, const uint32_t* __restrict__ out_deg, int64_t n,
+                            int reorder, uint32_t* key, uint32_t* val, uint32_t* class_count) {
+  __shared__ uint32_t cc[4];
+  if (threadIdx.x < 4) cc[threadIdx.x] = 0;
+  __syncthreads();
+  GRID_STRIDE(i, n) {
+    uint32_t di = in_deg[i], dout = out_deg[i];
+    uint32_t cls = di > 0 ? (dout > 0 ? 0u : 1u) : (dout > 0 ? 2u : 3u);
+    uint32_t deg = cls <= 1 ? di : (cls == 2 ? dout : 0u);
+    uint32_t rank = reorder ? (deg >= 0x7FFFFFu ? 0u : 0x7FFFFFu - deg) : 0u;
+    key[i] = (cls << 23) | rank;
+    val[i] = (uint32_t)i;
+    atomicAdd(&cc[cls], 1u);
+  }
+  __syncthreads();
+  if (threadIdx.x < 4 && cc[threadIdx.x]) atomicAdd(&class_count[threadIdx.x], cc[threadIdx.x]);
+}
+
+__global__ void k_invert(const uint32_t* __restrict__ perm, int64_t n, int32_t* inv) {
+  GRID_STRIDE(k, n) inv[perm[k]] = (int32_t)k;
+}
+
+// renumbered key (leader << b) | follower; a dropped self-loop becomes the sentinel
+__global__ void k_edge_keys(const int32_t* __restrict__ f, const int32_t* __restrict__ l, int64_t m,
+                            const int32_t* __restrict__ inv, int b, uint64_t sentinel, uint64_t* key) {
+  GRID_STRIDE(e, m) {
+    int32_t a = f[e], c = l[e];
+    key[e] = (a == c) ? sentinel : (((uint64_t)(uint32_t)inv[c] << b) | (uint64_t)(uint32_t)inv[a]);
+  }
+}
+
+__device__ __forceinline__ bool first_of_run(const uint64_t* key, int64_t e, uint64_t sentinel) {
+  uint64_t k = key[e];
+  return k != sentinel && (e == 0 || key[e - 1] != k);
+}
+
+__global__ void k_unique_flags(const uint64_t* __restrict__ key, int64_t m, uint64_t sentinel, uint32_t* flag) {
+  GRID_STRIDE(e, m) flag[e] = first_of_run(key, e, sentinel) ? 1u : 0u;
+}
+
+__global__ void k_unique_compact(const uint64_t* __restrict__ key, int64_t m, uint64_t sentinel,
+                                 const uint32_t* __restrict__ pos, int b, int32_t* li, int32_t* fi) {
+  const uint64_t mask = ((uint64_t)1 << b) - 1;
+  GRID_STRIDE(e, m) {
+    if (first_of_run(key, e, sentinel)) {
+      uint32_t p = pos[e];
+      uint64_t k = key[e];
+      li[p] = (int32_t)(k >> b);
+      fi[p] = (int32_t)(k & mask);
+    }
+  }
+}
+
+// row_ptr[r] = first unique edge of leader r; counts the rows seen
+__global__ void k_row_bounds(const int32_t* __restrict__ li, int64_t mu, int32_t* row_ptr, uint32_t* rows_seen) {
+  uint32_t c = 0;
+  GRID_STRIDE(e, mu) {
+    if (e == 0 || li[e - 1] != li[e]) {
+      row_ptr[li[e]] = (int32_t)e;
+      ++c;
+    }
+  }
+  if (c) atomicAdd(rows_seen, c);
+}
+
+__global__ void k_set_i32(int32_t* p, int32_t v) { *p = v; }
+
+__global__ void k_row_max(const int32_t* __restrict__ row_ptr, int32_t n_rows, int32_t* mx) {
+  int32_t best = 0;
+  GRID_STRIDE(r, n_rows) {
+    int32_t len = row_ptr[r + 1] - row_ptr[r];
+    best = len > best ? len : best;
+  }
+  atomicMax(mx, best);
+}
+
+__global__ void k_permute_rates(const double* __restrict__ lam, const double* __restrict__ mu,
+                                const uint32_t* __restrict__ perm, int64_t n, double* lam_i, double* mu_i) {
+  GRID_STRIDE(k, n) {
+    uint32_t o = perm[k];
+    lam_i[k] = lam[o];
+    mu_i[k] = mu[o];
+  }
+}
+
+// fptr[x] = first position of follower x in the follower-sorted list
+__global__ void k_lower_bound(const uint32_t* __restrict__ fs, int64_t mu, int64_t n, int32_t* fptr) {
+  GRID_STRIDE(x, n + 1) {
+    int64_t lo = 0, hi = mu;
+    while (lo < hi) {
+      int64_t mid = (lo + hi) >> 1;
+      if ((int64_t)fs[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    fptr[x] = (int32_t)lo;
+  }
+}
+
+// one warp per follower j: sigma_j, beta_j and sum of mu over L(j) (fixed lane order)
+__global__ void k_leader_sums(const int32_t* __restrict__ fptr, const uint32_t* __restrict__ ls,
+                              const double* __restrict__ lam_i, const double* __restrict__ mu_i, int64_t n,
+                              double* sigma, double* beta, double* musum) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t j = wid; j < n; j += nw) {
+    const int32_t b = fptr[j], e = fptr[j + 1];
+    double s = 0.0, sb = 0.0, sm = 0.0;
+    for (int32_t p = b + lane; p < e; p += 32) {
+      uint32_t l = ls[p];
+      double x = lam_i[l], y = mu_i[l];
+      s += x + y;
+      sb += x;
+      sm += y;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s += __shfl_xor_sync(0xffffffffu, s, o);
+      sb += __shfl_xor_sync(0xffffffffu, sb, o);
+      sm += __shfl_xor_sync(0xffffffffu, sm, o);
+    }
+    if (lane == 0) {
+      sigma[j] = s;
+      beta[j] = sb;
+      musum[j] = sm;
+    }
+  }
+}
+
+// c_j = mu_j/(lambda_j+mu_j), d_j = lambda_j/(lambda_j+mu_j), 1/sigma_j (0 without leaders)
+__global__ void k_user_vectors(const double* __restrict__ lam_i, const double* __restrict__ mu_i,
+                               const double* __restrict__ sigma, const double* __restrict__ beta,
+                               const double* __restrict__ musum, int64_t n, double* c64, double* d64,
+                               double* isig64, float* c32, float* mu32, float* isig32,
+                               unsigned long long* bnorm_bits, unsigned long long* rho_bits) {
+  double bn = 0.0, rho = 0.0;
+  GRID_STRIDE(k, n) {
+    double x = lam_i[k], y = mu_i[k], sg = sigma[k];
+    double c = y / (x + y), d = x / (x + y);
+    double is = sg > 0.0 ? 1.0 / sg : 0.0;
+    c64[k] = c;
+    d64[k] = d;
+    isig64[k] = is;
+    c32[k] = (float)c;
+    mu32[k] = (float)y;
+    isig32[k] = (float)is;
+    if (sg > 0.0) {
+      double b = beta[k] / sg, r = musum[k] / sg;
+      bn = b > bn ? b : bn;
+      rho = r > rho ? r : rho;
+    }
+  }
+  // non-negative doubles order like their bit patterns
+  atomicMax(bnorm_bits, (unsigned long long)__double_as_longlong(bn));
+  atomicMax(rho_bits, (unsigned long long)__double_as_longlong(rho));
+}
+
+// tile_row[k] = row holding nonzero k*T (largest r with row_ptr[r] <= k*T); last = n_rows-1
+__global__ void k_tile_rows(const int32_t* __restrict__ row_ptr, int32_t n_rows, int32_t num_tiles,
+                            int32_t* tile_row) {
+  GRID_STRIDE(k, (int64_t)num_tiles + 1) {
+    if (k == num_tiles) {
+      tile_row[k] = n_rows - 1;
+    } else {
+      const int64_t pos = k * (int64_t)kSpmvTile;
+      int32_t lo = 0, hi = n_rows;  // search r in [0, n_rows)
+      while (lo < hi) {
+        int32_t mid = (lo + hi + 1) >> 1;
+        if ((int64_t)row_ptr[mid] <= pos) lo = mid; else hi = mid - 1;
+      }
+      tile_row[k] = lo;
+    }
+  }
+}
+
+// tiles whose first row began in an earlier tile and ends inside this one
+__global__ void k_fix_flags(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ tile_row,
+                            int32_t num_tiles, int64_t mu, uint32_t* flag) {
+  GRID_STRIDE(k, num_tiles) {
+    const int64_t nnz0 = k * (int64_t)kSpmvTile;
+    const int64_t nnz1 = nnz0 + kSpmvTile < mu ? nnz0 + kSpmvTile : mu;
+    const int32_t r0 = tile_row[k];
+    flag[k] = (k > 0 && (int64_t)row_ptr[r0] < nnz0 && (int64_t)row_ptr[r0 + 1] <= nnz1) ? 1u : 0u;
+  }
+}
+
+__global__ void k_fix_compact(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ tile_row,
+                              int32_t num_tiles, int64_t mu, const uint32_t* __restrict__ pos, int32_t* fix) {
+  GRID_STRIDE(k, num_tiles) {
+    const int64_t nnz0 = k * (int64_t)kSpmvTile;
+    const int64_t nnz1 = nnz0 + kSpmvTile < mu ? nnz0 + kSpmvTile : mu;
+    const int32_t r0 = tile_row[k];
+    if (k > 0 && (int64_t)row_ptr[r0] < nnz0 && (int64_t)row_ptr[r0 + 1] <= nnz1) fix[pos[k]] = (int32_t)k;
+  }
+}
+
+__global__ void k_fill_i32(int32_t* x, int64_t lo, int64_t hi, int32_t v) {
+  GRID_STRIDE(i, hi - lo) x[lo + i] = v;
+}
+
+__global__ void k_copy_i32_to_u32(const int32_t* __restrict__ a, int64_t n, uint32_t* b) {
+  GRID_STRIDE(i, n) b[i] = (uint32_t)a[i];
+}
+
+template <typename T>
+T read1(const T* d, cudaStream_t s) {
+  T h{};
+  PSI_CUDA(cudaMemcpyAsync(&h, d, sizeof(T), cudaMemcpyDeviceToHost, s));
+  PSI_CUDA(cudaStreamSynchronize(s));
+  return h;
+}
+
+}  // namespace
+
+bool is_device_pointer(const void* p);
+
+void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const int32_t* leader,
+                 const double* lambda, const double* mu) {
+  cudaStream_t s = g.stream;
+  Allocator& al = g.al;
+  g.n = n;
+  g.m_input = m;
+  cudaEvent_t t0, t1;
+  PSI_CUDA(cudaEventCreate(&t0));
+  PSI_CUDA(cudaEventCreate(&t1));
+  PSI_CUDA(cudaEventRecord(t0, s));
+
+  // ---- stage inputs (host pointers are copied; device pointers are read in place)
+  DBuf<int32_t> fbuf, lbuf;
+  DBuf<double> lam_buf, mu_buf;
+  const int32_t* df = follower;
+  const int32_t* dl = leader;
+  const double* dlam = lambda;
+  const double* dmu = mu;
+  if (m > 0 && !is_device_pointer(follower)) {
+    fbuf.reset(al, (size_t)m);
+    copy_in(fbuf.get(), follower, sizeof(int32_t) * m, s);
+    df = fbuf.get();
+  }
+  if (m > 0 && !is_device_pointer(leader)) {
+    lbuf.reset(al, (size_t)m);
+    copy_in(lbuf.get(), leader, sizeof(int32_t) * m, s);
+    dl = lbuf.get();
+  }
+  if (!is_device_pointer(lambda)) {
+    lam_buf.reset(al, (size_t)n);
+    copy_in(lam_buf.get(), lambda, sizeof(double) * n, s);
+    dlam = lam_buf.get();
+  }
+  if (!is_device_pointer(mu)) {
+    mu_buf.reset(al, (size_t)n);
+    copy_in(mu_buf.get(), mu, sizeof(double) * n, s);
+    dmu = mu_buf.get();
+  }
+
+  // ---- 1. validation and raw degrees
+  DBuf<uint32_t> err(al, 8);  // [0] error bits, [1..4] class counts, [5] rows seen, [6..7] spare
+  PSI_CUDA(cudaMemsetAsync(err.get(), 0, 8 * sizeof(uint32_t), s));
+  DBuf<uint32_t> in_deg(al, (size_t)n), out_deg(al, (size_t)n);
+  PSI_CUDA(cudaMemsetAsync(in_deg.get(), 0, sizeof(uint32_t) * n, s));
+  PSI_CUDA(cudaMemsetAsync(out_deg.get(), 0, sizeof(uint32_t) * n, s));
+  k_check_rates<<<grid_for(n), 256, 0, s>>>(dlam, dmu, n, err.get());
+  PSI_LAUNCHED();
+  if (m > 0) {
+    k_edges<<<grid_for(m), 256, 0, s>>>(df, dl, m, n, g.opt.self_loops == PSI_DROP ? 1 : 0, in_deg.get(),
+                                        out_deg.get(), err.get());
+    PSI_LAUNCHED();
+  }
+  const uint32_t ebits = read1(err.get(), s);
+  PSI_REQUIRE(!(ebits & kErrId), PSI_ERR_OUT_OF_RANGE_ID, "an edge endpoint is outside [0, n)");
+  PSI_REQUIRE(!(ebits & kErrSelf), PSI_ERR_SELF_LOOP, "a user follows itself (self_loops = PSI_REJECT)");
+  PSI_REQUIRE(!(ebits & kErrRate), PSI_ERR_BAD_RATE, "lambda/mu must be finite, >= 0, with lambda + mu > 0");
+
+  // ---- 2. renumbering by class and degree
+  DBuf<uint32_t> perm32;
+  {
+    DBuf<uint32_t> k0(al, (size_t)n), k1(al, (size_t)n), v0(al, (size_t)n), v1(al, (size_t)n);
+    k_node_keys<<<grid_for(n), 256, 0, s>>>(in_deg.get(), out_deg.get(), n, g.opt.reorder ? 1 : 0, k0.get(),
+                                            v0.get(), err.get() + 1);
+    PSI_LAUNCHED();
+    bool alt = radix_sort<uint32_t>(k0.get(), k1.get(), v0.get(), v1.get(), n, 25, al, s);
+    perm32 = alt ? std::move(v1) : std::move(v0);
+  }
+  in_deg.release();
+  out_deg.release();
+  uint32_t cls[4];
+  PSI_CUDA(cudaMemcpyAsync(cls, err.get() + 1, sizeof(cls), cudaMemcpyDeviceToHost, s));
+  PSI_CUDA(cudaStreamSynchronize(s));
+  g.nX = (int32_t)cls[0];
+  g.nR = (int32_t)cls[1];
+  g.nU = (int32_t)cls[2];
+  g.nZ = (int32_t)cls[3];
+  g.n_rows = g.nX + g.nR;
+  g.perm.reset(al, (size_t)n);
+  PSI_CUDA(cudaMemcpyAsync(g.perm.get(), perm32.get(), sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+
+  // ---- 3. sort, merge duplicates, transposed CSR
+  const int b = bits_for((uint64_t)n);  // 2^b > n
+  const uint64_t sentinel = ((uint64_t)1 << (2 * b)) - 1;
+  int64_t mu_count = 0;
+  DBuf<int32_t> li;
+  {
+    DBuf<int32_t> inv(al, (size_t)n);
+    k_invert<<<grid_for(n), 256, 0, s>>>(perm32.get(), n, inv.get());
+    PSI_LAUNCHED();
+    DBuf<uint64_t> k0(al, (size_t)m), k1(al, (size_t)m);
+    if (m > 0) {
+      k_edge_keys<<<grid_for(m), 256, 0, s>>>(df, dl, m, inv.get(), b, sentinel, k0.get());
+      PSI_LAUNCHED();
+    }
+    inv.release();
+    fbuf.release();
+    lbuf.release();
+    bool alt = radix_sort<uint64_t>(k0.get(), k1.get(), nullptr, nullptr, m, 2 * b, al, s);
+    const uint64_t* keys = alt ? k1.get() : k0.get();
+    DBuf<uint32_t> pos(al, (size_t)m);
+    DBuf<uint32_t> total(al, 1);
+    if (m > 0) {
+      k_unique_flags<<<grid_for(m), 256, 0, s>>>(keys, m, sentinel, pos.get());
+      PSI_LAUNCHED();
+      exclusive_scan_u32(pos.get(), pos.get(), m, al, s, total.get());
+      mu_count = read1(total.get(), s);
+    } else {
+      mu_count = 0;
+    }
+    g.m_unique = mu_count;
+    g.num_tiles = (int32_t)ceil_div(mu_count, kSpmvTile);
+    const int64_t padded = (int64_t)g.num_tiles * kSpmvTile;
+    g.col.reset(al, (size_t)(padded > 0 ? padded : 4));
+    li.reset(al, (size_t)(mu_count > 0 ? mu_count : 1));
+    if (mu_count > 0) {
+      k_unique_compact<<<grid_for(m), 256, 0, s>>>(keys, m, sentinel, pos.get(), b, li.get(), g.col.get());
+      PSI_LAUNCHED();
+    }
+    if (padded > mu_count) {
+      k_fill_i32<<<grid_for(padded - mu_count), 256, 0, s>>>(g.col.get(), mu_count, padded, (int32_t)n);
+      PSI_LAUNCHED();
+    }
+  }
+  g.row_ptr.reset(al, (size_t)g.n_rows + 1);
+  {
+    if (mu_count > 0) {
+      k_row_bounds<<<grid_for(mu_count), 256, 0, s>>>(li.get(), mu_count, g.row_ptr.get(), err.get() + 5);
+      PSI_LAUNCHED();
+    }
+    k_set_i32<<<1, 1, 0, s>>>(g.row_ptr.get() + g.n_rows, (int32_t)mu_count);
+    PSI_LAUNCHED();
+    const uint32_t rows_seen = read1(err.get() + 5, s);
+    PSI_REQUIRE((int64_t)rows_seen == g.n_rows, PSI_ERR_CUDA, "internal: row count mismatch in CSR build");
+    DBuf<int32_t> mx(al, 1);
+    PSI_CUDA(cudaMemsetAsync(mx.get(), 0, sizeof(int32_t), s));
+    if (g.n_rows > 0) {
+      k_row_max<<<grid_for(g.n_rows), 256, 0, s>>>(g.row_ptr.get(), g.n_rows, mx.get());
+      PSI_LAUNCHED();
+    }
+    g.max_followers = read1(mx.get(), s);
+  }
+
+  // ---- 4. leader sums per follower
+  DBuf<double> lam_i(al, (size_t)n), mu_i(al, (size_t)n);
+  k_permute_rates<<<grid_for(n), 256, 0, s>>>(dlam, dmu, perm32.get(), n, lam_i.get(), mu_i.get());
+  PSI_LAUNCHED();
+  perm32.release();
+  lam_buf.release();
+  mu_buf.release();
+  DBuf<double> sigma(al, (size_t)n), beta(al, (size_t)n), musum(al, (size_t)n);
+  {
+    const int64_t mc = mu_count > 0 ? mu_count : 1;
+    DBuf<uint32_t> fk0(al, (size_t)mc), fk1(al, (size_t)mc), lv0(al, (size_t)mc), lv1(al, (size_t)mc);
+    if (mu_count > 0) {
+      k_copy_i32_to_u32<<<grid_for(mu_count), 256, 0, s>>>(g.col.get(), mu_count, fk0.get());
+      PSI_LAUNCHED();
+      k_copy_i32_to_u32<<<grid_for(mu_count), 256, 0, s>>>(li.get(), mu_count, lv0.get());
+      PSI_LAUNCHED();
+    }
+    li.release();
+    bool alt = radix_sort<uint32_t>(fk0.get(), fk1.get(), lv0.get(), lv1.get(), mu_count, b, al, s);
+    const uint32_t* fs = alt ? fk1.get() : fk0.get();
+    const uint32_t* ls = alt ? lv1.get() : lv0.get();
+    DBuf<int32_t> fptr(al, (size_t)n + 1);
+    k_lower_bound<<<grid_for(n + 1), 256, 0, s>>>(fs, mu_count, n, fptr.get());
+    PSI_LAUNCHED();
+    int64_t warps = n;
+    int blocks = (int)((warps * 32 + 255) / 256);
+    int cap = (int)num_sms() * 32;
+    k_leader_sums<<<blocks < cap ? blocks : cap, 256, 0, s>>>(fptr.get(), ls, lam_i.get(), mu_i.get(), n,
+                                                              sigma.get(), beta.get(), musum.get());
+    PSI_LAUNCHED();
+  }
+
+  // ---- 5. per-user constants
+  g.c64.reset(al, (size_t)n);
+  g.d64.reset(al, (size_t)n);
+  g.isig64.reset(al, (size_t)n);
+  g.c32.reset(al, (size_t)n);
+  g.mu32.reset(al, (size_t)n);
+  g.isig32.reset(al, (size_t)n);
+  DBuf<unsigned long long> norms(al, 2);
+  PSI_CUDA(cudaMemsetAsync(norms.get(), 0, 2 * sizeof(unsigned long long), s));
+  k_user_vectors<<<grid_for(n), 256, 0, s>>>(lam_i.get(), mu_i.get(), sigma.get(), beta.get(), musum.get(), n,
+                                             g.c64.get(), g.d64.get(), g.isig64.get(), g.c32.get(), g.mu32.get(),
+                                             g.isig32.get(), norms.get(), norms.get() + 1);
+  PSI_LAUNCHED();
+  g.lam64 = std::move(lam_i);
+  g.mu64 = std::move(mu_i);
+  {
+    unsigned long long nb[2];
+    PSI_CUDA(cudaMemcpyAsync(nb, norms.get(), sizeof(nb), cudaMemcpyDeviceToHost, s));
+    PSI_CUDA(cudaStreamSynchronize(s));
+    double v[2];
+    memcpy(v, nb, sizeof(v));
+    g.bnorm_inf = v[0];
+    g.rho_inf = v[1];
+  }
+
+  // ---- 6. tile schedule of the sparse product
+  g.tile_row.reset(al, (size_t)g.num_tiles + 1);
+  g.num_fix = 0;
+  if (g.num_tiles > 0) {
+    k_tile_rows<<<grid_for(g.num_tiles + 1), 256, 0, s>>>(g.row_ptr.get(), g.n_rows, g.num_tiles, g.tile_row.get());
+    PSI_LAUNCHED();
+    DBuf<uint32_t> fpos(al, (size_t)g.num_tiles);
+    DBuf<uint32_t> ftot(al, 1);
+    k_fix_flags<<<grid_for(g.num_tiles), 256, 0, s>>>(g.row_ptr.get(), g.tile_row.get(), g.num_tiles, mu_count,
+                                                      fpos.get());
+    PSI_LAUNCHED();
+    exclusive_scan_u32(fpos.get(), fpos.get(), g.num_tiles, al, s, ftot.get());
+    g.num_fix = (int32_t)read1(ftot.get(), s);
+    g.fix_tile.reset(al, (size_t)(g.num_fix > 0 ? g.num_fix : 1));
+    if (g.num_fix > 0) {
+      k_fix_compact<<<grid_for(g.num_tiles), 256, 0, s>>>(g.row_ptr.get(), g.tile_row.get(), g.num_tiles, mu_count,
+                                                          fpos.get(), g.fix_tile.get());
+      PSI_LAUNCHED();
+    }
+  } else {
+    k_set_i32<<<1, 1, 0, s>>>(g.tile_row.get(), g.n_rows - 1);
+    PSI_LAUNCHED();
+  }
+  PSI_CUDA(cudaEventRecord(t1, s));
+  PSI_CUDA(cudaStreamSynchronize(s));
+  float ms = 0.f;
+  PSI_CUDA(cudaEventElapsedTime(&ms, t0, t1));
+  g.build_ms = ms;
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+}
+
+}  // namespace psi

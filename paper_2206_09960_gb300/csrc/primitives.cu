@@ -1,0 +1,228 @@
+// primitives.cu -- exclusive scan, stable LSD radix sort, deterministic FP64 sum.
+#include "primitives.cuh"
+
+namespace psi {
+
+namespace {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+// block-wide exclusive scan of one value per thread; returns the block total in *total
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* smem_warp, uint32_t* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) smem_warp[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = (lane < (int)(blockDim.x >> 5)) ? smem_warp[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    smem_warp[lane] = w;  // inclusive warp totals
+  }
+  __syncthreads();
+  uint32_t warp_base = warp > 0 ? smem_warp[warp - 1] : 0u;
+  *total = smem_warp[(blockDim.x >> 5) - 1];
+  return warp_base + x - v;
+}
+
+__global__ void k_scan_reduce(const uint32_t* __restrict__ in, int64_t n, uint32_t* __restrict__ sums) {
+  __shared__ uint32_t sw[32];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  uint32_t acc = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i)
+    if (base + i < n) acc += in[base + i];
+  uint32_t tot;
+  block_exclusive_scan(acc, sw, &tot);
+  if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_down(const uint32_t* in, uint32_t* out, int64_t n,
+                            const uint32_t* __restrict__ offsets, uint32_t* d_total) {
+  __shared__ uint32_t sw[32];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  uint32_t v[kScanItems];
+  uint32_t acc = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    v[i] = (base + i < n) ? in[base + i] : 0u;
+    acc += v[i];
+  }
+  uint32_t tot;
+  uint32_t run = block_exclusive_scan(acc, sw, &tot) + (offsets ? offsets[blockIdx.x] : 0u);
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    if (base + i < n) out[base + i] = run;
+    run += v[i];
+  }
+  if (d_total && blockIdx.x == gridDim.x - 1 && threadIdx.x == blockDim.x - 1) *d_total = run;
+}
+
+// ---------------------------------------------------------------- radix sort
+constexpr int kRsThreads = 256;
+constexpr int kRsWarps = kRsThreads / 32;
+constexpr int kRsItems = 16;
+constexpr int kRsTile = kRsThreads * kRsItems;  // 4096 keys per tile
+constexpr int kRsPerWarp = 32 * kRsItems;       // 512 consecutive keys per warp
+
+template <typename K>
+__global__ void __launch_bounds__(kRsThreads) k_radix_histo(const K* __restrict__ keys, int64_t n, int shift,
+                                                           int64_t num_tiles, uint32_t* __restrict__ counts) {
+  __shared__ uint32_t h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kRsTile;
+#pragma unroll 4
+  for (int i = 0; i < kRsItems; ++i) {
+    int64_t idx = base + (int64_t)i * kRsThreads + threadIdx.x;
+    if (idx < n) atomicAdd(&h[(uint32_t)(keys[idx] >> shift) & 0xFFu], 1u);
+  }
+  __syncthreads();
+  counts[(int64_t)threadIdx.x * num_tiles + blockIdx.x] = h[threadIdx.x];
+}
+
+template <typename K, bool VALS>
+__global__ void __launch_bounds__(kRsThreads) k_radix_scatter(const K* __restrict__ keys, const uint32_t* __restrict__ vals,
+                                                             K* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
+                                                             int64_t n, int shift, int64_t num_tiles,
+                                                             const uint32_t* __restrict__ offsets) {
+  __shared__ uint32_t wh[kRsWarps][257];
+  __shared__ uint32_t tile_base[256];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < kRsWarps * 257; i += kRsThreads) (&wh[0][0])[i] = 0;
+  tile_base[threadIdx.x] = offsets[(int64_t)threadIdx.x * num_tiles + blockIdx.x];
+  __syncthreads();
+  const int64_t wbase = (int64_t)blockIdx.x * kRsTile + (int64_t)warp * kRsPerWarp;
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  K k[kRsItems];
+  uint32_t v[kRsItems];
+  uint32_t pos[kRsItems];
+  int dig[kRsItems];
+#pragma unroll
+  for (int r = 0; r < kRsItems; ++r) {
+    int64_t idx = wbase + (int64_t)r * 32 + lane;
+    bool ok = idx < n;
+    k[r] = ok ? keys[idx] : K(0);
+    if (VALS) v[r] = ok ? vals[idx] : 0u;
+    int d = ok ? (int)((uint32_t)(k[r] >> shift) & 0xFFu) : 256;
+    dig[r] = d;
+    uint32_t peers = __match_any_sync(0xffffffffu, d);
+    uint32_t before = wh[warp][d];
+    __syncwarp();
+    if ((peers & lt_mask) == 0) wh[warp][d] = before + __popc(peers);
+    __syncwarp();
+    pos[r] = before + __popc(peers & lt_mask);
+  }
+  __syncthreads();
+  {  // exclusive prefix of the per-warp counts, warp order, for digit = thread
+    const int d = threadIdx.x;
+    uint32_t run = 0;
+#pragma unroll
+    for (int w = 0; w < kRsWarps; ++w) {
+      uint32_t t = wh[w][d];
+      wh[w][d] = run;
+      run += t;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kRsItems; ++r) {
+    int d = dig[r];
+    if (d < 256) {
+      uint32_t o = tile_base[d] + wh[warp][d] + pos[r];
+      keys_out[o] = k[r];
+      if (VALS) vals_out[o] = v[r];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- FP64 sum
+constexpr int kSumThreads = 512;
+constexpr int kSumBlocks = 512;
+
+__global__ void k_sum_partial(const double* __restrict__ x, int64_t n, double* __restrict__ part) {
+  __shared__ double sh[kSumThreads];
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * kSumThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kSumThreads)
+    acc += x[i];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = kSumThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+}  // namespace
+
+void exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, Allocator& al, cudaStream_t s,
+                        uint32_t* d_total) {
+  if (n <= 0) {
+    if (d_total) PSI_CUDA(cudaMemsetAsync(d_total, 0, sizeof(uint32_t), s));
+    return;
+  }
+  const int64_t blocks = ceil_div(n, kScanTile);
+  if (blocks == 1) {
+    k_scan_down<<<1, kScanThreads, 0, s>>>(in, out, n, nullptr, d_total);
+    PSI_LAUNCHED();
+    return;
+  }
+  DBuf<uint32_t> sums(al, (size_t)blocks);
+  k_scan_reduce<<<(unsigned)blocks, kScanThreads, 0, s>>>(in, n, sums.get());
+  PSI_LAUNCHED();
+  exclusive_scan_u32(sums.get(), sums.get(), blocks, al, s, nullptr);
+  k_scan_down<<<(unsigned)blocks, kScanThreads, 0, s>>>(in, out, n, sums.get(), d_total);
+  PSI_LAUNCHED();
+}
+
+template <typename K>
+bool radix_sort(K* keys, K* keys_alt, uint32_t* vals, uint32_t* vals_alt, int64_t n, int bits, Allocator& al,
+                cudaStream_t s) {
+  if (n <= 1 || bits <= 0) return false;
+  const int64_t tiles = ceil_div(n, kRsTile);
+  DBuf<uint32_t> counts(al, (size_t)(tiles * 256));
+  K* src = keys;
+  K* dst = keys_alt;
+  uint32_t* vsrc = vals;
+  uint32_t* vdst = vals_alt;
+  bool flipped = false;
+  for (int shift = 0; shift < bits; shift += 8) {
+    k_radix_histo<K><<<(unsigned)tiles, kRsThreads, 0, s>>>(src, n, shift, tiles, counts.get());
+    PSI_LAUNCHED();
+    exclusive_scan_u32(counts.get(), counts.get(), tiles * 256, al, s, nullptr);
+    if (vals)
+      k_radix_scatter<K, true><<<(unsigned)tiles, kRsThreads, 0, s>>>(src, vsrc, dst, vdst, n, shift, tiles, counts.get());
+    else
+      k_radix_scatter<K, false><<<(unsigned)tiles, kRsThreads, 0, s>>>(src, nullptr, dst, nullptr, n, shift, tiles,
+                                                                      counts.get());
+    PSI_LAUNCHED();
+    std::swap(src, dst);
+    std::swap(vsrc, vdst);
+    flipped = !flipped;
+  }
+  return flipped;
+}
+
+template bool radix_sort<uint32_t>(uint32_t*, uint32_t*, uint32_t*, uint32_t*, int64_t, int, Allocator&, cudaStream_t);
+template bool radix_sort<uint64_t>(uint64_t*, uint64_t*, uint32_t*, uint32_t*, int64_t, int, Allocator&, cudaStream_t);
+
+void sum_f64(const double* x, int64_t n, double* d_out, Allocator& al, cudaStream_t s) {
+  DBuf<double> part(al, kSumBlocks);
+  k_sum_partial<<<kSumBlocks, kSumThreads, 0, s>>>(x, n, part.get());
+  PSI_LAUNCHED();
+  k_sum_partial<<<1, kSumThreads, 0, s>>>(part.get(), kSumBlocks, d_out);
+  PSI_LAUNCHED();
+}
+
+}  // namespace psi

@@ -1,0 +1,31 @@
+// primitives.cuh -- device-wide building blocks written for this library: exclusive
+// scan, stable LSD radix sort, deterministic FP64 sum.
+#pragma once
+
+#include "common.cuh"
+
+namespace psi {
+
+// out[i] = in[0] + ... + in[i-1] (uint32).  in == out is allowed.  If d_total is not
+// null it receives the sum of all n values (device memory).
+void exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, Allocator& al,
+                        cudaStream_t s, uint32_t* d_total = nullptr);
+
+// Stable LSD radix sort of keys on bits [0, bits), 8 bits per pass, carrying an optional
+// uint32 payload (vals may be null).  Sorts between (keys, vals) and (keys_alt,
+// vals_alt); returns true when the sorted data ended up in the *_alt buffers.
+template <typename K>
+bool radix_sort(K* keys, K* keys_alt, uint32_t* vals, uint32_t* vals_alt, int64_t n, int bits,
+                Allocator& al, cudaStream_t s);
+
+// Deterministic FP64 sum of n values (fixed order for a given n) into *d_out.
+void sum_f64(const double* x, int64_t n, double* d_out, Allocator& al, cudaStream_t s);
+
+// Number of bits needed to hold values in [0, v].
+inline int bits_for(uint64_t v) {
+  int b = 0;
+  while (b < 64 && (v >> b) != 0) ++b;
+  return b;
+}
+
+}  // namespace psi

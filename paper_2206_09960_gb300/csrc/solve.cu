@@ -1,0 +1,600 @@
+// solve.cu -- Power-psi (Algorithm 2) on the device: step kernels, the device-side stop
+// test, the three precision modes and the final psi.
+#include <cmath>
+
+#include "primitives.cuh"
+#include "solve.cuh"
+#include "spmv.cuh"
+
+namespace psi {
+
+namespace {
+
+constexpr int kFixWarps = 8;
+
+// Closes rows that began in an earlier tile: y = sum of the tile carries in tile order
+// plus the partial of the tile where the row ends.
+template <typename T, typename Epi>
+__global__ void __launch_bounds__(kFixWarps * 32) k_fixup(FixArgs a, Epi epi) {
+  if (a.state->done) return;
+  __shared__ double gsh[kFixWarps];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint64_t pol_s = policy_evict_first();
+  const uint64_t pol_k = policy_evict_last();
+  const T* ch = static_cast<const T*>(a.carry_head);
+  const T* ct = static_cast<const T*>(a.carry_tail);
+  double gap = 0.0;
+  for (int32_t q = blockIdx.x * kFixWarps + warp; q < a.num_fix; q += gridDim.x * kFixWarps) {
+    const int32_t k = a.fix_tile[q];
+    const int32_t r0 = a.tile_row[k];
+    const int32_t ks = a.row_ptr[r0] / kSpmvTile;  // tile where row r0 begins
+    T acc = T(0);
+    for (int32_t kk = ks + lane; kk < k; kk += 32) acc += ct[kk];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) epi.row(r0, acc + ch[k], gap, pol_s, pol_k);
+  }
+  if (lane == 0) gsh[warp] = gap;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kFixWarps; ++w) t += gsh[w];
+    a.gap_fix[blockIdx.x] = t;
+  }
+}
+
+// Sums the step's gap partials in a fixed order and applies the stop test of
+// Algorithm 2: stop when scale * ||s_t - s_{t-1}||_1 <= eps (Eqs. 15-16) or at max_iter.
+__global__ void __launch_bounds__(1024) k_finalize(DevState* st, const double* __restrict__ gp, int ngp,
+                                                  const double* __restrict__ gf, int ngf) {
+  if (st->done) return;
+  __shared__ double sh[1024];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < ngp; i += blockDim.x) acc += gp[i];
+  for (int i = threadIdx.x; i < ngf; i += blockDim.x) acc += gf[i];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double gap = sh[0] + st->extra_gap;
+    st->extra_gap = 0.0;
+    st->gap = gap;
+    st->gap_scaled = gap * st->scale;
+    st->total_iters += 1;
+    st->phase_iters += 1;
+    if (st->gap_scaled <= st->eps) {
+      st->done = 1;
+      st->converged = 1;
+    } else if (st->total_iters >= st->max_iter) {
+      st->done = 1;
+      st->converged = 0;
+    }
+  }
+}
+
+__global__ void k_phase_begin(DevState* st) {
+  st->phase_iters = 0;
+  st->converged = 0;
+  st->done = st->total_iters >= st->max_iter ? 1 : 0;
+}
+
+template <typename T>
+__global__ void k_fill(T* x, int64_t n, T v) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) x[i] = v;
+}
+
+template <typename D, typename S>
+__global__ void k_convert(D* dst, const S* src, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = (D)src[i];
+}
+
+// dst[i] = s[i] * isig[i] on [lo, hi); dst[n] = 0 pad
+template <typename T, typename S>
+__global__ void k_scale(T* dst, const S* s, const T* isig, int64_t lo, int64_t hi) {
+  for (int64_t i = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < hi; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = (T)s[i] * isig[i];
+}
+
+// out[k] = in[perm[k]] (gather into internal order)
+__global__ void k_gather_f64(double* out, const double* in, const int32_t* perm, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = in[perm[i]];
+}
+
+// non-row users of a warm start: their s_1 = c; the change |c - s_0| joins the first gap
+__global__ void k_nonrow_start(double* s, const double* c, int64_t lo, int64_t n, double* part) {
+  __shared__ double sh[256];
+  double acc = 0.0;
+  for (int64_t i = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    acc += fabs(c[i] - s[i]);
+    s[i] = c[i];
+  }
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void k_set_extra_gap(DevState* st, const double* part, int np) {
+  double acc = 0.0;
+  for (int i = 0; i < np; ++i) acc += part[i];
+  st->extra_gap = acc;
+}
+
+// psi of users without followers: G = 0, psi = d / N
+__global__ void k_psi_nonrow(double* psi, const double* d, int64_t lo, int64_t n) {
+  for (int64_t i = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    psi[i] = d[i] / (double)n;
+}
+
+int elementwise_grid(int64_t n) {
+  int64_t g = ceil_div(n > 0 ? n : 1, 256);
+  int64_t cap = num_sms() * 8;
+  return (int)(g < cap ? g : cap);
+}
+
+template <typename T>
+void fill(T* x, int64_t n, T v, cudaStream_t s) {
+  if (n <= 0) return;
+  k_fill<T><<<elementwise_grid(n), 256, 0, s>>>(x, n, v);
+  PSI_LAUNCHED();
+}
+
+template <typename T, typename Epi>
+int spmv_grid() {
+  static int per_sm = -1;
+  if (per_sm < 0) {
+    int b = 0;
+    PSI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_spmv<T, Epi>, kSpmvThreads, 0));
+    per_sm = b > 0 ? b : 1;
+  }
+  return per_sm * (int)num_sms();
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ step launch
+struct Stepper {
+  Graph& g;
+  cudaStream_t s;
+  bool profile;
+  std::vector<cudaEvent_t>& ev;   // pairs (start, stop) per product
+  std::vector<int>& ev_phase;     // phase-local index of each pair
+  int phase_step = 0;
+  int launches = 0;
+
+  template <typename T, typename Epi>
+  void step(const T* u, const Epi& epi) {
+    SpmvArgs a{};
+    a.row_ptr = g.row_ptr.get();
+    a.col = g.col.get();
+    a.tile_row = g.tile_row.get();
+    a.num_tiles = g.num_tiles;
+    a.n_rows = g.n_rows;
+    a.m = g.m_unique;
+    a.state = g.state.get();
+    a.gap_part = g.gap_part.get();
+    a.carry_head = g.carry_head.get();
+    a.carry_tail = g.carry_tail.get();
+    int grid = 0, fgrid = 0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (profile) {
+      PSI_CUDA(cudaEventCreate(&e0));
+      PSI_CUDA(cudaEventCreate(&e1));
+      PSI_CUDA(cudaEventRecord(e0, s));
+    }
+    if (g.num_tiles > 0) {
+      grid = spmv_grid<T, Epi>();
+      if (grid > g.num_tiles) grid = g.num_tiles;
+      k_spmv<T, Epi><<<grid, kSpmvThreads, 0, s>>>(a, u, epi);
+      PSI_LAUNCHED();
+    }
+    if (g.num_fix > 0) {
+      FixArgs f{};
+      f.row_ptr = g.row_ptr.get();
+      f.tile_row = g.tile_row.get();
+      f.fix_tile = g.fix_tile.get();
+      f.num_fix = g.num_fix;
+      f.state = g.state.get();
+      f.gap_fix = g.gap_fix.get();
+      f.carry_head = g.carry_head.get();
+      f.carry_tail = g.carry_tail.get();
+      fgrid = (int)ceil_div(g.num_fix, kFixWarps);
+      int cap = (int)num_sms() * 8;
+      if (fgrid > cap) fgrid = cap;
+      k_fixup<T, Epi><<<fgrid, kFixWarps * 32, 0, s>>>(f, epi);
+      PSI_LAUNCHED();
+    }
+    if (profile) {
+      PSI_CUDA(cudaEventRecord(e1, s));
+      ev.push_back(e0);
+      ev.push_back(e1);
+      ev_phase.push_back(phase_step);
+    }
+    k_finalize<<<1, 1024, 0, s>>>(g.state.get(), g.gap_part.get(), grid, g.gap_fix.get(), fgrid);
+    PSI_LAUNCHED();
+    ++phase_step;
+    ++launches;
+  }
+};
+
+// Runs one phase of steps; step(k) launches phase step k.  Keeps two batches in flight
+// and stops when the device reports done.  Returns the steps executed.
+template <typename F>
+static int run_phase(Graph& g, cudaStream_t s, Stepper& st, F&& step_k, int batch) {
+  k_phase_begin<<<1, 1, 0, s>>>(g.state.get());
+  PSI_LAUNCHED();
+  st.phase_step = 0;
+  cudaEvent_t evs[2];
+  PSI_CUDA(cudaEventCreateWithFlags(&evs[0], cudaEventDisableTiming));
+  PSI_CUDA(cudaEventCreateWithFlags(&evs[1], cudaEventDisableTiming));
+  DevState* hs = g.host_state;  // two pinned slots
+  int k = 0;
+  auto launch_batch = [&](int slot) {
+    for (int i = 0; i < batch; ++i) step_k(k++);
+    PSI_CUDA(cudaMemcpyAsync(hs + slot, g.state.get(), sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    PSI_CUDA(cudaEventRecord(evs[slot], s));
+  };
+  launch_batch(0);
+  int b = 1;
+  int executed = 0;
+  for (;;) {
+    launch_batch(b & 1);
+    PSI_CUDA(cudaEventSynchronize(evs[(b - 1) & 1]));
+    if (hs[(b - 1) & 1].done) {
+      PSI_CUDA(cudaEventSynchronize(evs[b & 1]));
+      executed = hs[b & 1].phase_iters;
+      break;
+    }
+    ++b;
+  }
+  cudaEventDestroy(evs[0]);
+  cudaEventDestroy(evs[1]);
+  return executed;
+}
+
+// One step outside the batched loop (the FP64 refinement step): run it and read the state.
+template <typename F>
+static DevState run_single(Graph& g, cudaStream_t s, Stepper& st, F&& step_0) {
+  k_phase_begin<<<1, 1, 0, s>>>(g.state.get());
+  PSI_LAUNCHED();
+  st.phase_step = 0;
+  step_0();
+  PSI_CUDA(cudaMemcpyAsync(g.host_state, g.state.get(), sizeof(DevState), cudaMemcpyDeviceToHost, s));
+  PSI_CUDA(cudaStreamSynchronize(s));
+  return g.host_state[0];
+}
+
+static DevState read_state(Graph& g, cudaStream_t s) {
+  PSI_CUDA(cudaMemcpyAsync(g.host_state, g.state.get(), sizeof(DevState), cudaMemcpyDeviceToHost, s));
+  PSI_CUDA(cudaStreamSynchronize(s));
+  return g.host_state[0];
+}
+
+void ensure_iteration_buffers(Graph& g) {
+  if (g.allocated_iter) return;
+  Allocator& al = g.al;
+  const size_t n = (size_t)g.n;
+  const int prec = g.opt.precision;
+  if (prec == PSI_FP32_REFINE || prec == PSI_FP64) {
+    g.s64.reset(al, n);
+    g.u64a.reset(al, n + 1);
+    g.u64b.reset(al, n + 1);
+  }
+  if (prec == PSI_FP64) g.s64b.reset(al, n);
+  if (prec == PSI_FP32) {
+    g.s32a.reset(al, n);
+    g.s32b.reset(al, n);
+  }
+  if (prec == PSI_FP32 || prec == PSI_FP32_REFINE) {
+    g.u32a.reset(al, n + 1);
+    g.u32b.reset(al, n + 1);
+  }
+  if (prec == PSI_FP32_REFINE) g.u32c.reset(al, n + 1);
+  g.psi64.reset(al, n);
+  const size_t nt = (size_t)(g.num_tiles > 0 ? g.num_tiles : 1);
+  g.carry_head.reset(al, nt);
+  g.carry_tail.reset(al, nt);
+  g.gap_part.reset(al, (size_t)num_sms() * 32);
+  g.gap_fix.reset(al, (size_t)num_sms() * 8);
+  g.state.reset(al, 1);
+  if (!g.host_state) PSI_CUDA(cudaMallocHost((void**)&g.host_state, 2 * sizeof(DevState)));
+  g.allocated_iter = true;
+}
+
+static void init_state(Graph& g, cudaStream_t s, double eps, int32_t max_iter) {
+  DevState h{};
+  h.max_iter = max_iter;
+  h.eps = eps;
+  const double bn = g.opt.bnorm_mode == PSI_BNORM_INF ? g.bnorm_inf : 1.0;
+  h.scale = bn * (g.opt.tol_mode == PSI_TOL_PSI ? 1.0 / (double)g.n : 1.0);
+  g.host_state[0] = h;
+  PSI_CUDA(cudaMemcpyAsync(g.state.get(), g.host_state, sizeof(DevState), cudaMemcpyHostToDevice, s));
+  PSI_CUDA(cudaStreamSynchronize(s));  // the pinned slot is reused below
+}
+
+// s_dst (internal order) = the caller's warm start (input order, host or device)
+static void load_init(Graph& g, cudaStream_t s, const double* init_s, double* s_dst) {
+  const int64_t n = g.n;
+  DBuf<double> tmp(g.al, (size_t)n);
+  copy_in(tmp.get(), init_s, sizeof(double) * n, s);
+  k_gather_f64<<<elementwise_grid(n), 256, 0, s>>>(s_dst, tmp.get(), g.perm.get(), n);
+  PSI_LAUNCHED();
+}
+
+// Users without followers have s_t = c for t >= 1; with a warm start their change
+// |c - s_0| belongs to the first step's gap.  Sets s to c there and queues that change.
+static void nonrow_start(Graph& g, cudaStream_t s, double* s64) {
+  const int64_t n = g.n;
+  if (g.n_rows >= n) return;
+  const int blocks = 64;
+  DBuf<double> part(g.al, blocks);
+  k_nonrow_start<<<blocks, 256, 0, s>>>(s64, g.c64.get(), g.n_rows, n, part.get());
+  PSI_LAUNCHED();
+  k_set_extra_gap<<<1, 1, 0, s>>>(g.state.get(), part.get(), blocks);
+  PSI_LAUNCHED();
+}
+
+psi_status solve(Graph& g, double eps, int32_t max_iter, const double* init_s, psi_solve_info* info) {
+  PSI_REQUIRE(max_iter >= 0, PSI_ERR_INVALID_ARG, "max_iter must be >= 0");
+  PSI_REQUIRE(!std::isnan(eps), PSI_ERR_INVALID_ARG, "eps is NaN");
+  cudaStream_t s = g.stream;
+  ensure_iteration_buffers(g);
+  g.solved = false;
+  const int64_t n = g.n;
+  const int32_t nX = g.nX;
+  const int64_t u_lo = (int64_t)g.nX + g.nR;      // U begins here
+  const int64_t g_hi = u_lo + g.nU;               // X and U (the gathered users) end here
+  const int prec = g.opt.precision;
+  const int batch = g.m_unique > ((int64_t)1 << 24) ? 2 : 8;
+  const int eg = elementwise_grid(n);
+
+  cudaEvent_t t0, t1;
+  PSI_CUDA(cudaEventCreate(&t0));
+  PSI_CUDA(cudaEventCreate(&t1));
+  init_state(g, s, eps, max_iter);
+  PSI_CUDA(cudaEventRecord(t0, s));
+
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> ev_phase;
+  struct Timed { size_t first; int steps; bool refine; };
+  std::vector<Timed> timed;  // event pairs of each phase: first pair, steps executed, FP64 refinement?
+  Stepper st{g, s, g.opt.profile != 0, ev, ev_phase};
+  // Algorithm 2 enters its loop only while gap (initially 1) > eps
+  const bool iterate = (1.0 > eps) && max_iter > 0;
+  int refinements = 0;
+  const double* u_final64 = nullptr;
+  const float* u_final32 = nullptr;
+  // gathered vector of s_0 when a warm start is given (U users use s_0 in step 1 only)
+  DBuf<double> u0_64;
+  DBuf<float> u0_32;
+
+  if (prec == PSI_FP64) {
+    double* sb[2] = {g.s64.get(), g.s64b.get()};
+    double* ub[2] = {g.u64a.get(), g.u64b.get()};
+    for (int b = 0; b < 2; ++b) {  // X from s_0 = c, U = c/sigma (s_t = c there for t >= 1)
+      fill<double>(ub[b], n + 1, 0.0, s);
+      k_scale<double, double><<<eg, 256, 0, s>>>(ub[b], g.c64.get(), g.isig64.get(), 0, g_hi);
+      PSI_LAUNCHED();
+    }
+    const double* u_first = ub[0];
+    if (init_s) {
+      load_init(g, s, init_s, sb[0]);
+      u0_64.reset(g.al, (size_t)n + 1);
+      fill<double>(u0_64.get(), n + 1, 0.0, s);
+      k_scale<double, double><<<eg, 256, 0, s>>>(u0_64.get(), sb[0], g.isig64.get(), 0, g_hi);
+      PSI_LAUNCHED();
+      if (iterate) nonrow_start(g, s, sb[0]);
+      u_first = u0_64.get();
+    } else {
+      PSI_CUDA(cudaMemcpyAsync(sb[0], g.c64.get(), sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    }
+    PSI_CUDA(cudaMemcpyAsync(sb[1], sb[0], sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    int steps = 0;
+    if (iterate) {
+      size_t first = ev_phase.size();
+      steps = run_phase(g, s, st, [&](int k) {
+        EpiPlain<double> e{g.c64.get(), g.mu64.get(), g.isig64.get(), sb[k & 1], sb[(k + 1) & 1], ub[(k + 1) & 1], nX};
+        st.step<double>(k == 0 ? u_first : ub[k & 1], e);
+      }, batch);
+      timed.push_back({first, steps, false});
+    }
+    g.last_s_kind = (steps & 1) ? 1 : 0;
+    u_final64 = (steps == 0) ? u_first : ub[steps & 1];
+  } else if (prec == PSI_FP32) {
+    float* sb[2] = {g.s32a.get(), g.s32b.get()};
+    float* ub[2] = {g.u32a.get(), g.u32b.get()};
+    for (int b = 0; b < 2; ++b) {
+      fill<float>(ub[b], n + 1, 0.0f, s);
+      k_scale<float, float><<<eg, 256, 0, s>>>(ub[b], g.c32.get(), g.isig32.get(), 0, g_hi);
+      PSI_LAUNCHED();
+    }
+    const float* u_first = ub[0];
+    if (init_s) {
+      DBuf<double> s0(g.al, (size_t)n);
+      load_init(g, s, init_s, s0.get());
+      DBuf<double> u0(g.al, (size_t)n + 1);
+      fill<double>(u0.get(), n + 1, 0.0, s);
+      k_scale<double, double><<<eg, 256, 0, s>>>(u0.get(), s0.get(), g.isig64.get(), 0, g_hi);
+      PSI_LAUNCHED();
+      u0_32.reset(g.al, (size_t)n + 1);
+      k_convert<float, double><<<eg, 256, 0, s>>>(u0_32.get(), u0.get(), n + 1);
+      PSI_LAUNCHED();
+      if (iterate) nonrow_start(g, s, s0.get());
+      k_convert<float, double><<<eg, 256, 0, s>>>(sb[0], s0.get(), n);
+      PSI_LAUNCHED();
+      u_first = u0_32.get();
+    } else {
+      k_convert<float, double><<<eg, 256, 0, s>>>(sb[0], g.c64.get(), n);
+      PSI_LAUNCHED();
+    }
+    PSI_CUDA(cudaMemcpyAsync(sb[1], sb[0], sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
+    int steps = 0;
+    if (iterate) {
+      size_t first = ev_phase.size();
+      steps = run_phase(g, s, st, [&](int k) {
+        EpiPlain<float> e{g.c32.get(), g.mu32.get(), g.isig32.get(), sb[k & 1], sb[(k + 1) & 1], ub[(k + 1) & 1], nX};
+        st.step<float>(k == 0 ? u_first : ub[k & 1], e);
+      }, batch);
+      timed.push_back({first, steps, false});
+    }
+    g.last_s_kind = (steps & 1) ? 3 : 2;
+    u_final32 = (steps == 0) ? u_first : ub[steps & 1];
+  } else {  // PSI_FP32_REFINE
+    double* s64 = g.s64.get();
+    double* ub[2] = {g.u64a.get(), g.u64b.get()};
+    float* v0 = g.u32c.get();
+    float* vb[2] = {g.u32a.get(), g.u32b.get()};
+    for (int b = 0; b < 2; ++b) {
+      fill<double>(ub[b], n + 1, 0.0, s);  // U = c/sigma in both FP64 gathered buffers
+      k_scale<double, double><<<eg, 256, 0, s>>>(ub[b], g.c64.get(), g.isig64.get(), u_lo, g_hi);
+      PSI_LAUNCHED();
+      fill<float>(vb[b], n + 1, 0.0f, s);  // series terms of U users vanish after the first
+    }
+    fill<float>(v0, n + 1, 0.0f, s);
+    int cur_u = 0;            // FP64 buffer that will hold u of the current s64
+    bool u_current = false;   // whether it does now
+    const double* u_resid_in = nullptr;
+    bool resid_first = false;
+    if (init_s) {
+      load_init(g, s, init_s, s64);
+      u0_64.reset(g.al, (size_t)n + 1);
+      fill<double>(u0_64.get(), n + 1, 0.0, s);
+      k_scale<double, double><<<eg, 256, 0, s>>>(u0_64.get(), s64, g.isig64.get(), 0, g_hi);
+      PSI_LAUNCHED();
+      if (iterate) nonrow_start(g, s, s64);
+      u_resid_in = u0_64.get();  // the first step is an FP64 step from s_0
+      resid_first = true;
+    } else {
+      PSI_CUDA(cudaMemcpyAsync(s64, g.c64.get(), sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+      // the first series term is c itself: v0 = c/sigma on X and U
+      k_scale<float, float><<<eg, 256, 0, s>>>(v0, g.c32.get(), g.isig32.get(), 0, g_hi);
+      PSI_LAUNCHED();
+    }
+    bool v0_u_cleared = false;
+    if (iterate) {
+      for (;;) {
+        if (!resid_first) {
+          // FP32 series from v0 (Eq. 13), terms summed into s64
+          size_t first = ev_phase.size();
+          int steps = run_phase(g, s, st, [&](int k) {
+            const float* vin = (k == 0) ? v0 : vb[(k + 1) & 1];
+            EpiSeries e{g.mu32.get(), g.isig32.get(), s64, vb[k & 1], nX};
+            st.step<float>(vin, e);
+          }, batch);
+          timed.push_back({first, steps, false});
+          if (steps > 0) u_current = false;
+          DevState h = read_state(g, s);
+          if (!h.converged) break;  // the step cap came first
+          // FP64 gathered vector of the series' s64 (X users; U hold c/sigma)
+          k_scale<double, double><<<eg, 256, 0, s>>>(ub[cur_u], s64, g.isig64.get(), 0, nX);
+          PSI_LAUNCHED();
+          u_current = true;
+          u_resid_in = ub[cur_u];
+        }
+        resid_first = false;
+        if (!v0_u_cleared && u_lo < g_hi) {  // later series start from a residual: U terms are 0
+          fill<float>(v0 + u_lo, g_hi - u_lo, 0.0f, s);
+          v0_u_cleared = true;
+        }
+        // one FP64 step s <- s A + c from s64; its gap is the one tested
+        size_t first = ev_phase.size();
+        double* u_out = ub[cur_u ^ 1];
+        DevState h = run_single(g, s, st, [&]() {
+          EpiResid e{g.c64.get(), g.mu64.get(), g.isig64.get(), s64, u_out, v0, nX};
+          st.step<double>(u_resid_in, e);
+        });
+        timed.push_back({first, h.phase_iters, true});
+        if (h.phase_iters == 0) break;  // the step cap came first
+        ++refinements;
+        cur_u ^= 1;
+        u_current = true;
+        if (h.converged || h.total_iters >= max_iter) break;
+      }
+    }
+    if (!u_current) {  // psi from the current s64 (after a capped series, or no loop)
+      k_scale<double, double><<<eg, 256, 0, s>>>(ub[cur_u], s64, g.isig64.get(), 0, nX);
+      PSI_LAUNCHED();
+    }
+    g.last_s_kind = 0;
+    // without any step, psi comes from s_0 itself (a warm start reaches U users too)
+    u_final64 = (!iterate && init_s) ? u0_64.get() : ub[cur_u];
+  }
+
+  // final step of Algorithm 2: psi^T = (s^T B + d^T) / N, one more product
+  const DevState h = read_state(g, s);
+  {
+    DevState run = h;
+    run.done = 0;
+    run.max_iter = INT32_MAX;
+    g.host_state[1] = run;
+    PSI_CUDA(cudaMemcpyAsync(g.state.get(), &g.host_state[1], sizeof(DevState), cudaMemcpyHostToDevice, s));
+  }
+  st.phase_step = 0;
+  if (u_final64) {
+    EpiFinal<double> e{g.lam64.get(), g.d64.get(), g.psi64.get(), (double)n};
+    st.step<double>(u_final64, e);
+  } else {
+    EpiFinal<float> e{g.lam64.get(), g.d64.get(), g.psi64.get(), (double)n};
+    st.step<float>(u_final32, e);
+  }
+  if (g.n_rows < n) {
+    k_psi_nonrow<<<elementwise_grid(n - g.n_rows), 256, 0, s>>>(g.psi64.get(), g.d64.get(), g.n_rows, n);
+    PSI_LAUNCHED();
+  }
+  PSI_CUDA(cudaEventRecord(t1, s));
+  DBuf<double> dsum(g.al, 1);
+  sum_f64(g.psi64.get(), n, dsum.get(), g.al, s);
+  PSI_CUDA(cudaMemcpyAsync(&g.host_state[0].gap, dsum.get(), sizeof(double), cudaMemcpyDeviceToHost, s));
+  PSI_CUDA(cudaStreamSynchronize(s));
+  const double psi_sum = g.host_state[0].gap;
+  float ms = 0.f;
+  PSI_CUDA(cudaEventElapsedTime(&ms, t0, t1));
+  double spmv_ms = 0.0, refine_ms = 0.0;
+  int timed_n = 0, refine_n = 0;
+  for (const Timed& ph : timed) {
+    for (int q = 0; q < ph.steps; ++q) {
+      size_t idx = ph.first + (size_t)q;
+      if (idx >= ev_phase.size()) break;
+      float e = 0.f;
+      PSI_CUDA(cudaEventElapsedTime(&e, ev[2 * idx], ev[2 * idx + 1]));
+      if (ph.refine) {
+        refine_ms += e;
+        ++refine_n;
+      } else {
+        spmv_ms += e;
+        ++timed_n;
+      }
+    }
+  }
+  for (auto e : ev) cudaEventDestroy(e);
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  g.solved = true;
+  if (info) {
+    info->iters = h.total_iters;
+    info->converged = iterate ? h.converged : 1;
+    info->refinements = refinements;
+    info->spmv_launches = h.total_iters + 1;
+    info->gap_s_l1 = h.gap;
+    info->gap_scaled = h.gap_scaled;
+    info->gap_psi_bound = h.gap * g.bnorm_inf / (double)n;
+    info->psi_sum = psi_sum;
+    info->ms = ms;
+    info->spmv_ms = spmv_ms;
+    info->spmv_timed = timed_n;
+    info->refine_timed = refine_n;
+    info->refine_ms = refine_ms;
+  }
+  if (!iterate) return PSI_OK;  // Algorithm 2 with gap = 1 <= eps: psi from s_0
+  return h.converged ? PSI_OK : PSI_ERR_NOT_CONVERGED;
+}
+
+}  // namespace psi

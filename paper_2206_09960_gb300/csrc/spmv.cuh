@@ -1,0 +1,236 @@
+// spmv.cuh -- the Power-psi sparse product, one launch per step.
+//
+// With a_ji = mu_i / sigma_j and b_ji = lambda_i / sigma_j (Sec. II) the operator
+// factorises: s^T A = mu (.) G(s), s^T B = lambda (.) G(s), where
+//     G(s)_i = sum_{j follows i} s_j / sigma_j = sum_{j in F(i)} u_j,   u = s (.) (1/sigma).
+// So one step of Eq. 14 is a pattern-only pull over the followers F(i) of every user i
+// (the transposed CSR: rows = leaders, columns = followers) followed by a per-row
+// epilogue; no per-edge value is stored.
+//
+// Load balance is merge-based: the nonzeros are cut into fixed tiles of kSpmvTile (each
+// thread owns kSpmvItems consecutive nonzeros, loaded as two 16-byte vectors), rows are
+// found by a binary search over the tile's slice of row_ptr, and partial row sums are
+// joined by a block-wide segmented scan.  A row that starts in an earlier tile is closed
+// by the fix-up kernel, which adds the tile carries in tile order.  Every sum therefore
+// runs in an order fixed by the graph alone: results are bit-reproducible.
+#pragma once
+
+#include "common.cuh"
+
+namespace psi {
+
+// ------------------------------------------------------------------ epilogues
+// row(r, y, gap): y = G(.)_r for row r (a user with followers); add |change| to gap.
+
+// Algorithm 2 step in precision T: s_new = c + mu*y (Eq. 14), gap += |s_new - s_old|,
+// u_new = s_new/sigma for users that have leaders.
+template <typename T>
+struct EpiPlain {
+  const T* c;
+  const T* mu;
+  const T* isig;
+  const T* s_old;
+  T* s_new;
+  T* u_new;
+  int32_t nX;
+  __device__ __forceinline__ void row(int32_t r, T y, double& gap, uint64_t pol_s, uint64_t pol_k) const {
+    T s = ld_stream(c + r, pol_s) + ld_stream(mu + r, pol_s) * y;
+    gap += fabs((double)s - (double)ld_stream(s_old + r, pol_s));
+    s_new[r] = s;
+    if (r < nX) st_keep(u_new + r, s * ld_stream(isig + r, pol_s), pol_k);
+  }
+};
+
+// Series step (Eq. 13): term_t = mu * G(term_{t-1}) in FP32, s += term_t in FP64,
+// gap += |term_t| (= |s_t - s_{t-1}|), v_new = term_t / sigma.
+struct EpiSeries {
+  const float* mu;
+  const float* isig;
+  double* s64;
+  float* v_new;
+  int32_t nX;
+  __device__ __forceinline__ void row(int32_t r, float y, double& gap, uint64_t pol_s, uint64_t pol_k) const {
+    float t = ld_stream(mu + r, pol_s) * y;
+    s64[r] += (double)t;
+    gap += fabs((double)t);
+    if (r < nX) st_keep(v_new + r, t * ld_stream(isig + r, pol_s), pol_k);
+  }
+};
+
+// FP64 step from the FP64 iterate: s_new = c + mu*y, r = s_new - s, gap += |r|, s = s_new,
+// u_new = s_new/sigma (next FP64 gather), v32 = r/sigma (start of an FP32 correction series).
+struct EpiResid {
+  const double* c;
+  const double* mu;
+  const double* isig;
+  double* s64;
+  double* u_new;
+  float* v32;
+  int32_t nX;
+  __device__ __forceinline__ void row(int32_t r, double y, double& gap, uint64_t pol_s, uint64_t pol_k) const {
+    double sn = ld_stream(c + r, pol_s) + ld_stream(mu + r, pol_s) * y;
+    double rr = sn - s64[r];
+    gap += fabs(rr);
+    s64[r] = sn;
+    if (r < nX) {
+      double is = ld_stream(isig + r, pol_s);
+      st_keep(u_new + r, sn * is, pol_k);
+      v32[r] = (float)(rr * is);
+    }
+  }
+};
+
+// Final step of Algorithm 2: psi_r = (lambda_r * G(s)_r + d_r) / N.
+template <typename T>
+struct EpiFinal {
+  const double* lam;
+  const double* d;
+  double* psi;
+  double n;
+  __device__ __forceinline__ void row(int32_t r, T y, double& gap, uint64_t pol_s, uint64_t) const {
+    psi[r] = (ld_stream(lam + r, pol_s) * (double)y + ld_stream(d + r, pol_s)) / n;
+  }
+};
+
+struct SpmvArgs {
+  const int32_t* row_ptr;
+  const int32_t* col;
+  const int32_t* tile_row;
+  int32_t num_tiles;
+  int32_t n_rows;
+  int64_t m;
+  const DevState* state;  // skip the step when state->done
+  double* gap_part;       // [gridDim.x]
+  void* carry_head;       // [num_tiles] T
+  void* carry_tail;       // [num_tiles] T
+};
+
+struct FixArgs {
+  const int32_t* row_ptr;
+  const int32_t* tile_row;
+  const int32_t* fix_tile;
+  int32_t num_fix;
+  const DevState* state;
+  double* gap_fix;        // [gridDim.x]
+  const void* carry_head;
+  const void* carry_tail;
+};
+
+// Segmented scan element: f = a row ended inside the span, v = sum after the last row
+// end.  Combining a left span L with the right span R that follows it:
+//   (L.f | R.f, R.f ? R.v : L.v + R.v).
+template <typename T>
+__device__ __forceinline__ void seg_join(int lf, T lv, int& rf, T& rv) {  // R <- L . R
+  if (!rf) rv = lv + rv;
+  rf |= lf;
+}
+
+template <typename T, typename Epi>
+__global__ void __launch_bounds__(kSpmvThreads) k_spmv(SpmvArgs a, const T* __restrict__ u, Epi epi) {
+  if (a.state->done) return;
+  __shared__ int32_t rp[kSpmvTile + 2];
+  __shared__ int wf[kSpmvThreads / 32];
+  __shared__ T wv[kSpmvThreads / 32];
+  __shared__ double gsh[kSpmvThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint64_t pol_s = policy_evict_first();
+  const uint64_t pol_k = policy_evict_last();
+  T* carry_head = static_cast<T*>(a.carry_head);
+  T* carry_tail = static_cast<T*>(a.carry_tail);
+  double gap = 0.0;
+
+  for (int32_t tile = blockIdx.x; tile < a.num_tiles; tile += gridDim.x) {
+    const int64_t nnz0 = (int64_t)tile * kSpmvTile;
+    const int32_t r0 = a.tile_row[tile];
+    const int32_t r_hi = a.tile_row[tile + 1];
+    const int32_t nr = r_hi - r0 + 1;  // rows touching [nnz0, nnz0 + tile)
+    __syncthreads();                    // rp reuse across tiles
+    for (int i = threadIdx.x; i <= nr; i += kSpmvThreads) rp[i] = a.row_ptr[r0 + i];
+    // this thread's nonzeros: p0 .. p0 + kSpmvItems - 1 (col is padded to whole tiles)
+    const int64_t p0 = nnz0 + (int64_t)threadIdx.x * kSpmvItems;
+    T x[kSpmvItems];
+    {
+      const int4* cp = reinterpret_cast<const int4*>(a.col + p0);
+#pragma unroll
+      for (int q = 0; q < kSpmvItems / 4; ++q) {
+        int4 c4 = ld_stream_v4(cp + q, pol_s);
+        x[4 * q + 0] = ld_gather(u + c4.x, pol_k);
+        x[4 * q + 1] = ld_gather(u + c4.y, pol_k);
+        x[4 * q + 2] = ld_gather(u + c4.z, pol_k);
+        x[4 * q + 3] = ld_gather(u + c4.w, pol_k);
+      }
+    }
+    __syncthreads();
+    // first row whose end lies beyond p0
+    int lo = 0, hi = nr;
+    while (lo < hi) {
+      int mid = (lo + hi) >> 1;
+      if ((int64_t)rp[mid + 1] > p0) hi = mid; else lo = mid + 1;
+    }
+    int cur = lo;
+    int64_t next_end = cur < nr ? (int64_t)rp[cur + 1] : INT64_MAX;
+    T acc = T(0), first_val = T(0);
+    int has_end = 0, first_row = 0;
+#pragma unroll
+    for (int i = 0; i < kSpmvItems; ++i) {
+      acc += x[i];
+      if (p0 + i + 1 == next_end) {  // row `cur` ends at nonzero p0 + i
+        if (!has_end) {
+          has_end = 1;
+          first_row = cur;
+          first_val = acc;
+        } else {
+          epi.row(r0 + cur, acc, gap, pol_s, pol_k);
+        }
+        acc = T(0);
+        ++cur;
+        next_end = cur < nr ? (int64_t)rp[cur + 1] : INT64_MAX;
+      }
+    }
+    // block-wide segmented scan of (has_end, acc) in thread order
+    int f = has_end;
+    T v = acc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int fu = __shfl_up_sync(0xffffffffu, f, o);
+      T vu = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) seg_join(fu, vu, f, v);
+    }
+    if (lane == 31) { wf[warp] = f; wv[warp] = v; }
+    int fe = __shfl_up_sync(0xffffffffu, f, 1);  // exclusive within the warp
+    T ve = __shfl_up_sync(0xffffffffu, v, 1);
+    if (lane == 0) { fe = 0; ve = T(0); }
+    __syncthreads();
+    int fw = 0;  // inclusive prefix of the warps before this one
+    T vw = T(0);
+    for (int w = 0; w < warp; ++w) {
+      int g = wf[w];
+      T gv = wv[w];
+      seg_join(fw, vw, g, gv);
+      fw = g;
+      vw = gv;
+    }
+    seg_join(fw, vw, fe, ve);  // exclusive prefix of this thread
+    if (has_end) {
+      T y = ve + first_val;
+      if (!fe && (int64_t)rp[0] < nnz0) carry_head[tile] = y;  // row r0 began in an earlier tile
+      else epi.row(r0 + first_row, y, gap, pol_s, pol_k);
+    }
+    if (threadIdx.x == kSpmvThreads - 1) {
+      seg_join(fw, vw, f, v);  // inclusive prefix of the whole tile
+      carry_tail[tile] = v;
+    }
+  }
+  // per-CTA gap partial, fixed order
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) gap += __shfl_xor_sync(0xffffffffu, gap, o);
+  if (lane == 0) gsh[warp] = gap;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kSpmvThreads / 32; ++w) t += gsh[w];
+    a.gap_part[blockIdx.x] = t;
+  }
+}
+
+}  // namespace psi

@@ -1,0 +1,330 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Bars: relative L1 of psi <= 1e-12 in FP64 mode and <= 1e-6 with FP32 storage; the top-100
+ranking (psi descending, ties by id) identical, except where two oracle values differ by
+less than the comparison tolerance (reported as a near-tie, not a mismatch); integer
+outputs (ranking ids, edge counts) bit-exact.
+"""
+import json
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+import psigen
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "closed_forms.json")
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def gpu_solve(n, f, l, lam, mu, eps, precision="fp32_refine", tol_mode="psi", bnorm_mode="none",
+              max_iter=20000, on_device=True, init_s=None, k=100, **kw):
+    torch = _torch()
+    from paper_2206_09960_gb300 import Graph
+
+    f = np.ascontiguousarray(f, np.int32)
+    l = np.ascontiguousarray(l, np.int32)
+    lam = np.ascontiguousarray(lam, np.float64)
+    mu = np.ascontiguousarray(mu, np.float64)
+    if on_device:
+        args = [torch.from_numpy(x).cuda() for x in (f, l, lam, mu)]
+    else:
+        args = [f, l, lam, mu]
+    with Graph(n, *args, precision=precision, tol_mode=tol_mode, bnorm_mode=bnorm_mode, **kw) as g:
+        init = None if init_s is None else torch.from_numpy(np.ascontiguousarray(init_s, np.float64)).cuda()
+        info = g.solve(eps, max_iter, init)
+        psi = g.scores().cpu().numpy()
+        s = g.iterate().cpu().numpy()
+        kk = min(k, n)
+        ids, vals = g.topk(kk)
+        stats = g.stats()
+    return dict(info=info, psi=psi, s=s, ids=ids.cpu().numpy(), vals=vals.cpu().numpy(), stats=stats)
+
+
+def rel_l1(a, b):
+    return float(np.abs(a - b).sum() / np.abs(b).sum())
+
+
+def assert_same_ranking(gpu_ids, psi_ref, tol):
+    """GPU top-k ids equal the oracle's ranking, allowing swaps only among near-ties."""
+    k = len(gpu_ids)
+    ref_ids, ref_vals = oracle.topk(psi_ref, k)
+    if np.array_equal(gpu_ids, ref_ids):
+        return
+    for pos in np.nonzero(gpu_ids != ref_ids)[0]:
+        a, b = psi_ref[gpu_ids[pos]], psi_ref[ref_ids[pos]]
+        assert abs(a - b) <= tol * max(abs(a), abs(b)), (pos, gpu_ids[pos], ref_ids[pos], a, b)
+
+
+def _cases():
+    with open(GOLDEN) as fh:
+        return json.load(fh)["cases"]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refine", "fp32"])
+@pytest.mark.parametrize("case", _cases(), ids=lambda c: c["name"])
+def test_closed_forms(case, precision):
+    n = case["n"]
+    e = np.array(case["edges"], np.int32).reshape(-1, 2)
+    lam = np.array([float(Fraction(x)) for x in case["lambda"]])
+    mu = np.array([float(Fraction(x)) for x in case["mu"]])
+    want = np.array([float(Fraction(x)) for x in case["psi"]])
+    out = gpu_solve(n, e[:, 0], e[:, 1], lam, mu, 1e-15, precision=precision, tol_mode="s_abs", max_iter=500,
+                    k=n)
+    tol = 1e-14 if precision != "fp32" else 1e-6
+    np.testing.assert_allclose(out["psi"], want, rtol=tol, atol=tol)
+    assert abs(out["info"]["psi_sum"] - want.sum()) < 1e-6
+
+
+def test_two_cycle_gap_sequence_and_stop_rule():
+    """Gaps 3/8, 3/16, 9/128 (golden); the stop rule of Algorithm 2 picks t exactly."""
+    f, l, lam, mu = [0, 1], [1, 0], [1.0, 3.0], [3.0, 1.0]
+    for eps, tol_mode, bn, t in [(0.3, "s_abs", "none", 2), (0.3, "s_abs", "inf", 1), (0.2, "psi", "none", 1),
+                                 (0.05, "psi", "none", 3)]:
+        for prec in ("fp64", "fp32_refine", "fp32"):
+            out = gpu_solve(2, f, l, lam, mu, eps, precision=prec, tol_mode=tol_mode, bnorm_mode=bn, k=2)
+            # fp32_refine confirms the FP32 series' stop with one FP64 step (gap 9/128-ish here)
+            want = t + 1 if prec == "fp32_refine" else t
+            assert out["info"]["iters"] == want, (eps, tol_mode, bn, prec, out["info"])
+    out = gpu_solve(2, f, l, lam, mu, 1.0, precision="fp64", tol_mode="s_abs", k=2)
+    assert out["info"]["iters"] == 0
+    np.testing.assert_allclose(out["s"], [0.75, 0.25])
+    out = gpu_solve(2, f, l, lam, mu, 1e-30, precision="fp64", tol_mode="s_abs", max_iter=4, k=2)
+    assert out["info"]["iters"] == 4 and out["info"]["status"] == "PSI_ERR_NOT_CONVERGED"
+
+
+def test_poisson1000_fp64_matches_direct_solve_and_oracle():
+    from oracle import dense
+
+    w = psigen.workload("poisson1000", seed=0)
+    n = w["n"]
+    ref = oracle.solve(n, w["follower"], w["leader"], w["lam"], w["mu"], eps=1e-12, tol_mode=oracle.TOL_S_ABS)
+    direct = dense.direct_psi(n, w["follower"], w["leader"], w["lam"], w["mu"])
+    out = gpu_solve(n, w["follower"], w["leader"], w["lam"], w["mu"], 1e-12, precision="fp64", tol_mode="s_abs")
+    assert out["info"]["converged"]
+    assert abs(out["info"]["iters"] - ref["iters"]) <= 1
+    assert rel_l1(out["psi"], ref["psi"]) <= 1e-12
+    assert rel_l1(out["psi"], direct) <= 1e-12
+    assert_same_ranking(out["ids"], direct, 1e-12)
+    assert out["stats"]["m_unique"] == ref["m_unique"]
+
+
+@pytest.mark.parametrize("scale", [14, 17])
+def test_chunglu_fp32_refine(scale):
+    w = psigen.workload("chunglu", seed=1, scale=scale)
+    n = w["n"]
+    ref = oracle.solve(n, w["follower"], w["leader"], w["lam"], w["mu"], to_floor=True, max_iter=5000)
+    out = gpu_solve(n, w["follower"], w["leader"], w["lam"], w["mu"], 1e-8)
+    assert out["info"]["converged"], out["info"]
+    assert out["info"]["gap_scaled"] <= 1e-8
+    assert rel_l1(out["psi"], ref["psi"]) <= 1e-6
+    assert_same_ranking(out["ids"], ref["psi"], 1e-6)
+    assert out["stats"]["m_unique"] == ref["m_unique"]
+    assert abs(out["info"]["psi_sum"] - ref["psi"].sum()) <= 1e-6 * ref["psi"].sum()
+
+
+def test_chunglu_full_size_fp32_refine():
+    """The Chung-Lu workload at its full size (N=2^20, 2e7 draws)."""
+    w = psigen.workload("chunglu", seed=0)
+    n = w["n"]
+    ref = oracle.solve(n, w["follower"], w["leader"], w["lam"], w["mu"], to_floor=True, max_iter=5000)
+    out = gpu_solve(n, w["follower"], w["leader"], w["lam"], w["mu"], 1e-8)
+    assert out["info"]["converged"]
+    assert rel_l1(out["psi"], ref["psi"]) <= 1e-6
+    assert_same_ranking(out["ids"], ref["psi"], 1e-6)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32_refine", 1e-6)])
+def test_rmat_small(precision, tol):
+    w = psigen.workload("rmat", seed=2, scale=16)
+    n = w["n"]
+    ref = oracle.solve(n, w["follower"], w["leader"], w["lam"], w["mu"], to_floor=True, max_iter=5000)
+    eps = 1e-15 if precision == "fp64" else 1e-8
+    out = gpu_solve(n, w["follower"], w["leader"], w["lam"], w["mu"], eps, precision=precision, max_iter=5000)
+    if precision == "fp64":  # may stop at the rounding floor before eps
+        assert out["info"]["gap_scaled"] < 1e-13
+    else:
+        assert out["info"]["converged"]
+    assert rel_l1(out["psi"], ref["psi"]) <= tol
+    assert_same_ranking(out["ids"], ref["psi"], tol)
+
+
+def test_fp32_plain_mode_is_close():
+    w = psigen.workload("rmat", seed=3, scale=14)
+    n = w["n"]
+    ref = oracle.solve(n, w["follower"], w["leader"], w["lam"], w["mu"], to_floor=True)
+    out = gpu_solve(n, w["follower"], w["leader"], w["lam"], w["mu"], 1e-6, precision="fp32")
+    assert rel_l1(out["psi"], ref["psi"]) <= 2e-5
+
+
+def _run_pair(n, f, l, lam, mu, precision="fp32_refine"):
+    ref = oracle.solve(n, f, l, lam, mu, to_floor=True, max_iter=20000)
+    out = gpu_solve(n, f, l, lam, mu, 1e-14 if precision == "fp64" else 1e-9, precision=precision,
+                    max_iter=20000, k=min(100, n))
+    return ref, out
+
+
+@pytest.mark.parametrize("lengths", [[1] * 50, [31, 32, 33], [4096, 1, 2048, 2049, 5], [20000], [2047, 2048, 2049]],
+                         ids=["ones", "warpish", "tiles", "one_long_row", "tile_edges"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
+def test_row_length_bins(lengths, precision):
+    """Rows (followers per leader) of chosen lengths, including one row spanning many tiles,
+    rows ending exactly on tile boundaries and ragged tails."""
+    rng = np.random.default_rng(sum(lengths))
+    n = max(lengths) + len(lengths) + 10
+    f, l = [], []
+    for i, L in enumerate(lengths):
+        fol = rng.choice(np.delete(np.arange(n), i), L, replace=False)
+        f += fol.tolist()
+        l += [i] * L
+    # leaders follow someone too, so the iteration mixes
+    for i in range(len(lengths)):
+        f.append(i)
+        l.append((i + 1) % len(lengths) if len(lengths) > 1 else n - 1)
+    lam, mu = rng.uniform(0.1, 1, n), rng.uniform(0.1, 1, n)
+    ref, out = _run_pair(n, np.array(f), np.array(l), lam, mu, precision)
+    tol = 1e-12 if precision == "fp64" else 1e-6
+    assert rel_l1(out["psi"], ref["psi"]) <= tol
+    assert_same_ranking(out["ids"], ref["psi"], tol)
+
+
+def test_single_row_holds_every_edge():
+    n = 300_001
+    f = np.arange(1, n, dtype=np.int32)
+    l = np.zeros(n - 1, np.int32)
+    rng = np.random.default_rng(4)
+    lam, mu = rng.uniform(0.1, 1, n), rng.uniform(0.1, 1, n)
+    c, d = mu / (lam + mu), lam / (lam + mu)
+    want = d / n
+    want[0] = d[0] * (1 + c[1:].sum()) / n  # star closed form
+    for prec, tol in (("fp64", 1e-13), ("fp32_refine", 1e-7)):
+        out = gpu_solve(n, f, l, lam, mu, 1e-12, precision=prec, tol_mode="s_abs", k=10)
+        assert rel_l1(out["psi"], want) <= tol
+        assert abs(out["psi"][0] - want[0]) <= tol * want[0]
+
+
+def test_empty_graph_and_dropped_self_loops():
+    n = 50
+    rng = np.random.default_rng(5)
+    lam, mu = rng.uniform(0.1, 1, n), rng.uniform(0.1, 1, n)
+    for prec, steps in (("fp64", 1), ("fp32", 1), ("fp32_refine", 2)):  # refine: + one FP64 check step
+        out = gpu_solve(n, np.zeros(0, np.int32), np.zeros(0, np.int32), lam, mu, 1e-10, precision=prec, k=10)
+        np.testing.assert_allclose(out["psi"], lam / (lam + mu) / n, rtol=1e-15)
+        assert out["info"]["iters"] == steps
+    loops = np.arange(n, dtype=np.int32)
+    out = gpu_solve(n, loops, loops, lam, mu, 1e-10, self_loops="drop", k=10)
+    np.testing.assert_allclose(out["psi"], lam / (lam + mu) / n, rtol=1e-15)
+    assert out["stats"]["m_unique"] == 0
+
+
+def test_duplicates_are_merged():
+    w = psigen.workload("rmat", seed=6, scale=12)
+    n = w["n"]
+    f, l = w["follower"], w["leader"]
+    # same operator; the internal numbering (by raw degree) and so the summation order may differ
+    a = gpu_solve(n, f, l, w["lam"], w["mu"], 1e-14, precision="fp64")
+    b = gpu_solve(n, np.concatenate([f, f[::3]]), np.concatenate([l, l[::3]]), w["lam"], w["mu"], 1e-14,
+                  precision="fp64")
+    assert rel_l1(a["psi"], b["psi"]) <= 1e-13
+    np.testing.assert_array_equal(a["ids"], b["ids"])
+    assert a["stats"]["m_unique"] == b["stats"]["m_unique"] == oracle.canonical_edges(n, f, l)[0].size
+
+
+def test_errors_are_statuses():
+    from paper_2206_09960_gb300 import PsiError, _binding as B
+
+    n = 10
+    lam, mu = np.ones(n), np.ones(n)
+    cases = [
+        (np.array([0, 11], np.int32), np.array([1, 2], np.int32), lam, mu, {}, B.PSI_ERR_OUT_OF_RANGE_ID),
+        (np.array([0, -1], np.int32), np.array([1, 2], np.int32), lam, mu, {}, B.PSI_ERR_OUT_OF_RANGE_ID),
+        (np.array([0, 3], np.int32), np.array([1, 3], np.int32), lam, mu, {}, B.PSI_ERR_SELF_LOOP),
+        (np.array([0], np.int32), np.array([1], np.int32), np.r_[np.nan, lam[1:]], mu, {}, B.PSI_ERR_BAD_RATE),
+        (np.array([0], np.int32), np.array([1], np.int32), np.r_[-1.0, lam[1:]], mu, {}, B.PSI_ERR_BAD_RATE),
+        (np.array([0], np.int32), np.array([1], np.int32), np.r_[0.0, lam[1:]], np.r_[0.0, mu[1:]], {},
+         B.PSI_ERR_BAD_RATE),
+    ]
+    for f, l, la, m_, kw, want in cases:
+        with pytest.raises(PsiError) as e:
+            gpu_solve(n, f, l, la, m_, 1e-8, **kw)
+        assert e.value.status == want
+    # a solve-less handle reports NOT_SOLVED; bad k is INVALID_ARG
+    from paper_2206_09960_gb300 import Graph
+
+    with Graph(n, np.array([0], np.int32), np.array([1], np.int32), lam, mu) as g:
+        with pytest.raises(PsiError) as e:
+            g.scores()
+        assert e.value.status == B.PSI_ERR_NOT_SOLVED
+        g.solve(1e-8)
+        with pytest.raises(PsiError) as e:
+            g.topk(n + 1)
+        assert e.value.status == B.PSI_ERR_INVALID_ARG
+
+
+def test_host_and_device_inputs_agree_and_results_are_deterministic():
+    w = psigen.workload("chunglu", seed=7, scale=15)
+    args = (w["n"], w["follower"], w["leader"], w["lam"], w["mu"], 1e-8)
+    a = gpu_solve(*args, on_device=True)
+    b = gpu_solve(*args, on_device=False)
+    c = gpu_solve(*args, on_device=True)
+    np.testing.assert_array_equal(a["psi"], b["psi"])
+    np.testing.assert_array_equal(a["psi"], c["psi"])
+    np.testing.assert_array_equal(a["ids"], c["ids"])
+    assert a["info"]["iters"] == c["info"]["iters"]
+
+
+def test_reorder_off_gives_same_scores():
+    w = psigen.workload("rmat", seed=8, scale=13)
+    args = (w["n"], w["follower"], w["leader"], w["lam"], w["mu"], 1e-12)
+    a = gpu_solve(*args, precision="fp64", reorder=True)
+    b = gpu_solve(*args, precision="fp64", reorder=False)
+    assert rel_l1(a["psi"], b["psi"]) <= 1e-13
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refine", "fp32"])
+def test_warm_start_resume(precision):
+    """Resuming from the converged iterate takes very few steps and lands on the same psi."""
+    w = psigen.workload("chunglu", seed=9, scale=14)
+    args = (w["n"], w["follower"], w["leader"], w["lam"], w["mu"])
+    eps = 1e-10 if precision != "fp32" else 1e-6  # FP32 storage cannot reach 1e-10
+    cold = gpu_solve(*args, eps, precision=precision)
+    warm = gpu_solve(*args, eps, precision=precision, init_s=cold["s"])
+    assert warm["info"]["iters"] <= max(3, cold["info"]["iters"] // 4)
+    tol = 1e-9 if precision != "fp32" else 1e-5
+    assert rel_l1(warm["psi"], cold["psi"]) <= tol
+    # a warm start from an arbitrary vector still converges to the same fixed point
+    rnd = np.random.default_rng(1).uniform(0, 3, w["n"])
+    other = gpu_solve(*args, eps, precision=precision, init_s=rnd)
+    assert rel_l1(other["psi"], cold["psi"]) <= (1e-8 if precision != "fp32" else 1e-5)
+
+
+def test_homogeneous_activity_topk_ties_bit_exact():
+    """lambda=.15, mu=.85 everywhere: psi is PageRank; users without followers tie exactly at
+    (1-alpha)/N, so the ranking's tie-break (ascending id) is exercised."""
+    w = psigen.workload("rmat", seed=10, scale=12)
+    n = w["n"]
+    lam, mu = np.full(n, 0.15), np.full(n, 0.85)
+    out = gpu_solve(n, w["follower"], w["leader"], lam, mu, 1e-13, precision="fp64", k=n)
+    order = sorted(range(n), key=lambda i: (-out["psi"][i], i))
+    np.testing.assert_array_equal(out["ids"], np.array(order, np.int32))
+    np.testing.assert_array_equal(out["vals"], out["psi"][order])
+    pr = oracle.pagerank(n, w["follower"], w["leader"], 0.85)
+    assert rel_l1(out["psi"], pr) <= 1e-12
+
+
+def test_profile_reports_kernel_time():
+    w = psigen.workload("rmat", seed=11, scale=15)
+    out = gpu_solve(w["n"], w["follower"], w["leader"], w["lam"], w["mu"], 1e-8, profile=True)
+    info = out["info"]
+    assert info["spmv_timed"] + info["refine_timed"] == info["iters"]
+    assert info["refine_timed"] == info["refinements"] >= 1
+    assert 0 < info["spmv_ms"] + info["refine_ms"] <= info["ms"]
