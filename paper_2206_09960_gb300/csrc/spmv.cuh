@@ -128,7 +128,8 @@ __device__ __forceinline__ void seg_join(int lf, T lv, int& rf, T& rv) {  // R <
 template <typename T, typename Epi>
 __global__ void __launch_bounds__(kSpmvThreads) k_spmv(SpmvArgs a, const T* __restrict__ u, Epi epi) {
   if (a.state->done) return;
-  __shared__ int32_t rp[kSpmvTile + 2];
+  __shared__ int32_t rp[kSpmvTile + 2];  // row_ptr slice of the tile's rows
+  __shared__ T ys[kSpmvTile + 1];        // G(.) of every row that ends in the tile
   __shared__ int wf[kSpmvThreads / 32];
   __shared__ T wv[kSpmvThreads / 32];
   __shared__ double gsh[kSpmvThreads / 32];
@@ -141,10 +142,11 @@ __global__ void __launch_bounds__(kSpmvThreads) k_spmv(SpmvArgs a, const T* __re
 
   for (int32_t tile = blockIdx.x; tile < a.num_tiles; tile += gridDim.x) {
     const int64_t nnz0 = (int64_t)tile * kSpmvTile;
+    const int64_t nnz1 = nnz0 + kSpmvTile < a.m ? nnz0 + kSpmvTile : a.m;
     const int32_t r0 = a.tile_row[tile];
     const int32_t r_hi = a.tile_row[tile + 1];
     const int32_t nr = r_hi - r0 + 1;  // rows touching [nnz0, nnz0 + tile)
-    __syncthreads();                    // rp reuse across tiles
+    __syncthreads();                    // shared buffers are reused across tiles
     for (int i = threadIdx.x; i <= nr; i += kSpmvThreads) rp[i] = a.row_ptr[r0 + i];
     // this thread's nonzeros: p0 .. p0 + kSpmvItems - 1 (col is padded to whole tiles)
     const int64_t p0 = nnz0 + (int64_t)threadIdx.x * kSpmvItems;
@@ -180,7 +182,7 @@ __global__ void __launch_bounds__(kSpmvThreads) k_spmv(SpmvArgs a, const T* __re
           first_row = cur;
           first_val = acc;
         } else {
-          epi.row(r0 + cur, acc, gap, pol_s, pol_k);
+          ys[cur] = acc;               // the row began inside this thread's span
         }
         acc = T(0);
         ++cur;
@@ -211,14 +213,19 @@ __global__ void __launch_bounds__(kSpmvThreads) k_spmv(SpmvArgs a, const T* __re
       vw = gv;
     }
     seg_join(fw, vw, fe, ve);  // exclusive prefix of this thread
-    if (has_end) {
-      T y = ve + first_val;
-      if (!fe && (int64_t)rp[0] < nnz0) carry_head[tile] = y;  // row r0 began in an earlier tile
-      else epi.row(r0 + first_row, y, gap, pol_s, pol_k);
-    }
+    if (has_end) ys[first_row] = ve + first_val;
     if (threadIdx.x == kSpmvThreads - 1) {
       seg_join(fw, vw, f, v);  // inclusive prefix of the whole tile
       carry_tail[tile] = v;
+    }
+    __syncthreads();
+    // epilogues of the rows that end in this tile, one row per thread, coalesced; a first
+    // row that began in an earlier tile leaves its partial for the fix-up kernel
+    const bool head_open = (int64_t)rp[0] < nnz0;
+    for (int i = threadIdx.x; i < nr; i += kSpmvThreads) {
+      if ((int64_t)rp[i + 1] > nnz1) break;  // this row and the next ones end later
+      if (i == 0 && head_open) carry_head[tile] = ys[0];
+      else epi.row(r0 + i, ys[i], gap, pol_s, pol_k);
     }
   }
   // per-CTA gap partial, fixed order
