@@ -175,6 +175,32 @@ void psi_graph_destroy(psi_graph* g);
 const char* psi_status_string(psi_status s);
 const char* psi_last_error(void);
 
+/*
+ * psi_topk_noalloc -- the ranking of psi_topk (psi descending, equal psi by ascending
+ * user id) for a psi vector the caller holds in its own device memory, with no device
+ * allocation: the paper has no counterpart; this entry point exists for callers that
+ * cannot let a library call cudaMalloc, e.g. a serving process that reserves all of its
+ * device memory up front in its own arena, or a host framework whose allocator owns every
+ * device byte (a late cudaMalloc could fail, fragment that budget, or synchronise the
+ * device mid-request).
+ *   psi_in    device pointer: n FP64 values >= 0 (for example written by psi_scores);
+ *             user id = index
+ *   n         1 <= n < 2^31 - 1
+ *   k         1 <= k <= min(n, 4096); larger k is PSI_ERR_INVALID_ARG
+ *   ids_out   device pointer, k int32 user ids; vals_out device pointer, k FP64 (or NULL)
+ *   stream    cudaStream_t to queue the work on (NULL = legacy default stream)
+ * The work is queued and the call returns without waiting; results are complete when the
+ * stream reaches that point.  Host pointers are PSI_ERR_INVALID_ARG.
+ * Working memory is one fixed 50,432-byte device array inside the library (held on every
+ * device that loads it until the process exits).  All calls share it and it keeps the
+ * last call's contents (each call clears what must start at zero), so calls whose work
+ * overlaps on the GPU -- two streams or two host threads -- race and must be serialised by
+ * the caller.  The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ */
+psi_status psi_topk_noalloc(const double* psi_in, int64_t n, int32_t k, int32_t* ids_out, double* vals_out,
+                            void* stream);
+
 /* Number of CUDA kernels this library has launched in this process (instrumentation). */
 int64_t psi_kernel_launches(void);
 

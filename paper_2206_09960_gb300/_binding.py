@@ -28,7 +28,7 @@ SELF_LOOPS = {"reject": PSI_REJECT, "drop": PSI_DROP}
 # every symbol include/psi.h declares
 EXPORTS = ["psi_options_default", "psi_graph_create", "psi_solve", "psi_scores", "psi_topk",
            "psi_get_iterate", "psi_graph_get_stats", "psi_graph_destroy", "psi_status_string",
-           "psi_last_error", "psi_kernel_launches", "psi_version"]
+           "psi_last_error", "psi_kernel_launches", "psi_version", "psi_topk_noalloc"]
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -109,6 +109,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.psi_status_string.restype = ctypes.c_char_p
         lib.psi_last_error.argtypes = []
         lib.psi_last_error.restype = ctypes.c_char_p
+        lib.psi_topk_noalloc.argtypes = [vp, i64, i32, vp, vp, vp]
+        lib.psi_topk_noalloc.restype = i32
         lib.psi_kernel_launches.argtypes = []
         lib.psi_kernel_launches.restype = i64
         lib.psi_version.argtypes = []
@@ -174,6 +176,12 @@ def psi_graph_get_stats(h) -> psi_graph_stats:
 
 def psi_graph_destroy(h):
     load().psi_graph_destroy(h)
+
+
+def psi_topk_noalloc(psi_ptr, n, k, ids_ptr, vals_ptr, stream_ptr=None):
+    """Ranking of a caller-held device psi vector without any device allocation (queued on
+    the stream; the call does not wait)."""
+    _check(load().psi_topk_noalloc(psi_ptr, int(n), int(k), ids_ptr, vals_ptr, stream_ptr))
 
 
 def psi_kernel_launches() -> int:
