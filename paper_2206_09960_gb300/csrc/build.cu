@@ -12,9 +12,11 @@
 //  5. per-user constants c, d, 1/sigma in FP64 and FP32; ||B||_inf = max_j beta_j/sigma_j;
 //  6. the merge-path tile schedule of the sparse product.
 #include <cmath>
+#include <cstring>
 
 #include "primitives.cuh"
 #include "solve.cuh"
+#include "spmv.cuh"
 
 namespace psi {
 
@@ -64,6 +66,8 @@ __global__ void k_node_keys(const uint32_t* __restrict__ in_deg, const uint32_t*
   GRID_STRIDE(i, n) {
     uint32_t di = in_deg[i], dout = out_deg[i];
     uint32_t cls = di > 0 ? (dout > 0 ? 0u : 1u) : (dout > 0 ? 2u : 3u);
+    // rows (X, R) by row length (in-degree, which in these graphs also tracks how often a
+    // user is gathered); U by how often it is gathered (out-degree)
     uint32_t deg = cls <= 1 ? di : (cls == 2 ? dout : 0u);
     uint32_t rank = reorder ? (deg >= 0x7FFFFFu ? 0u : 0x7FFFFFu - deg) : 0u;
     key[i] = (cls << 23) | rank;
@@ -141,53 +145,27 @@ __global__ void k_permute_rates(const double* __restrict__ lam, const double* __
   }
 }
 
-// fptr[x] = first position of follower x in the follower-sorted list
-__global__ void k_lower_bound(const uint32_t* __restrict__ fs, int64_t mu, int64_t n, int32_t* fptr) {
-  GRID_STRIDE(x, n + 1) {
-    int64_t lo = 0, hi = mu;
-    while (lo < hi) {
-      int64_t mid = (lo + hi) >> 1;
-      if ((int64_t)fs[mid] < x) lo = mid + 1; else hi = mid;
-    }
-    fptr[x] = (int32_t)lo;
+// row ids of the follower-grouped CSR: followers X -> [0, nX), U -> [nX, nX + nU)
+__global__ void k_compact_rows(uint32_t* fs, int64_t mu, int32_t nX, int32_t nR) {
+  GRID_STRIDE(e, mu) {
+    uint32_t f = fs[e];
+    fs[e] = f < (uint32_t)nX ? f : f - (uint32_t)nR;
   }
 }
 
-// one warp per follower j: sigma_j, beta_j and sum of mu over L(j) (fixed lane order)
-__global__ void k_leader_sums(const int32_t* __restrict__ fptr, const uint32_t* __restrict__ ls,
-                              const double* __restrict__ lam_i, const double* __restrict__ mu_i, int64_t n,
-                              double* sigma, double* beta, double* musum) {
-  const int lane = threadIdx.x & 31;
-  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t j = wid; j < n; j += nw) {
-    const int32_t b = fptr[j], e = fptr[j + 1];
-    double s = 0.0, sb = 0.0, sm = 0.0;
-    for (int32_t p = b + lane; p < e; p += 32) {
-      uint32_t l = ls[p];
-      double x = lam_i[l], y = mu_i[l];
-      s += x + y;
-      sb += x;
-      sm += y;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      s += __shfl_xor_sync(0xffffffffu, s, o);
-      sb += __shfl_xor_sync(0xffffffffu, sb, o);
-      sm += __shfl_xor_sync(0xffffffffu, sm, o);
-    }
-    if (lane == 0) {
-      sigma[j] = s;
-      beta[j] = sb;
-      musum[j] = sm;
-    }
+// w[k] = lambda_k + mu_k (or lambda_k), with the pad entry w[n] = 0
+__global__ void k_leader_weights(const double* __restrict__ lam_i, const double* __restrict__ mu_i, int64_t n,
+                                 double* w_sum, double* w_lam) {
+  GRID_STRIDE(k, n + 1) {
+    w_sum[k] = k < n ? lam_i[k] + mu_i[k] : 0.0;
+    w_lam[k] = k < n ? lam_i[k] : 0.0;
   }
 }
 
 // c_j = mu_j/(lambda_j+mu_j), d_j = lambda_j/(lambda_j+mu_j), 1/sigma_j (0 without leaders)
 __global__ void k_user_vectors(const double* __restrict__ lam_i, const double* __restrict__ mu_i,
-                               const double* __restrict__ sigma, const double* __restrict__ beta,
-                               const double* __restrict__ musum, int64_t n, double* c64, double* d64,
+                               const double* __restrict__ sigma, const double* __restrict__ beta, int64_t n,
+                               double* c64, double* d64,
                                double* isig64, float* c32, float* mu32, float* isig32,
                                unsigned long long* bnorm_bits, unsigned long long* rho_bits) {
   double bn = 0.0, rho = 0.0;
@@ -202,7 +180,7 @@ __global__ void k_user_vectors(const double* __restrict__ lam_i, const double* _
     mu32[k] = (float)y;
     isig32[k] = (float)is;
     if (sg > 0.0) {
-      double b = beta[k] / sg, r = musum[k] / sg;
+      double b = beta[k] / sg, r = (sg - beta[k]) / sg;
       bn = b > bn ? b : bn;
       rho = r > rho ? r : rho;
     }
@@ -259,12 +237,91 @@ __global__ void k_copy_i32_to_u32(const int32_t* __restrict__ a, int64_t n, uint
   GRID_STRIDE(i, n) b[i] = (uint32_t)a[i];
 }
 
+
 template <typename T>
 T read1(const T* d, cudaStream_t s) {
   T h{};
   PSI_CUDA(cudaMemcpyAsync(&h, d, sizeof(T), cudaMemcpyDeviceToHost, s));
   PSI_CUDA(cudaStreamSynchronize(s));
   return h;
+}
+
+// Merge-path schedule of a CSR with n_rows non-empty rows and m nonzeros.
+struct Schedule {
+  DBuf<int32_t> tile_row;  // [tiles + 1]
+  DBuf<int32_t> fix_tile;  // tiles whose first row began in an earlier tile
+  int32_t tiles = 0;
+  int32_t num_fix = 0;
+};
+
+Schedule make_schedule(const int32_t* row_ptr, int32_t n_rows, int64_t m, Allocator& al, cudaStream_t s) {
+  Schedule sc;
+  sc.tiles = (int32_t)ceil_div(m, kSpmvTile);
+  sc.tile_row.reset(al, (size_t)sc.tiles + 1);
+  if (sc.tiles == 0) {
+    k_set_i32<<<1, 1, 0, s>>>(sc.tile_row.get(), n_rows - 1);
+    PSI_LAUNCHED();
+    sc.fix_tile.reset(al, 1);
+    return sc;
+  }
+  k_tile_rows<<<grid_for(sc.tiles + 1), 256, 0, s>>>(row_ptr, n_rows, sc.tiles, sc.tile_row.get());
+  PSI_LAUNCHED();
+  DBuf<uint32_t> fpos(al, (size_t)sc.tiles);
+  DBuf<uint32_t> ftot(al, 1);
+  k_fix_flags<<<grid_for(sc.tiles), 256, 0, s>>>(row_ptr, sc.tile_row.get(), sc.tiles, m, fpos.get());
+  PSI_LAUNCHED();
+  exclusive_scan_u32(fpos.get(), fpos.get(), sc.tiles, al, s, ftot.get());
+  sc.num_fix = (int32_t)read1(ftot.get(), s);
+  sc.fix_tile.reset(al, (size_t)(sc.num_fix > 0 ? sc.num_fix : 1));
+  if (sc.num_fix > 0) {
+    k_fix_compact<<<grid_for(sc.tiles), 256, 0, s>>>(row_ptr, sc.tile_row.get(), sc.tiles, m, fpos.get(),
+                                                     sc.fix_tile.get());
+    PSI_LAUNCHED();
+  }
+  return sc;
+}
+
+// y = (CSR) w with out[user] = y for every row (one product + fix-up, FP64)
+void run_store_product(const int32_t* row_ptr, const int32_t* col, const Schedule& sc, int32_t n_rows, int64_t m,
+                       const double* w, const EpiStore& epi, Allocator& al, cudaStream_t s) {
+  if (sc.tiles == 0) return;
+  DBuf<DevState> st(al, 1);
+  PSI_CUDA(cudaMemsetAsync(st.get(), 0, sizeof(DevState), s));
+  int per_sm = 0;
+  PSI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmv<double, EpiStore>, kSpmvThreads, 0));
+  int grid = (per_sm > 0 ? per_sm : 1) * (int)num_sms();
+  if (grid > sc.tiles) grid = sc.tiles;
+  DBuf<double> gap_part(al, (size_t)grid), carry_head(al, (size_t)sc.tiles), carry_tail(al, (size_t)sc.tiles);
+  SpmvArgs a{};
+  a.row_ptr = row_ptr;
+  a.col = col;
+  a.tile_row = sc.tile_row.get();
+  a.num_tiles = sc.tiles;
+  a.n_rows = n_rows;
+  a.m = m;
+  a.state = st.get();
+  a.gap_part = gap_part.get();
+  a.carry_head = carry_head.get();
+  a.carry_tail = carry_tail.get();
+  k_spmv<double, EpiStore><<<grid, kSpmvThreads, 0, s>>>(a, w, epi);
+  PSI_LAUNCHED();
+  if (sc.num_fix > 0) {
+    int fgrid = (int)ceil_div(sc.num_fix, kFixWarps);
+    const int cap = (int)num_sms() * 8;
+    if (fgrid > cap) fgrid = cap;
+    DBuf<double> gap_fix(al, (size_t)fgrid);
+    FixArgs f{};
+    f.row_ptr = row_ptr;
+    f.tile_row = sc.tile_row.get();
+    f.fix_tile = sc.fix_tile.get();
+    f.num_fix = sc.num_fix;
+    f.state = st.get();
+    f.gap_fix = gap_fix.get();
+    f.carry_head = carry_head.get();
+    f.carry_tail = carry_tail.get();
+    k_fixup<double, EpiStore><<<fgrid, kFixWarps * 32, 0, s>>>(f, epi);
+    PSI_LAUNCHED();
+  }
 }
 
 }  // namespace
@@ -413,36 +470,67 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
     g.max_followers = read1(mx.get(), s);
   }
 
-  // ---- 4. leader sums per follower
+  // ---- 4. leader sums per follower: sigma = L (lambda + mu), beta = L lambda, as two
+  //         load-balanced products over the follower-grouped CSR (rows X then U)
   DBuf<double> lam_i(al, (size_t)n), mu_i(al, (size_t)n);
   k_permute_rates<<<grid_for(n), 256, 0, s>>>(dlam, dmu, perm32.get(), n, lam_i.get(), mu_i.get());
   PSI_LAUNCHED();
   perm32.release();
   lam_buf.release();
   mu_buf.release();
-  DBuf<double> sigma(al, (size_t)n), beta(al, (size_t)n), musum(al, (size_t)n);
-  {
-    const int64_t mc = mu_count > 0 ? mu_count : 1;
-    DBuf<uint32_t> fk0(al, (size_t)mc), fk1(al, (size_t)mc), lv0(al, (size_t)mc), lv1(al, (size_t)mc);
-    if (mu_count > 0) {
-      k_copy_i32_to_u32<<<grid_for(mu_count), 256, 0, s>>>(g.col.get(), mu_count, fk0.get());
-      PSI_LAUNCHED();
-      k_copy_i32_to_u32<<<grid_for(mu_count), 256, 0, s>>>(li.get(), mu_count, lv0.get());
+  DBuf<double> sigma(al, (size_t)n), beta(al, (size_t)n);
+  PSI_CUDA(cudaMemsetAsync(sigma.get(), 0, sizeof(double) * n, s));
+  PSI_CUDA(cudaMemsetAsync(beta.get(), 0, sizeof(double) * n, s));
+  if (mu_count > 0) {
+    const int64_t mc = mu_count;
+    const int32_t n_f = g.nX + g.nU;  // followers: users with leaders
+    const int32_t tiles_f = (int32_t)ceil_div(mc, kSpmvTile);
+    DBuf<uint32_t> fk0(al, (size_t)mc), fk1(al, (size_t)mc);
+    DBuf<uint32_t> lv0(al, (size_t)tiles_f * kSpmvTile), lv1(al, (size_t)mc);
+    k_copy_i32_to_u32<<<grid_for(mc), 256, 0, s>>>(g.col.get(), mc, fk0.get());
+    PSI_LAUNCHED();
+    k_copy_i32_to_u32<<<grid_for(mc), 256, 0, s>>>(li.get(), mc, lv0.get());
+    PSI_LAUNCHED();
+    li.release();
+    bool alt = radix_sort<uint32_t>(fk0.get(), fk1.get(), lv0.get(), lv1.get(), mc, b, al, s);
+    uint32_t* fs = alt ? fk1.get() : fk0.get();
+    uint32_t* ls = alt ? lv1.get() : lv0.get();
+    DBuf<uint32_t> lpad;
+    if (ls != lv0.get()) {  // the column array of the product needs whole tiles
+      lpad = std::move(lv0);
+      PSI_CUDA(cudaMemcpyAsync(lpad.get(), ls, sizeof(uint32_t) * mc, cudaMemcpyDeviceToDevice, s));
+      ls = lpad.get();
+    } else {
+      lpad = std::move(lv0);
+    }
+    if ((int64_t)tiles_f * kSpmvTile > mc) {
+      k_fill_i32<<<grid_for((int64_t)tiles_f * kSpmvTile - mc), 256, 0, s>>>(reinterpret_cast<int32_t*>(ls), mc,
+                                                                            (int64_t)tiles_f * kSpmvTile, (int32_t)n);
       PSI_LAUNCHED();
     }
+    k_compact_rows<<<grid_for(mc), 256, 0, s>>>(fs, mc, g.nX, g.nR);
+    PSI_LAUNCHED();
+    DBuf<int32_t> rp_f(al, (size_t)n_f + 1);
+    PSI_CUDA(cudaMemsetAsync(err.get() + 6, 0, sizeof(uint32_t), s));
+    k_row_bounds<<<grid_for(mc), 256, 0, s>>>(reinterpret_cast<const int32_t*>(fs), mc, rp_f.get(), err.get() + 6);
+    PSI_LAUNCHED();
+    k_set_i32<<<1, 1, 0, s>>>(rp_f.get() + n_f, (int32_t)mc);
+    PSI_LAUNCHED();
+    const uint32_t frows = read1(err.get() + 6, s);
+    PSI_REQUIRE((int64_t)frows == n_f, PSI_ERR_CUDA, "internal: follower row count mismatch");
+    fk0.release();
+    fk1.release();
+    lv1.release();
+    Schedule sch = make_schedule(rp_f.get(), n_f, mc, al, s);
+    DBuf<double> w_sum(al, (size_t)n + 1), w_lam(al, (size_t)n + 1);
+    k_leader_weights<<<grid_for(n + 1), 256, 0, s>>>(lam_i.get(), mu_i.get(), n, w_sum.get(), w_lam.get());
+    PSI_LAUNCHED();
+    run_store_product(rp_f.get(), reinterpret_cast<const int32_t*>(ls), sch, n_f, mc, w_sum.get(),
+                      EpiStore{sigma.get(), g.nX, g.nR}, al, s);
+    run_store_product(rp_f.get(), reinterpret_cast<const int32_t*>(ls), sch, n_f, mc, w_lam.get(),
+                      EpiStore{beta.get(), g.nX, g.nR}, al, s);
+  } else {
     li.release();
-    bool alt = radix_sort<uint32_t>(fk0.get(), fk1.get(), lv0.get(), lv1.get(), mu_count, b, al, s);
-    const uint32_t* fs = alt ? fk1.get() : fk0.get();
-    const uint32_t* ls = alt ? lv1.get() : lv0.get();
-    DBuf<int32_t> fptr(al, (size_t)n + 1);
-    k_lower_bound<<<grid_for(n + 1), 256, 0, s>>>(fs, mu_count, n, fptr.get());
-    PSI_LAUNCHED();
-    int64_t warps = n;
-    int blocks = (int)((warps * 32 + 255) / 256);
-    int cap = (int)num_sms() * 32;
-    k_leader_sums<<<blocks < cap ? blocks : cap, 256, 0, s>>>(fptr.get(), ls, lam_i.get(), mu_i.get(), n,
-                                                              sigma.get(), beta.get(), musum.get());
-    PSI_LAUNCHED();
   }
 
   // ---- 5. per-user constants
@@ -454,9 +542,9 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
   g.isig32.reset(al, (size_t)n);
   DBuf<unsigned long long> norms(al, 2);
   PSI_CUDA(cudaMemsetAsync(norms.get(), 0, 2 * sizeof(unsigned long long), s));
-  k_user_vectors<<<grid_for(n), 256, 0, s>>>(lam_i.get(), mu_i.get(), sigma.get(), beta.get(), musum.get(), n,
-                                             g.c64.get(), g.d64.get(), g.isig64.get(), g.c32.get(), g.mu32.get(),
-                                             g.isig32.get(), norms.get(), norms.get() + 1);
+  k_user_vectors<<<grid_for(n), 256, 0, s>>>(lam_i.get(), mu_i.get(), sigma.get(), beta.get(), n, g.c64.get(),
+                                             g.d64.get(), g.isig64.get(), g.c32.get(), g.mu32.get(), g.isig32.get(),
+                                             norms.get(), norms.get() + 1);
   PSI_LAUNCHED();
   g.lam64 = std::move(lam_i);
   g.mu64 = std::move(mu_i);
@@ -470,28 +558,12 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
     g.rho_inf = v[1];
   }
 
-  // ---- 6. tile schedule of the sparse product
-  g.tile_row.reset(al, (size_t)g.num_tiles + 1);
-  g.num_fix = 0;
-  if (g.num_tiles > 0) {
-    k_tile_rows<<<grid_for(g.num_tiles + 1), 256, 0, s>>>(g.row_ptr.get(), g.n_rows, g.num_tiles, g.tile_row.get());
-    PSI_LAUNCHED();
-    DBuf<uint32_t> fpos(al, (size_t)g.num_tiles);
-    DBuf<uint32_t> ftot(al, 1);
-    k_fix_flags<<<grid_for(g.num_tiles), 256, 0, s>>>(g.row_ptr.get(), g.tile_row.get(), g.num_tiles, mu_count,
-                                                      fpos.get());
-    PSI_LAUNCHED();
-    exclusive_scan_u32(fpos.get(), fpos.get(), g.num_tiles, al, s, ftot.get());
-    g.num_fix = (int32_t)read1(ftot.get(), s);
-    g.fix_tile.reset(al, (size_t)(g.num_fix > 0 ? g.num_fix : 1));
-    if (g.num_fix > 0) {
-      k_fix_compact<<<grid_for(g.num_tiles), 256, 0, s>>>(g.row_ptr.get(), g.tile_row.get(), g.num_tiles, mu_count,
-                                                          fpos.get(), g.fix_tile.get());
-      PSI_LAUNCHED();
-    }
-  } else {
-    k_set_i32<<<1, 1, 0, s>>>(g.tile_row.get(), g.n_rows - 1);
-    PSI_LAUNCHED();
+  // ---- 6. tile schedule of the Power-psi product
+  {
+    Schedule sch = make_schedule(g.row_ptr.get(), g.n_rows, mu_count, al, s);
+    g.tile_row = std::move(sch.tile_row);
+    g.fix_tile = std::move(sch.fix_tile);
+    g.num_fix = sch.num_fix;
   }
   PSI_CUDA(cudaEventRecord(t1, s));
   PSI_CUDA(cudaStreamSynchronize(s));

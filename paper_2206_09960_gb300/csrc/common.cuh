@@ -151,10 +151,25 @@ __device__ __forceinline__ void st_keep(double* p, double v, uint64_t pol) {
   asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(v), "l"(pol) : "memory");
 }
 
+// 8 column indices (32 bytes) in one 256-bit load, streamed past L1
+__device__ __forceinline__ void ld_stream_v8(const int* p, uint64_t pol, int (&c)[8]) {
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8], %9;"
+               : "=r"(c[0]), "=r"(c[1]), "=r"(c[2]), "=r"(c[3]), "=r"(c[4]), "=r"(c[5]), "=r"(c[6]), "=r"(c[7])
+               : "l"(p), "l"(pol));
+}
+
 // ---------------------------------------------------------------- sizes
+#ifndef PSI_SPMV_ITEMS
+#define PSI_SPMV_ITEMS 8
+#endif
+#ifndef PSI_SPMV_PREFETCH
+#define PSI_SPMV_PREFETCH 0
+#endif
 constexpr int kSpmvThreads = 256;
-constexpr int kSpmvItems = 8;                          // nnz per thread per tile
-constexpr int kSpmvTile = kSpmvThreads * kSpmvItems;   // nnz per tile (multiple of 4)
+constexpr int kSpmvItems = PSI_SPMV_ITEMS;             // nnz per thread per tile (multiple of 8)
+constexpr int kSpmvTile = kSpmvThreads * kSpmvItems;   // nnz per tile
+constexpr bool kSpmvPrefetch = PSI_SPMV_PREFETCH != 0; // gather the next tile while finishing this one
+static_assert(kSpmvItems % 8 == 0, "column loads are 32-byte vectors");
 
 // ---------------------------------------------------------------- device-side loop state
 struct DevState {

@@ -71,9 +71,9 @@ __global__ void k_scan_down(const uint32_t* in, uint32_t* out, int64_t n,
 // ---------------------------------------------------------------- radix sort
 constexpr int kRsThreads = 256;
 constexpr int kRsWarps = kRsThreads / 32;
-constexpr int kRsItems = 16;
-constexpr int kRsTile = kRsThreads * kRsItems;  // 4096 keys per tile
-constexpr int kRsPerWarp = 32 * kRsItems;       // 512 consecutive keys per warp
+constexpr int kRsItems = 8;
+constexpr int kRsTile = kRsThreads * kRsItems;  // 2048 keys per tile
+constexpr int kRsPerWarp = 32 * kRsItems;       // 256 consecutive keys per warp
 
 template <typename K>
 __global__ void __launch_bounds__(kRsThreads) k_radix_histo(const K* __restrict__ keys, int64_t n, int shift,
@@ -91,23 +91,31 @@ __global__ void __launch_bounds__(kRsThreads) k_radix_histo(const K* __restrict_
   counts[(int64_t)threadIdx.x * num_tiles + blockIdx.x] = h[threadIdx.x];
 }
 
+// Stable scatter of one tile: items are ranked per warp (warp-major, then round, then
+// lane: the input order), placed in shared memory in digit order, and written out so that
+// each digit's run of the tile lands contiguously (coalesced) at its global offset.
 template <typename K, bool VALS>
 __global__ void __launch_bounds__(kRsThreads) k_radix_scatter(const K* __restrict__ keys, const uint32_t* __restrict__ vals,
                                                              K* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
                                                              int64_t n, int shift, int64_t num_tiles,
                                                              const uint32_t* __restrict__ offsets) {
+  extern __shared__ __align__(16) unsigned char rs_dyn[];
+  K* sk = reinterpret_cast<K*>(rs_dyn);
+  uint32_t* sv = reinterpret_cast<uint32_t*>(rs_dyn + (size_t)kRsTile * sizeof(K));
   __shared__ uint32_t wh[kRsWarps][257];
   __shared__ uint32_t tile_base[256];
+  __shared__ uint32_t dstart[256];
+  __shared__ uint32_t wsum[kRsWarps];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < kRsWarps * 257; i += kRsThreads) (&wh[0][0])[i] = 0;
   tile_base[threadIdx.x] = offsets[(int64_t)threadIdx.x * num_tiles + blockIdx.x];
   __syncthreads();
-  const int64_t wbase = (int64_t)blockIdx.x * kRsTile + (int64_t)warp * kRsPerWarp;
+  const int64_t tile0 = (int64_t)blockIdx.x * kRsTile;
+  const int64_t wbase = tile0 + (int64_t)warp * kRsPerWarp;
   const uint32_t lt_mask = (1u << lane) - 1u;
   K k[kRsItems];
   uint32_t v[kRsItems];
-  uint32_t pos[kRsItems];
-  int dig[kRsItems];
+  uint32_t dp[kRsItems];  // digit (9 bits, 256 = no item) << 16 | rank inside the warp's digit run
 #pragma unroll
   for (int r = 0; r < kRsItems; ++r) {
     int64_t idx = wbase + (int64_t)r * 32 + lane;
@@ -115,35 +123,69 @@ __global__ void __launch_bounds__(kRsThreads) k_radix_scatter(const K* __restric
     k[r] = ok ? keys[idx] : K(0);
     if (VALS) v[r] = ok ? vals[idx] : 0u;
     int d = ok ? (int)((uint32_t)(k[r] >> shift) & 0xFFu) : 256;
-    dig[r] = d;
     uint32_t peers = __match_any_sync(0xffffffffu, d);
     uint32_t before = wh[warp][d];
     __syncwarp();
     if ((peers & lt_mask) == 0) wh[warp][d] = before + __popc(peers);
     __syncwarp();
-    pos[r] = before + __popc(peers & lt_mask);
+    dp[r] = ((uint32_t)d << 16) | (before + __popc(peers & lt_mask));
   }
   __syncthreads();
-  {  // exclusive prefix of the per-warp counts, warp order, for digit = thread
+  // per digit (= thread): exclusive prefix over warps, then exclusive scan over digits
+  uint32_t total = 0;
+  {
     const int d = threadIdx.x;
-    uint32_t run = 0;
 #pragma unroll
     for (int w = 0; w < kRsWarps; ++w) {
       uint32_t t = wh[w][d];
-      wh[w][d] = run;
-      run += t;
+      wh[w][d] = total;
+      total += t;
     }
   }
+  uint32_t x = total;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[warp] = x;
+  __syncthreads();
+  uint32_t wb = 0;
+  for (int w = 0; w < warp; ++w) wb += wsum[w];
+  dstart[threadIdx.x] = wb + x - total;
   __syncthreads();
 #pragma unroll
   for (int r = 0; r < kRsItems; ++r) {
-    int d = dig[r];
+    const int d = (int)(dp[r] >> 16);
     if (d < 256) {
-      uint32_t o = tile_base[d] + wh[warp][d] + pos[r];
-      keys_out[o] = k[r];
-      if (VALS) vals_out[o] = v[r];
+      const uint32_t lp = dstart[d] + wh[warp][d] + (dp[r] & 0xFFFFu);
+      sk[lp] = k[r];
+      if (VALS) sv[lp] = v[r];
     }
   }
+  __syncthreads();
+  const int64_t rem = n - tile0;
+  const int valid = rem < kRsTile ? (int)rem : kRsTile;
+  for (int i = threadIdx.x; i < valid; i += kRsThreads) {
+    const K key = sk[i];
+    const int d = (int)((uint32_t)(key >> shift) & 0xFFu);
+    const uint32_t o = tile_base[d] + (uint32_t)i - dstart[d];
+    keys_out[o] = key;
+    if (VALS) vals_out[o] = sv[i];
+  }
+}
+
+template <typename K, bool VALS>
+void launch_scatter(const K* src, const uint32_t* vsrc, K* dst, uint32_t* vdst, int64_t n, int shift, int64_t tiles,
+                    const uint32_t* offsets, cudaStream_t s) {
+  const size_t dyn = (size_t)kRsTile * (sizeof(K) + (VALS ? sizeof(uint32_t) : 0));
+  static bool configured = false;
+  if (!configured) {
+    PSI_CUDA(cudaFuncSetAttribute(k_radix_scatter<K, VALS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    configured = true;
+  }
+  k_radix_scatter<K, VALS><<<(unsigned)tiles, kRsThreads, dyn, s>>>(src, vsrc, dst, vdst, n, shift, tiles, offsets);
+  PSI_LAUNCHED();
 }
 
 // ---------------------------------------------------------------- FP64 sum
@@ -201,12 +243,8 @@ bool radix_sort(K* keys, K* keys_alt, uint32_t* vals, uint32_t* vals_alt, int64_
     k_radix_histo<K><<<(unsigned)tiles, kRsThreads, 0, s>>>(src, n, shift, tiles, counts.get());
     PSI_LAUNCHED();
     exclusive_scan_u32(counts.get(), counts.get(), tiles * 256, al, s, nullptr);
-    if (vals)
-      k_radix_scatter<K, true><<<(unsigned)tiles, kRsThreads, 0, s>>>(src, vsrc, dst, vdst, n, shift, tiles, counts.get());
-    else
-      k_radix_scatter<K, false><<<(unsigned)tiles, kRsThreads, 0, s>>>(src, nullptr, dst, nullptr, n, shift, tiles,
-                                                                      counts.get());
-    PSI_LAUNCHED();
+    if (vals) launch_scatter<K, true>(src, vsrc, dst, vdst, n, shift, tiles, counts.get(), s);
+    else launch_scatter<K, false>(src, nullptr, dst, nullptr, n, shift, tiles, counts.get(), s);
     std::swap(src, dst);
     std::swap(vsrc, vdst);
     flipped = !flipped;

@@ -10,39 +10,6 @@ namespace psi {
 
 namespace {
 
-constexpr int kFixWarps = 8;
-
-// Closes rows that began in an earlier tile: y = sum of the tile carries in tile order
-// plus the partial of the tile where the row ends.
-template <typename T, typename Epi>
-__global__ void __launch_bounds__(kFixWarps * 32) k_fixup(FixArgs a, Epi epi) {
-  if (a.state->done) return;
-  __shared__ double gsh[kFixWarps];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint64_t pol_s = policy_evict_first();
-  const uint64_t pol_k = policy_evict_last();
-  const T* ch = static_cast<const T*>(a.carry_head);
-  const T* ct = static_cast<const T*>(a.carry_tail);
-  double gap = 0.0;
-  for (int32_t q = blockIdx.x * kFixWarps + warp; q < a.num_fix; q += gridDim.x * kFixWarps) {
-    const int32_t k = a.fix_tile[q];
-    const int32_t r0 = a.tile_row[k];
-    const int32_t ks = a.row_ptr[r0] / kSpmvTile;  // tile where row r0 begins
-    T acc = T(0);
-    for (int32_t kk = ks + lane; kk < k; kk += 32) acc += ct[kk];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) epi.row(r0, acc + ch[k], gap, pol_s, pol_k);
-  }
-  if (lane == 0) gsh[warp] = gap;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < kFixWarps; ++w) t += gsh[w];
-    a.gap_fix[blockIdx.x] = t;
-  }
-}
-
 // Sums the step's gap partials in a fixed order and applies the stop test of
 // Algorithm 2: stop when scale * ||s_t - s_{t-1}||_1 <= eps (Eqs. 15-16) or at max_iter.
 __global__ void __launch_bounds__(1024) k_finalize(DevState* st, const double* __restrict__ gp, int ngp,

@@ -51,7 +51,7 @@ struct EpiSeries {
   int32_t nX;
   __device__ __forceinline__ void row(int32_t r, float y, double& gap, uint64_t pol_s, uint64_t pol_k) const {
     float t = ld_stream(mu + r, pol_s) * y;
-    s64[r] += (double)t;
+    s64[r] = ld_stream(s64 + r, pol_s) + (double)t;
     gap += fabs((double)t);
     if (r < nX) st_keep(v_new + r, t * ld_stream(isig + r, pol_s), pol_k);
   }
@@ -89,6 +89,17 @@ struct EpiFinal {
   double n;
   __device__ __forceinline__ void row(int32_t r, T y, double& gap, uint64_t pol_s, uint64_t) const {
     psi[r] = (ld_stream(lam + r, pol_s) * (double)y + ld_stream(d + r, pol_s)) / n;
+  }
+};
+
+// Plain product output: out[user] = y, with row r standing for user r < nX ? r : r + skip
+// (used to form per-user sums over a CSR whose rows skip a block of users).
+struct EpiStore {
+  double* out;
+  int32_t nX;
+  int32_t skip;
+  __device__ __forceinline__ void row(int32_t r, double y, double&, uint64_t, uint64_t) const {
+    out[r < nX ? r : r + skip] = y;
   }
 };
 
@@ -140,6 +151,21 @@ __global__ void __launch_bounds__(kSpmvThreads) k_spmv(SpmvArgs a, const T* __re
   T* carry_tail = static_cast<T*>(a.carry_tail);
   double gap = 0.0;
 
+  // column indices and gathered values of one tile: this thread's kSpmvItems nonzeros
+  // (col is padded to whole tiles, pad entries point at u[n] = 0)
+  auto gather_tile = [&](int32_t t, T (&x)[kSpmvItems]) {
+    const int* cp = a.col + (int64_t)t * kSpmvTile + (int64_t)threadIdx.x * kSpmvItems;
+#pragma unroll
+    for (int q = 0; q < kSpmvItems / 8; ++q) {
+      int c[8];
+      ld_stream_v8(cp + 8 * q, pol_s, c);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) x[8 * q + j] = ld_gather(u + c[j], pol_k);
+    }
+  };
+  T xn[kSpmvItems];
+  if ((int32_t)blockIdx.x < a.num_tiles) gather_tile(blockIdx.x, xn);
+
   for (int32_t tile = blockIdx.x; tile < a.num_tiles; tile += gridDim.x) {
     const int64_t nnz0 = (int64_t)tile * kSpmvTile;
     const int64_t nnz1 = nnz0 + kSpmvTile < a.m ? nnz0 + kSpmvTile : a.m;
@@ -147,20 +173,16 @@ __global__ void __launch_bounds__(kSpmvThreads) k_spmv(SpmvArgs a, const T* __re
     const int32_t r_hi = a.tile_row[tile + 1];
     const int32_t nr = r_hi - r0 + 1;  // rows touching [nnz0, nnz0 + tile)
     __syncthreads();                    // shared buffers are reused across tiles
-    for (int i = threadIdx.x; i <= nr; i += kSpmvThreads) rp[i] = a.row_ptr[r0 + i];
-    // this thread's nonzeros: p0 .. p0 + kSpmvItems - 1 (col is padded to whole tiles)
+    for (int i = threadIdx.x; i <= nr; i += kSpmvThreads) rp[i] = ld_stream(a.row_ptr + r0 + i, pol_s);
     const int64_t p0 = nnz0 + (int64_t)threadIdx.x * kSpmvItems;
     T x[kSpmvItems];
-    {
-      const int4* cp = reinterpret_cast<const int4*>(a.col + p0);
 #pragma unroll
-      for (int q = 0; q < kSpmvItems / 4; ++q) {
-        int4 c4 = ld_stream_v4(cp + q, pol_s);
-        x[4 * q + 0] = ld_gather(u + c4.x, pol_k);
-        x[4 * q + 1] = ld_gather(u + c4.y, pol_k);
-        x[4 * q + 2] = ld_gather(u + c4.z, pol_k);
-        x[4 * q + 3] = ld_gather(u + c4.w, pol_k);
-      }
+    for (int i = 0; i < kSpmvItems; ++i) x[i] = xn[i];
+    const int32_t next = tile + gridDim.x;
+    if (kSpmvPrefetch) {
+      if (next < a.num_tiles) gather_tile(next, xn);
+    } else {
+      (void)next;
     }
     __syncthreads();
     // first row whose end lies beyond p0
@@ -227,6 +249,7 @@ __global__ void __launch_bounds__(kSpmvThreads) k_spmv(SpmvArgs a, const T* __re
       if (i == 0 && head_open) carry_head[tile] = ys[0];
       else epi.row(r0 + i, ys[i], gap, pol_s, pol_k);
     }
+    if (!kSpmvPrefetch && next < a.num_tiles) gather_tile(next, xn);
   }
   // per-CTA gap partial, fixed order
 #pragma unroll
@@ -237,6 +260,39 @@ __global__ void __launch_bounds__(kSpmvThreads) k_spmv(SpmvArgs a, const T* __re
     double t = 0.0;
     for (int w = 0; w < kSpmvThreads / 32; ++w) t += gsh[w];
     a.gap_part[blockIdx.x] = t;
+  }
+}
+
+constexpr int kFixWarps = 8;  // warps per fix-up block
+
+// Closes rows that began in an earlier tile: y = sum of the tile carries in tile order
+// plus the partial of the tile where the row ends.
+template <typename T, typename Epi>
+__global__ void __launch_bounds__(kFixWarps * 32) k_fixup(FixArgs a, Epi epi) {
+  if (a.state->done) return;
+  __shared__ double gsh[kFixWarps];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint64_t pol_s = policy_evict_first();
+  const uint64_t pol_k = policy_evict_last();
+  const T* ch = static_cast<const T*>(a.carry_head);
+  const T* ct = static_cast<const T*>(a.carry_tail);
+  double gap = 0.0;
+  for (int32_t q = blockIdx.x * kFixWarps + warp; q < a.num_fix; q += gridDim.x * kFixWarps) {
+    const int32_t k = a.fix_tile[q];
+    const int32_t r0 = a.tile_row[k];
+    const int32_t ks = a.row_ptr[r0] / kSpmvTile;  // tile where row r0 begins
+    T acc = T(0);
+    for (int32_t kk = ks + lane; kk < k; kk += 32) acc += ct[kk];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) epi.row(r0, acc + ch[k], gap, pol_s, pol_k);
+  }
+  if (lane == 0) gsh[warp] = gap;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kFixWarps; ++w) t += gsh[w];
+    a.gap_fix[blockIdx.x] = t;
   }
 }
 
