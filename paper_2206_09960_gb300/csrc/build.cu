@@ -82,12 +82,20 @@ __global__ void k_invert(const uint32_t* __restrict__ perm, int64_t n, int32_t* 
   GRID_STRIDE(k, n) inv[perm[k]] = (int32_t)k;
 }
 
-// renumbered key (leader << b) | follower; a dropped self-loop becomes the sentinel
+// key = (leader row << bf) | follower's gathered index (X: its id, U: id - nR); a dropped
+// self-loop becomes the sentinel
 __global__ void k_edge_keys(const int32_t* __restrict__ f, const int32_t* __restrict__ l, int64_t m,
-                            const int32_t* __restrict__ inv, int b, uint64_t sentinel, uint64_t* key) {
+                            const int32_t* __restrict__ inv, int32_t nX, int32_t nR, int bf, uint64_t sentinel,
+                            uint64_t* key) {
   GRID_STRIDE(e, m) {
     int32_t a = f[e], c = l[e];
-    key[e] = (a == c) ? sentinel : (((uint64_t)(uint32_t)inv[c] << b) | (uint64_t)(uint32_t)inv[a]);
+    if (a == c) {
+      key[e] = sentinel;
+    } else {
+      const uint32_t fi = (uint32_t)inv[a];
+      const uint32_t gi = fi < (uint32_t)nX ? fi : fi - (uint32_t)nR;
+      key[e] = ((uint64_t)(uint32_t)inv[c] << bf) | (uint64_t)gi;
+    }
   }
 }
 
@@ -142,14 +150,6 @@ __global__ void k_permute_rates(const double* __restrict__ lam, const double* __
     uint32_t o = perm[k];
     lam_i[k] = lam[o];
     mu_i[k] = mu[o];
-  }
-}
-
-// row ids of the follower-grouped CSR: followers X -> [0, nX), U -> [nX, nX + nU)
-__global__ void k_compact_rows(uint32_t* fs, int64_t mu, int32_t nX, int32_t nR) {
-  GRID_STRIDE(e, mu) {
-    uint32_t f = fs[e];
-    fs[e] = f < (uint32_t)nX ? f : f - (uint32_t)nR;
   }
 }
 
@@ -408,9 +408,14 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
   g.perm.reset(al, (size_t)n);
   PSI_CUDA(cudaMemcpyAsync(g.perm.get(), perm32.get(), sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
 
-  // ---- 3. sort, merge duplicates, transposed CSR
-  const int b = bits_for((uint64_t)n);  // 2^b > n
-  const uint64_t sentinel = ((uint64_t)1 << (2 * b)) - 1;
+  // ---- 3. sort, merge duplicates, transposed CSR.  Keys hold the leader row and the
+  //         follower's gathered index: bits_for(n_rows - 1) + bits_for(nu) bits (the low
+  //         field never reaches all ones, so the all-ones sentinel sorts last)
+  const int64_t nu = (int64_t)g.nX + g.nU;
+  const int bf = bits_for((uint64_t)nu);
+  const int bl = g.n_rows > 1 ? bits_for((uint64_t)(g.n_rows - 1)) : 1;
+  const int b = bf;  // width of the follower field (the follower sort below)
+  const uint64_t sentinel = ((uint64_t)1 << (bl + bf)) - 1;
   int64_t mu_count = 0;
   DBuf<int32_t> li;
   {
@@ -419,13 +424,13 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
     PSI_LAUNCHED();
     DBuf<uint64_t> k0(al, (size_t)m), k1(al, (size_t)m);
     if (m > 0) {
-      k_edge_keys<<<grid_for(m), 256, 0, s>>>(df, dl, m, inv.get(), b, sentinel, k0.get());
+      k_edge_keys<<<grid_for(m), 256, 0, s>>>(df, dl, m, inv.get(), g.nX, g.nR, bf, sentinel, k0.get());
       PSI_LAUNCHED();
     }
     inv.release();
     fbuf.release();
     lbuf.release();
-    bool alt = radix_sort<uint64_t>(k0.get(), k1.get(), nullptr, nullptr, m, 2 * b, al, s);
+    bool alt = radix_sort<uint64_t>(k0.get(), k1.get(), nullptr, nullptr, m, bl + bf, al, s);
     const uint64_t* keys = alt ? k1.get() : k0.get();
     DBuf<uint32_t> pos(al, (size_t)m);
     DBuf<uint32_t> total(al, 1);
@@ -443,11 +448,11 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
     g.col.reset(al, (size_t)(padded > 0 ? padded : 4));
     li.reset(al, (size_t)(mu_count > 0 ? mu_count : 1));
     if (mu_count > 0) {
-      k_unique_compact<<<grid_for(m), 256, 0, s>>>(keys, m, sentinel, pos.get(), b, li.get(), g.col.get());
+      k_unique_compact<<<grid_for(m), 256, 0, s>>>(keys, m, sentinel, pos.get(), bf, li.get(), g.col.get());
       PSI_LAUNCHED();
     }
     if (padded > mu_count) {
-      k_fill_i32<<<grid_for(padded - mu_count), 256, 0, s>>>(g.col.get(), mu_count, padded, (int32_t)n);
+      k_fill_i32<<<grid_for(padded - mu_count), 256, 0, s>>>(g.col.get(), mu_count, padded, (int32_t)nu);
       PSI_LAUNCHED();
     }
   }
@@ -508,8 +513,6 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
                                                                             (int64_t)tiles_f * kSpmvTile, (int32_t)n);
       PSI_LAUNCHED();
     }
-    k_compact_rows<<<grid_for(mc), 256, 0, s>>>(fs, mc, g.nX, g.nR);
-    PSI_LAUNCHED();
     DBuf<int32_t> rp_f(al, (size_t)n_f + 1);
     PSI_CUDA(cudaMemsetAsync(err.get() + 6, 0, sizeof(uint32_t), s));
     k_row_bounds<<<grid_for(mc), 256, 0, s>>>(reinterpret_cast<const int32_t*>(fs), mc, rp_f.get(), err.get() + 6);

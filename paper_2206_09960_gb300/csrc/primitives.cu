@@ -78,17 +78,21 @@ constexpr int kRsPerWarp = 32 * kRsItems;       // 256 consecutive keys per warp
 template <typename K>
 __global__ void __launch_bounds__(kRsThreads) k_radix_histo(const K* __restrict__ keys, int64_t n, int shift,
                                                            int64_t num_tiles, uint32_t* __restrict__ counts) {
-  __shared__ uint32_t h[256];
-  h[threadIdx.x] = 0;
+  __shared__ uint32_t h[kRsWarps][256];  // one sub-histogram per warp: contention stays inside a warp
+  for (int i = threadIdx.x; i < kRsWarps * 256; i += kRsThreads) (&h[0][0])[i] = 0;
   __syncthreads();
+  const int warp = threadIdx.x >> 5;
   const int64_t base = (int64_t)blockIdx.x * kRsTile;
 #pragma unroll 4
   for (int i = 0; i < kRsItems; ++i) {
     int64_t idx = base + (int64_t)i * kRsThreads + threadIdx.x;
-    if (idx < n) atomicAdd(&h[(uint32_t)(keys[idx] >> shift) & 0xFFu], 1u);
+    if (idx < n) atomicAdd(&h[warp][(uint32_t)(keys[idx] >> shift) & 0xFFu], 1u);
   }
   __syncthreads();
-  counts[(int64_t)threadIdx.x * num_tiles + blockIdx.x] = h[threadIdx.x];
+  uint32_t t = 0;
+#pragma unroll
+  for (int w = 0; w < kRsWarps; ++w) t += h[w][threadIdx.x];
+  counts[(int64_t)threadIdx.x * num_tiles + blockIdx.x] = t;
 }
 
 // Stable scatter of one tile: items are ranked per warp (warp-major, then round, then

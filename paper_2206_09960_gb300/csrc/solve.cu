@@ -59,11 +59,15 @@ __global__ void k_convert(D* dst, const S* src, int64_t n) {
     dst[i] = (D)src[i];
 }
 
-// dst[i] = s[i] * isig[i] on [lo, hi); dst[n] = 0 pad
+// Gathered vectors live in their own index space: users with leaders only, X at [0, nX)
+// and U at [nX, nX + nU) (user nX + nR + j at nX + j), plus a zero pad entry at nX + nU.
+// dst[i] = s[user(i)] * isig[user(i)] for i in [lo, hi).
 template <typename T, typename S>
-__global__ void k_scale(T* dst, const S* s, const T* isig, int64_t lo, int64_t hi) {
-  for (int64_t i = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < hi; i += (int64_t)gridDim.x * blockDim.x)
-    dst[i] = (T)s[i] * isig[i];
+__global__ void k_to_u(T* dst, const S* s, const T* isig, int32_t nX, int32_t nR, int64_t lo, int64_t hi) {
+  for (int64_t i = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < hi; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t user = i < nX ? i : i + nR;
+    dst[i] = (T)s[user] * isig[user];
+  }
 }
 
 // out[k] = in[perm[k]] (gather into internal order)
@@ -249,11 +253,12 @@ void ensure_iteration_buffers(Graph& g) {
   if (g.allocated_iter) return;
   Allocator& al = g.al;
   const size_t n = (size_t)g.n;
+  const size_t nu = (size_t)g.nX + (size_t)g.nU;  // gathered entries; pad at nu
   const int prec = g.opt.precision;
   if (prec == PSI_FP32_REFINE || prec == PSI_FP64) {
     g.s64.reset(al, n);
-    g.u64a.reset(al, n + 1);
-    g.u64b.reset(al, n + 1);
+    g.u64a.reset(al, nu + 1);
+    g.u64b.reset(al, nu + 1);
   }
   if (prec == PSI_FP64) g.s64b.reset(al, n);
   if (prec == PSI_FP32) {
@@ -261,10 +266,10 @@ void ensure_iteration_buffers(Graph& g) {
     g.s32b.reset(al, n);
   }
   if (prec == PSI_FP32 || prec == PSI_FP32_REFINE) {
-    g.u32a.reset(al, n + 1);
-    g.u32b.reset(al, n + 1);
+    g.u32a.reset(al, nu + 1);
+    g.u32b.reset(al, nu + 1);
   }
-  if (prec == PSI_FP32_REFINE) g.u32c.reset(al, n + 1);
+  if (prec == PSI_FP32_REFINE) g.u32c.reset(al, nu + 1);
   g.psi64.reset(al, n);
   const size_t nt = (size_t)(g.num_tiles > 0 ? g.num_tiles : 1);
   g.carry_head.reset(al, nt);
@@ -317,8 +322,8 @@ psi_status solve(Graph& g, double eps, int32_t max_iter, const double* init_s, p
   g.solved = false;
   const int64_t n = g.n;
   const int32_t nX = g.nX;
-  const int64_t u_lo = (int64_t)g.nX + g.nR;      // U begins here
-  const int64_t g_hi = u_lo + g.nU;               // X and U (the gathered users) end here
+  const int32_t nR = g.nR;
+  const int64_t nu = (int64_t)g.nX + g.nU;        // gathered entries (X, then U); pad at nu
   const int prec = g.opt.precision;
   const int batch = g.m_unique > ((int64_t)1 << 24) ? 2 : 8;
   const int eg = elementwise_grid(n);
@@ -347,16 +352,16 @@ psi_status solve(Graph& g, double eps, int32_t max_iter, const double* init_s, p
     double* sb[2] = {g.s64.get(), g.s64b.get()};
     double* ub[2] = {g.u64a.get(), g.u64b.get()};
     for (int b = 0; b < 2; ++b) {  // X from s_0 = c, U = c/sigma (s_t = c there for t >= 1)
-      fill<double>(ub[b], n + 1, 0.0, s);
-      k_scale<double, double><<<eg, 256, 0, s>>>(ub[b], g.c64.get(), g.isig64.get(), 0, g_hi);
+      fill<double>(ub[b], nu + 1, 0.0, s);
+      k_to_u<double, double><<<eg, 256, 0, s>>>(ub[b], g.c64.get(), g.isig64.get(), nX, nR, 0, nu);
       PSI_LAUNCHED();
     }
     const double* u_first = ub[0];
     if (init_s) {
       load_init(g, s, init_s, sb[0]);
-      u0_64.reset(g.al, (size_t)n + 1);
-      fill<double>(u0_64.get(), n + 1, 0.0, s);
-      k_scale<double, double><<<eg, 256, 0, s>>>(u0_64.get(), sb[0], g.isig64.get(), 0, g_hi);
+      u0_64.reset(g.al, (size_t)nu + 1);
+      fill<double>(u0_64.get(), nu + 1, 0.0, s);
+      k_to_u<double, double><<<eg, 256, 0, s>>>(u0_64.get(), sb[0], g.isig64.get(), nX, nR, 0, nu);
       PSI_LAUNCHED();
       if (iterate) nonrow_start(g, s, sb[0]);
       u_first = u0_64.get();
@@ -379,20 +384,20 @@ psi_status solve(Graph& g, double eps, int32_t max_iter, const double* init_s, p
     float* sb[2] = {g.s32a.get(), g.s32b.get()};
     float* ub[2] = {g.u32a.get(), g.u32b.get()};
     for (int b = 0; b < 2; ++b) {
-      fill<float>(ub[b], n + 1, 0.0f, s);
-      k_scale<float, float><<<eg, 256, 0, s>>>(ub[b], g.c32.get(), g.isig32.get(), 0, g_hi);
+      fill<float>(ub[b], nu + 1, 0.0f, s);
+      k_to_u<float, float><<<eg, 256, 0, s>>>(ub[b], g.c32.get(), g.isig32.get(), nX, nR, 0, nu);
       PSI_LAUNCHED();
     }
     const float* u_first = ub[0];
     if (init_s) {
       DBuf<double> s0(g.al, (size_t)n);
       load_init(g, s, init_s, s0.get());
-      DBuf<double> u0(g.al, (size_t)n + 1);
-      fill<double>(u0.get(), n + 1, 0.0, s);
-      k_scale<double, double><<<eg, 256, 0, s>>>(u0.get(), s0.get(), g.isig64.get(), 0, g_hi);
+      DBuf<double> u0(g.al, (size_t)nu + 1);
+      fill<double>(u0.get(), nu + 1, 0.0, s);
+      k_to_u<double, double><<<eg, 256, 0, s>>>(u0.get(), s0.get(), g.isig64.get(), nX, nR, 0, nu);
       PSI_LAUNCHED();
-      u0_32.reset(g.al, (size_t)n + 1);
-      k_convert<float, double><<<eg, 256, 0, s>>>(u0_32.get(), u0.get(), n + 1);
+      u0_32.reset(g.al, (size_t)nu + 1);
+      k_convert<float, double><<<eg, 256, 0, s>>>(u0_32.get(), u0.get(), nu + 1);
       PSI_LAUNCHED();
       if (iterate) nonrow_start(g, s, s0.get());
       k_convert<float, double><<<eg, 256, 0, s>>>(sb[0], s0.get(), n);
@@ -420,21 +425,21 @@ psi_status solve(Graph& g, double eps, int32_t max_iter, const double* init_s, p
     float* v0 = g.u32c.get();
     float* vb[2] = {g.u32a.get(), g.u32b.get()};
     for (int b = 0; b < 2; ++b) {
-      fill<double>(ub[b], n + 1, 0.0, s);  // U = c/sigma in both FP64 gathered buffers
-      k_scale<double, double><<<eg, 256, 0, s>>>(ub[b], g.c64.get(), g.isig64.get(), u_lo, g_hi);
+      fill<double>(ub[b], nu + 1, 0.0, s);  // U = c/sigma in both FP64 gathered buffers
+      k_to_u<double, double><<<eg, 256, 0, s>>>(ub[b], g.c64.get(), g.isig64.get(), nX, nR, nX, nu);
       PSI_LAUNCHED();
-      fill<float>(vb[b], n + 1, 0.0f, s);  // series terms of U users vanish after the first
+      fill<float>(vb[b], nu + 1, 0.0f, s);  // series terms of U users vanish after the first
     }
-    fill<float>(v0, n + 1, 0.0f, s);
+    fill<float>(v0, nu + 1, 0.0f, s);
     int cur_u = 0;            // FP64 buffer that will hold u of the current s64
     bool u_current = false;   // whether it does now
     const double* u_resid_in = nullptr;
     bool resid_first = false;
     if (init_s) {
       load_init(g, s, init_s, s64);
-      u0_64.reset(g.al, (size_t)n + 1);
-      fill<double>(u0_64.get(), n + 1, 0.0, s);
-      k_scale<double, double><<<eg, 256, 0, s>>>(u0_64.get(), s64, g.isig64.get(), 0, g_hi);
+      u0_64.reset(g.al, (size_t)nu + 1);
+      fill<double>(u0_64.get(), nu + 1, 0.0, s);
+      k_to_u<double, double><<<eg, 256, 0, s>>>(u0_64.get(), s64, g.isig64.get(), nX, nR, 0, nu);
       PSI_LAUNCHED();
       if (iterate) nonrow_start(g, s, s64);
       u_resid_in = u0_64.get();  // the first step is an FP64 step from s_0
@@ -442,7 +447,7 @@ psi_status solve(Graph& g, double eps, int32_t max_iter, const double* init_s, p
     } else {
       PSI_CUDA(cudaMemcpyAsync(s64, g.c64.get(), sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
       // the first series term is c itself: v0 = c/sigma on X and U
-      k_scale<float, float><<<eg, 256, 0, s>>>(v0, g.c32.get(), g.isig32.get(), 0, g_hi);
+      k_to_u<float, float><<<eg, 256, 0, s>>>(v0, g.c32.get(), g.isig32.get(), nX, nR, 0, nu);
       PSI_LAUNCHED();
     }
     bool v0_u_cleared = false;
@@ -461,14 +466,14 @@ psi_status solve(Graph& g, double eps, int32_t max_iter, const double* init_s, p
           DevState h = read_state(g, s);
           if (!h.converged) break;  // the step cap came first
           // FP64 gathered vector of the series' s64 (X users; U hold c/sigma)
-          k_scale<double, double><<<eg, 256, 0, s>>>(ub[cur_u], s64, g.isig64.get(), 0, nX);
+          k_to_u<double, double><<<eg, 256, 0, s>>>(ub[cur_u], s64, g.isig64.get(), nX, nR, 0, nX);
           PSI_LAUNCHED();
           u_current = true;
           u_resid_in = ub[cur_u];
         }
         resid_first = false;
-        if (!v0_u_cleared && u_lo < g_hi) {  // later series start from a residual: U terms are 0
-          fill<float>(v0 + u_lo, g_hi - u_lo, 0.0f, s);
+        if (!v0_u_cleared && g.nU > 0) {  // later series start from a residual: U terms are 0
+          fill<float>(v0 + nX, g.nU, 0.0f, s);
           v0_u_cleared = true;
         }
         // one FP64 step s <- s A + c from s64; its gap is the one tested
@@ -487,7 +492,7 @@ psi_status solve(Graph& g, double eps, int32_t max_iter, const double* init_s, p
       }
     }
     if (!u_current) {  // psi from the current s64 (after a capped series, or no loop)
-      k_scale<double, double><<<eg, 256, 0, s>>>(ub[cur_u], s64, g.isig64.get(), 0, nX);
+      k_to_u<double, double><<<eg, 256, 0, s>>>(ub[cur_u], s64, g.isig64.get(), nX, nR, 0, nX);
       PSI_LAUNCHED();
     }
     g.last_s_kind = 0;
