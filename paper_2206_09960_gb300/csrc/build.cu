@@ -1,6 +1,7 @@
 // build.cu -- the operator of Sec. II built on the device from an edge list.
 //
-//  1. validate ids, self-loops and rates; count (raw) in- and out-degrees;
+//  1. validate ids, self-loops and rates; mark users with followers / with leaders (exact)
+//     and count degrees (on a fixed 1-in-k subset of the edges for large graphs);
 //  2. renumber users by class (X: followers and leaders, R: followers only, U: leaders
 //     only, Z: isolated) and, within a class, by decreasing degree, so rows form one range
 //     [0, nX+nR) and the gathered users one compact L2-friendly range;
@@ -44,28 +45,37 @@ __global__ void k_check_rates(const double* __restrict__ lam, const double* __re
   if (bad) atomicOr(err, bad);
 }
 
+// Validates every edge and marks, exactly, who has followers (has_fol) and who has leaders
+// (has_lead) with plain byte stores.  Degrees are only an ordering key for locality: they
+// are counted on every `stride`-th edge (all edges when stride == 1).
 __global__ void k_edges(const int32_t* __restrict__ f, const int32_t* __restrict__ l, int64_t m, int64_t n,
-                        int drop_self, uint32_t* in_deg, uint32_t* out_deg, uint32_t* err) {
+                        int drop_self, int64_t stride, uint8_t* has_fol, uint8_t* has_lead, uint32_t* in_deg,
+                        uint32_t* out_deg, uint32_t* err) {
   uint32_t bits = 0;
   GRID_STRIDE(e, m) {
     int32_t a = f[e], b = l[e];
     if (a < 0 || a >= n || b < 0 || b >= n) { bits |= kErrId; continue; }
     if (a == b) { if (!drop_self) bits |= kErrSelf; continue; }
-    atomicAdd(&out_deg[a], 1u);
-    atomicAdd(&in_deg[b], 1u);
+    has_lead[a] = 1;
+    has_fol[b] = 1;
+    if (e % stride == 0) {
+      atomicAdd(&out_deg[a], 1u);
+      atomicAdd(&in_deg[b], 1u);
+    }
   }
   if (bits) atomicOr(err, bits);
 }
 
 // key = class (2 bits) | rank (23 bits); value = user id.  A stable sort gives ties by id.
-__global__ void k_node_keys(const uint32_t* __restrict__ in_deg, const uint32_t* __restrict__ out_deg, int64_t n,
+__global__ void k_node_keys(const uint8_t* __restrict__ has_fol, const uint8_t* __restrict__ has_lead,
+                            const uint32_t* __restrict__ in_deg, const uint32_t* __restrict__ out_deg, int64_t n,
                             int reorder, uint32_t* key, uint32_t* val, uint32_t* class_count) {
   __shared__ uint32_t cc[4];
   if (threadIdx.x < 4) cc[threadIdx.x] = 0;
   __syncthreads();
   GRID_STRIDE(i, n) {
     uint32_t di = in_deg[i], dout = out_deg[i];
-    uint32_t cls = di > 0 ? (dout > 0 ? 0u : 1u) : (dout > 0 ? 2u : 3u);
+    uint32_t cls = has_fol[i] ? (has_lead[i] ? 0u : 1u) : (has_lead[i] ? 2u : 3u);
     // rows (X, R) by row length (in-degree, which in these graphs also tracks how often a
     // user is gathered); U by how often it is gathered (out-degree)
     uint32_t deg = cls <= 1 ? di : (cls == 2 ? dout : 0u);
@@ -371,13 +381,18 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
   DBuf<uint32_t> err(al, 8);  // [0] error bits, [1..4] class counts, [5] rows seen, [6..7] spare
   PSI_CUDA(cudaMemsetAsync(err.get(), 0, 8 * sizeof(uint32_t), s));
   DBuf<uint32_t> in_deg(al, (size_t)n), out_deg(al, (size_t)n);
+  DBuf<uint8_t> has_fol(al, (size_t)n), has_lead(al, (size_t)n);
   PSI_CUDA(cudaMemsetAsync(in_deg.get(), 0, sizeof(uint32_t) * n, s));
   PSI_CUDA(cudaMemsetAsync(out_deg.get(), 0, sizeof(uint32_t) * n, s));
+  PSI_CUDA(cudaMemsetAsync(has_fol.get(), 0, n, s));
+  PSI_CUDA(cudaMemsetAsync(has_lead.get(), 0, n, s));
   k_check_rates<<<grid_for(n), 256, 0, s>>>(dlam, dmu, n, err.get());
   PSI_LAUNCHED();
   if (m > 0) {
-    k_edges<<<grid_for(m), 256, 0, s>>>(df, dl, m, n, g.opt.self_loops == PSI_DROP ? 1 : 0, in_deg.get(),
-                                        out_deg.get(), err.get());
+    // degree sample: every edge up to 2^26 edges, then a fixed 1-in-k subset
+    const int64_t stride = m > ((int64_t)1 << 26) ? (m >> 26) + 1 : 1;
+    k_edges<<<grid_for(m), 256, 0, s>>>(df, dl, m, n, g.opt.self_loops == PSI_DROP ? 1 : 0, stride, has_fol.get(),
+                                        has_lead.get(), in_deg.get(), out_deg.get(), err.get());
     PSI_LAUNCHED();
   }
   const uint32_t ebits = read1(err.get(), s);
@@ -389,14 +404,16 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
   DBuf<uint32_t> perm32;
   {
     DBuf<uint32_t> k0(al, (size_t)n), k1(al, (size_t)n), v0(al, (size_t)n), v1(al, (size_t)n);
-    k_node_keys<<<grid_for(n), 256, 0, s>>>(in_deg.get(), out_deg.get(), n, g.opt.reorder ? 1 : 0, k0.get(),
-                                            v0.get(), err.get() + 1);
+    k_node_keys<<<grid_for(n), 256, 0, s>>>(has_fol.get(), has_lead.get(), in_deg.get(), out_deg.get(), n,
+                                            g.opt.reorder ? 1 : 0, k0.get(), v0.get(), err.get() + 1);
     PSI_LAUNCHED();
     bool alt = radix_sort<uint32_t>(k0.get(), k1.get(), v0.get(), v1.get(), n, 25, al, s);
     perm32 = alt ? std::move(v1) : std::move(v0);
   }
   in_deg.release();
   out_deg.release();
+  has_fol.release();
+  has_lead.release();
   uint32_t cls[4];
   PSI_CUDA(cudaMemcpyAsync(cls, err.get() + 1, sizeof(cls), cudaMemcpyDeviceToHost, s));
   PSI_CUDA(cudaStreamSynchronize(s));
