@@ -175,6 +175,38 @@ void psi_graph_destroy(psi_graph* g);
 const char* psi_status_string(psi_status s);
 const char* psi_last_error(void);
 
+/* ------------------------------------------------------------------------------------
+ * Scenario batches: S sets of activity rates (lambda, mu) on one follower graph, solved
+ * together.  Each scenario is an independent Power-psi problem (Algorithm 2 with its own
+ * A, B, c, d from Sec. II, its own gap, stop test and step count); one sparse product per
+ * step serves every scenario, so each column index fetched feeds S values.  Precision is
+ * always PSI_FP32_REFINE (FP32 series, FP64 iterate and confirming step, FP64 psi).
+ */
+typedef struct psi_batch psi_batch; /* opaque; owns all of its device memory */
+
+/*
+ * follower/leader/m as in psi_graph_create.  lambda and mu hold S * n FP64 values,
+ * scenario-major (scenario q's rates at [q * n, (q+1) * n)), host or device.
+ * 1 <= S <= 64.  Every scenario's rates are validated (PSI_ERR_BAD_RATE).
+ */
+psi_status psi_batch_create(int64_t n, int64_t m, const int32_t* follower, const int32_t* leader, int32_t S,
+                            const double* lambda, const double* mu, const psi_options* opt, psi_batch** out);
+
+/* Power-psi for every scenario to eps (scaled per opt->tol_mode / bnorm_mode, each scenario
+ * with its own ||B||_inf), at most max_iter steps each.  info may be NULL or hold S entries.
+ * Returns OK when every scenario converged, else NOT_CONVERGED (psi still computed). */
+psi_status psi_batch_solve(psi_batch* b, double eps, int32_t max_iter, psi_solve_info* info);
+
+/* psi of every scenario: S * n FP64 values, scenario-major, input user ids. */
+psi_status psi_batch_scores(const psi_batch* b, double* psi_out);
+
+/* The k highest psi of every scenario (as psi_topk): ids_out[S * k], vals_out[S * k]
+ * (vals_out may be NULL), scenario-major. */
+psi_status psi_batch_topk(const psi_batch* b, int32_t k, int32_t* ids_out, double* vals_out);
+
+psi_status psi_batch_get_stats(const psi_batch* b, psi_graph_stats* stats);
+void psi_batch_destroy(psi_batch* b);
+
 /*
  * psi_topk_noalloc -- the ranking of psi_topk (psi descending, equal psi by ascending
  * user id) for a psi vector the caller holds in its own device memory, with no device

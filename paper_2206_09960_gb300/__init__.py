@@ -17,7 +17,7 @@ from ._binding import (PsiError, psi_get_iterate, psi_graph_create, psi_graph_de
                        psi_graph_get_stats, psi_kernel_launches, psi_options_default, psi_scores, psi_solve,
                        psi_topk, psi_version)
 
-__all__ = ["Graph", "PsiError", "psi_graph_create", "psi_solve", "psi_scores", "psi_topk",
+__all__ = ["Graph", "Batch", "PsiError", "psi_graph_create", "psi_solve", "psi_scores", "psi_topk",
            "psi_get_iterate", "psi_graph_get_stats", "psi_graph_destroy", "psi_options_default",
            "psi_kernel_launches", "psi_version", "load"]
 
@@ -149,3 +149,74 @@ class Graph:
 
     def stats(self) -> dict:
         return psi_graph_get_stats(self._h).as_dict()
+
+
+class Batch:
+    """S activity scenarios on one follower graph, solved together.
+
+    ``lam``/``mu`` are [S, n] FP64 (scenario-major), host or device; 1 <= S <= 64."""
+
+    def __init__(self, n, follower, leader, lam, mu, tol_mode="psi", bnorm_mode="none", self_loops="reject",
+                 reorder=True, stream=None, allocator="torch"):
+        import torch
+
+        B.load()
+        self.n = int(n)
+        self.S = int(lam.shape[0])
+        opt = psi_options_default()
+        opt.precision = B.PSI_FP32_REFINE
+        opt.tol_mode = B.TOL_MODE[tol_mode]
+        opt.bnorm_mode = B.BNORM_MODE[bnorm_mode]
+        opt.self_loops = B.SELF_LOOPS[self_loops]
+        opt.reorder = 1 if reorder else 0
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        opt.stream = ctypes.c_void_p(stream.cuda_stream)
+        self._alloc = None
+        if allocator == "torch":
+            self._alloc = _TorchAllocator(torch.cuda.current_device())
+            opt.allocator = ctypes.pointer(self._alloc.struct)
+        self._opt = opt
+        m = int(follower.shape[0]) if follower is not None else 0
+        self._h = B.psi_batch_create(self.n, m, _ptr(follower), _ptr(leader), self.S, _ptr(lam), _ptr(mu), opt)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            B.psi_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def solve(self, eps, max_iter=10000):
+        st, infos = B.psi_batch_solve(self._h, eps, max_iter, self.S)
+        return B.status_name(st), [i.as_dict() for i in infos]
+
+    def scores(self, out=None):
+        import torch
+
+        if out is None:
+            out = torch.empty((self.S, self.n), dtype=torch.float64, device="cuda")
+        B.psi_batch_scores(self._h, _ptr(out))
+        return out
+
+    def topk(self, k):
+        import torch
+
+        ids = torch.empty((self.S, k), dtype=torch.int32, device="cuda")
+        vals = torch.empty((self.S, k), dtype=torch.float64, device="cuda")
+        B.psi_batch_topk(self._h, k, _ptr(ids), _ptr(vals))
+        return ids, vals
+
+    def stats(self) -> dict:
+        return B.psi_batch_get_stats(self._h).as_dict()

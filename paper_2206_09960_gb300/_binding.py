@@ -28,7 +28,8 @@ SELF_LOOPS = {"reject": PSI_REJECT, "drop": PSI_DROP}
 # every symbol include/psi.h declares
 EXPORTS = ["psi_options_default", "psi_graph_create", "psi_solve", "psi_scores", "psi_topk",
            "psi_get_iterate", "psi_graph_get_stats", "psi_graph_destroy", "psi_status_string",
-           "psi_last_error", "psi_kernel_launches", "psi_version", "psi_topk_noalloc"]
+           "psi_last_error", "psi_kernel_launches", "psi_version", "psi_topk_noalloc", "psi_batch_create",
+           "psi_batch_solve", "psi_batch_scores", "psi_batch_topk", "psi_batch_get_stats", "psi_batch_destroy"]
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -109,6 +110,19 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.psi_status_string.restype = ctypes.c_char_p
         lib.psi_last_error.argtypes = []
         lib.psi_last_error.restype = ctypes.c_char_p
+        lib.psi_batch_create.argtypes = [i64, i64, vp, vp, i32, vp, vp, ctypes.POINTER(psi_options),
+                                         ctypes.POINTER(vp)]
+        lib.psi_batch_create.restype = i32
+        lib.psi_batch_solve.argtypes = [vp, dbl, i32, vp]
+        lib.psi_batch_solve.restype = i32
+        lib.psi_batch_scores.argtypes = [vp, vp]
+        lib.psi_batch_scores.restype = i32
+        lib.psi_batch_topk.argtypes = [vp, i32, vp, vp]
+        lib.psi_batch_topk.restype = i32
+        lib.psi_batch_get_stats.argtypes = [vp, ctypes.POINTER(psi_graph_stats)]
+        lib.psi_batch_get_stats.restype = i32
+        lib.psi_batch_destroy.argtypes = [vp]
+        lib.psi_batch_destroy.restype = None
         lib.psi_topk_noalloc.argtypes = [vp, i64, i32, vp, vp, vp]
         lib.psi_topk_noalloc.restype = i32
         lib.psi_kernel_launches.argtypes = []
@@ -182,6 +196,38 @@ def psi_topk_noalloc(psi_ptr, n, k, ids_ptr, vals_ptr, stream_ptr=None):
     """Ranking of a caller-held device psi vector without any device allocation (queued on
     the stream; the call does not wait)."""
     _check(load().psi_topk_noalloc(psi_ptr, int(n), int(k), ids_ptr, vals_ptr, stream_ptr))
+
+
+def psi_batch_create(n, m, follower_ptr, leader_ptr, S, lambda_ptr, mu_ptr, opt):
+    h = ctypes.c_void_p()
+    _check(load().psi_batch_create(int(n), int(m), follower_ptr, leader_ptr, int(S), lambda_ptr, mu_ptr,
+                                   ctypes.byref(opt) if opt is not None else None, ctypes.byref(h)))
+    return h
+
+
+def psi_batch_solve(h, eps, max_iter, S):
+    infos = (psi_solve_info * int(S))()
+    st = load().psi_batch_solve(h, float(eps), int(max_iter), infos)
+    _check(st, (PSI_OK, PSI_ERR_NOT_CONVERGED))
+    return st, infos
+
+
+def psi_batch_scores(h, out_ptr):
+    _check(load().psi_batch_scores(h, out_ptr))
+
+
+def psi_batch_topk(h, k, ids_ptr, vals_ptr):
+    _check(load().psi_batch_topk(h, int(k), ids_ptr, vals_ptr))
+
+
+def psi_batch_get_stats(h) -> psi_graph_stats:
+    s = psi_graph_stats()
+    _check(load().psi_batch_get_stats(h, ctypes.byref(s)))
+    return s
+
+
+def psi_batch_destroy(h):
+    load().psi_batch_destroy(h)
 
 
 def psi_kernel_launches() -> int:

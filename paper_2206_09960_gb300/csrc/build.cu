@@ -9,7 +9,8 @@
 //     (L(j) is a set), and cut the transposed CSR: row i = followers of leader i;
 //  4. regroup the unique edges by follower (stable radix on the follower id) and form,
 //     for every follower j, sigma_j = sum_{l in L(j)} (lambda_l + mu_l) and
-//     beta_j = sum_{l in L(j)} lambda_l in FP64 (the denominators of a_ji, b_ji);
+//     beta_j = sum_{l in L(j)} lambda_l in FP64 (the denominators of a_ji, b_ji) in one
+//     load-balanced product over that follower-grouped CSR;
 //  5. per-user constants c, d, 1/sigma in FP64 and FP32; ||B||_inf = max_j beta_j/sigma_j;
 //  6. the merge-path tile schedule of the sparse product.
 #include <cmath>
@@ -18,6 +19,7 @@
 #include "primitives.cuh"
 #include "solve.cuh"
 #include "spmv.cuh"
+#include "build.cuh"
 
 namespace psi {
 
@@ -163,13 +165,10 @@ __global__ void k_permute_rates(const double* __restrict__ lam, const double* __
   }
 }
 
-// w[k] = lambda_k + mu_k (or lambda_k), with the pad entry w[n] = 0
+// w[k] = (lambda_k + mu_k, lambda_k), with the pad entry w[n] = (0, 0)
 __global__ void k_leader_weights(const double* __restrict__ lam_i, const double* __restrict__ mu_i, int64_t n,
-                                 double* w_sum, double* w_lam) {
-  GRID_STRIDE(k, n + 1) {
-    w_sum[k] = k < n ? lam_i[k] + mu_i[k] : 0.0;
-    w_lam[k] = k < n ? lam_i[k] : 0.0;
-  }
+                                 D2* w) {
+  GRID_STRIDE(k, n + 1) w[k] = k < n ? D2(lam_i[k] + mu_i[k], lam_i[k]) : D2(0.0, 0.0);
 }
 
 // c_j = mu_j/(lambda_j+mu_j), d_j = lambda_j/(lambda_j+mu_j), 1/sigma_j (0 without leaders)
@@ -201,13 +200,13 @@ __global__ void k_user_vectors(const double* __restrict__ lam_i, const double* _
 }
 
 // tile_row[k] = row holding nonzero k*T (largest r with row_ptr[r] <= k*T); last = n_rows-1
-__global__ void k_tile_rows(const int32_t* __restrict__ row_ptr, int32_t n_rows, int32_t num_tiles,
+__global__ void k_tile_rows(const int32_t* __restrict__ row_ptr, int32_t n_rows, int32_t num_tiles, int32_t tile,
                             int32_t* tile_row) {
   GRID_STRIDE(k, (int64_t)num_tiles + 1) {
     if (k == num_tiles) {
       tile_row[k] = n_rows - 1;
     } else {
-      const int64_t pos = k * (int64_t)kSpmvTile;
+      const int64_t pos = k * (int64_t)tile;
       int32_t lo = 0, hi = n_rows;  // search r in [0, n_rows)
       while (lo < hi) {
         int32_t mid = (lo + hi + 1) >> 1;
@@ -220,20 +219,21 @@ __global__ void k_tile_rows(const int32_t* __restrict__ row_ptr, int32_t n_rows,
 
 // tiles whose first row began in an earlier tile and ends inside this one
 __global__ void k_fix_flags(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ tile_row,
-                            int32_t num_tiles, int64_t mu, uint32_t* flag) {
+                            int32_t num_tiles, int32_t tile, int64_t mu, uint32_t* flag) {
   GRID_STRIDE(k, num_tiles) {
-    const int64_t nnz0 = k * (int64_t)kSpmvTile;
-    const int64_t nnz1 = nnz0 + kSpmvTile < mu ? nnz0 + kSpmvTile : mu;
+    const int64_t nnz0 = k * (int64_t)tile;
+    const int64_t nnz1 = nnz0 + tile < mu ? nnz0 + tile : mu;
     const int32_t r0 = tile_row[k];
     flag[k] = (k > 0 && (int64_t)row_ptr[r0] < nnz0 && (int64_t)row_ptr[r0 + 1] <= nnz1) ? 1u : 0u;
   }
 }
 
 __global__ void k_fix_compact(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ tile_row,
-                              int32_t num_tiles, int64_t mu, const uint32_t* __restrict__ pos, int32_t* fix) {
+                              int32_t num_tiles, int32_t tile, int64_t mu, const uint32_t* __restrict__ pos,
+                              int32_t* fix) {
   GRID_STRIDE(k, num_tiles) {
-    const int64_t nnz0 = k * (int64_t)kSpmvTile;
-    const int64_t nnz1 = nnz0 + kSpmvTile < mu ? nnz0 + kSpmvTile : mu;
+    const int64_t nnz0 = k * (int64_t)tile;
+    const int64_t nnz1 = nnz0 + tile < mu ? nnz0 + tile : mu;
     const int32_t r0 = tile_row[k];
     if (k > 0 && (int64_t)row_ptr[r0] < nnz0 && (int64_t)row_ptr[r0 + 1] <= nnz1) fix[pos[k]] = (int32_t)k;
   }
@@ -256,17 +256,13 @@ T read1(const T* d, cudaStream_t s) {
   return h;
 }
 
-// Merge-path schedule of a CSR with n_rows non-empty rows and m nonzeros.
-struct Schedule {
-  DBuf<int32_t> tile_row;  // [tiles + 1]
-  DBuf<int32_t> fix_tile;  // tiles whose first row began in an earlier tile
-  int32_t tiles = 0;
-  int32_t num_fix = 0;
-};
+}  // namespace
 
-Schedule make_schedule(const int32_t* row_ptr, int32_t n_rows, int64_t m, Allocator& al, cudaStream_t s) {
+// Merge-path schedule of a CSR with n_rows non-empty rows and m nonzeros.
+Schedule make_schedule(const int32_t* row_ptr, int32_t n_rows, int64_t m, Allocator& al, cudaStream_t s,
+                       int32_t tile) {
   Schedule sc;
-  sc.tiles = (int32_t)ceil_div(m, kSpmvTile);
+  sc.tiles = (int32_t)ceil_div(m, tile);
   sc.tile_row.reset(al, (size_t)sc.tiles + 1);
   if (sc.tiles == 0) {
     k_set_i32<<<1, 1, 0, s>>>(sc.tile_row.get(), n_rows - 1);
@@ -274,34 +270,35 @@ Schedule make_schedule(const int32_t* row_ptr, int32_t n_rows, int64_t m, Alloca
     sc.fix_tile.reset(al, 1);
     return sc;
   }
-  k_tile_rows<<<grid_for(sc.tiles + 1), 256, 0, s>>>(row_ptr, n_rows, sc.tiles, sc.tile_row.get());
+  k_tile_rows<<<grid_for(sc.tiles + 1), 256, 0, s>>>(row_ptr, n_rows, sc.tiles, tile, sc.tile_row.get());
   PSI_LAUNCHED();
   DBuf<uint32_t> fpos(al, (size_t)sc.tiles);
   DBuf<uint32_t> ftot(al, 1);
-  k_fix_flags<<<grid_for(sc.tiles), 256, 0, s>>>(row_ptr, sc.tile_row.get(), sc.tiles, m, fpos.get());
+  k_fix_flags<<<grid_for(sc.tiles), 256, 0, s>>>(row_ptr, sc.tile_row.get(), sc.tiles, tile, m, fpos.get());
   PSI_LAUNCHED();
   exclusive_scan_u32(fpos.get(), fpos.get(), sc.tiles, al, s, ftot.get());
   sc.num_fix = (int32_t)read1(ftot.get(), s);
   sc.fix_tile.reset(al, (size_t)(sc.num_fix > 0 ? sc.num_fix : 1));
   if (sc.num_fix > 0) {
-    k_fix_compact<<<grid_for(sc.tiles), 256, 0, s>>>(row_ptr, sc.tile_row.get(), sc.tiles, m, fpos.get(),
+    k_fix_compact<<<grid_for(sc.tiles), 256, 0, s>>>(row_ptr, sc.tile_row.get(), sc.tiles, tile, m, fpos.get(),
                                                      sc.fix_tile.get());
     PSI_LAUNCHED();
   }
   return sc;
 }
 
-// y = (CSR) w with out[user] = y for every row (one product + fix-up, FP64)
+// y = (CSR) w for every row, both sums of the pair at once (one product + fix-up, FP64)
 void run_store_product(const int32_t* row_ptr, const int32_t* col, const Schedule& sc, int32_t n_rows, int64_t m,
-                       const double* w, const EpiStore& epi, Allocator& al, cudaStream_t s) {
+                       const D2* w, const EpiStore2& epi, Allocator& al, cudaStream_t s) {
   if (sc.tiles == 0) return;
   DBuf<DevState> st(al, 1);
   PSI_CUDA(cudaMemsetAsync(st.get(), 0, sizeof(DevState), s));
   int per_sm = 0;
-  PSI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmv<double, EpiStore>, kSpmvThreads, 0));
+  PSI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmv<D2, EpiStore2>, kSpmvThreads, 0));
   int grid = (per_sm > 0 ? per_sm : 1) * (int)num_sms();
   if (grid > sc.tiles) grid = sc.tiles;
-  DBuf<double> gap_part(al, (size_t)grid), carry_head(al, (size_t)sc.tiles), carry_tail(al, (size_t)sc.tiles);
+  DBuf<double> gap_part(al, (size_t)grid);
+  DBuf<D2> carry_head(al, (size_t)sc.tiles), carry_tail(al, (size_t)sc.tiles);
   SpmvArgs a{};
   a.row_ptr = row_ptr;
   a.col = col;
@@ -313,7 +310,7 @@ void run_store_product(const int32_t* row_ptr, const int32_t* col, const Schedul
   a.gap_part = gap_part.get();
   a.carry_head = carry_head.get();
   a.carry_tail = carry_tail.get();
-  k_spmv<double, EpiStore><<<grid, kSpmvThreads, 0, s>>>(a, w, epi);
+  k_spmv<D2, EpiStore2><<<grid, kSpmvThreads, 0, s>>>(a, w, epi);
   PSI_LAUNCHED();
   if (sc.num_fix > 0) {
     int fgrid = (int)ceil_div(sc.num_fix, kFixWarps);
@@ -329,17 +326,16 @@ void run_store_product(const int32_t* row_ptr, const int32_t* col, const Schedul
     f.gap_fix = gap_fix.get();
     f.carry_head = carry_head.get();
     f.carry_tail = carry_tail.get();
-    k_fixup<double, EpiStore><<<fgrid, kFixWarps * 32, 0, s>>>(f, epi);
+    k_fixup<D2, EpiStore2><<<fgrid, kFixWarps * 32, 0, s>>>(f, epi);
     PSI_LAUNCHED();
   }
 }
 
-}  // namespace
 
 bool is_device_pointer(const void* p);
 
 void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const int32_t* leader,
-                 const double* lambda, const double* mu) {
+                 const double* lambda, const double* mu, BuildHook* hook) {
   cudaStream_t s = g.stream;
   Allocator& al = g.al;
   g.n = n;
@@ -492,8 +488,8 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
     g.max_followers = read1(mx.get(), s);
   }
 
-  // ---- 4. leader sums per follower: sigma = L (lambda + mu), beta = L lambda, as two
-  //         load-balanced products over the follower-grouped CSR (rows X then U)
+  // ---- 4. leader sums per follower: (sigma, beta) = L (lambda + mu, lambda), one
+  //         load-balanced product over the follower-grouped CSR (rows X then U)
   DBuf<double> lam_i(al, (size_t)n), mu_i(al, (size_t)n);
   k_permute_rates<<<grid_for(n), 256, 0, s>>>(dlam, dmu, perm32.get(), n, lam_i.get(), mu_i.get());
   PSI_LAUNCHED();
@@ -541,14 +537,16 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
     fk0.release();
     fk1.release();
     lv1.release();
-    Schedule sch = make_schedule(rp_f.get(), n_f, mc, al, s);
-    DBuf<double> w_sum(al, (size_t)n + 1), w_lam(al, (size_t)n + 1);
-    k_leader_weights<<<grid_for(n + 1), 256, 0, s>>>(lam_i.get(), mu_i.get(), n, w_sum.get(), w_lam.get());
+    Schedule sch = make_schedule(rp_f.get(), n_f, mc, al, s, kSpmvTile);
+    DBuf<D2> w(al, (size_t)n + 1);
+    k_leader_weights<<<grid_for(n + 1), 256, 0, s>>>(lam_i.get(), mu_i.get(), n, w.get());
     PSI_LAUNCHED();
-    run_store_product(rp_f.get(), reinterpret_cast<const int32_t*>(ls), sch, n_f, mc, w_sum.get(),
-                      EpiStore{sigma.get(), g.nX, g.nR}, al, s);
-    run_store_product(rp_f.get(), reinterpret_cast<const int32_t*>(ls), sch, n_f, mc, w_lam.get(),
-                      EpiStore{beta.get(), g.nX, g.nR}, al, s);
+    run_store_product(rp_f.get(), reinterpret_cast<const int32_t*>(ls), sch, n_f, mc, w.get(),
+                      EpiStore2{sigma.get(), beta.get(), g.nX, g.nR}, al, s);
+    if (hook) {
+      FollowerCsr fc{rp_f.get(), reinterpret_cast<const int32_t*>(ls), &sch, n_f, mc};
+      hook->on_follower_csr(g, fc);
+    }
   } else {
     li.release();
   }
@@ -580,7 +578,7 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
 
   // ---- 6. tile schedule of the Power-psi product
   {
-    Schedule sch = make_schedule(g.row_ptr.get(), g.n_rows, mu_count, al, s);
+    Schedule sch = make_schedule(g.row_ptr.get(), g.n_rows, mu_count, al, s, kSpmvTile);
     g.tile_row = std::move(sch.tile_row);
     g.fix_tile = std::move(sch.fix_tile);
     g.num_fix = sch.num_fix;

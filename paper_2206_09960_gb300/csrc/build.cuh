@@ -1,0 +1,40 @@
+// build.cuh -- pieces of the graph build shared with the scenario-batch path.
+#pragma once
+
+#include "common.cuh"
+#include "spmv.cuh"
+
+namespace psi {
+
+// Merge-path schedule of a CSR with n_rows non-empty rows and m nonzeros cut in tiles of
+// `tile` nonzeros.
+struct Schedule {
+  DBuf<int32_t> tile_row;  // [tiles + 1]: row holding the tile's first nonzero
+  DBuf<int32_t> fix_tile;  // tiles whose first row began in an earlier tile
+  int32_t tiles = 0;
+  int32_t num_fix = 0;
+};
+
+Schedule make_schedule(const int32_t* row_ptr, int32_t n_rows, int64_t m, Allocator& al, cudaStream_t s,
+                       int32_t tile);
+
+// Per-user pair of sums over a CSR (one load-balanced FP64 product and its fix-up).
+void run_store_product(const int32_t* row_ptr, const int32_t* col, const Schedule& sc, int32_t n_rows, int64_t m,
+                       const D2* w, const EpiStore2& epi, Allocator& al, cudaStream_t s);
+
+// The follower-grouped CSR of a graph under construction: rows are the users with leaders
+// (X then U, compact), columns the leaders (internal ids), padded with the id n.
+struct FollowerCsr {
+  const int32_t* row_ptr;
+  const int32_t* col;
+  const Schedule* sched;
+  int32_t n_rows;
+  int64_t m;
+};
+
+struct BuildHook {
+  virtual ~BuildHook() = default;
+  virtual void on_follower_csr(Graph& g, const FollowerCsr& fc) = 0;
+};
+
+}  // namespace psi

@@ -1,0 +1,205 @@
+// spmm.cuh -- the Power-psi product for S activity scenarios on one graph at once.
+//
+// The follower pattern is the same for every scenario; only the per-user constants differ
+// (sigma, c, mu, lambda, d per scenario).  The gathered values of all scenarios of one user
+// are stored contiguously (row j of a [users x S] matrix), so one column index feeds S
+// values: for S = 64, one fully used 256-byte row per nonzero.
+//
+// Load balance: the nonzeros are cut into chunks of kSpmmChunk; one warp owns a chunk and
+// walks it nonzero by nonzero, all lanes together (row boundaries are warp-uniform, so no
+// divergence), lane l holding scenarios 2l and 2l+1.  A row that began in an earlier chunk
+// leaves its partial sums (S values) for the fix-up kernel, which adds the chunk carries
+// in chunk order: results are bit-reproducible.  Scenarios are masked out individually once
+// they have met their stop test.
+#pragma once
+
+#include "common.cuh"
+
+namespace psi {
+
+constexpr int kSpmmChunk = 128;  // nonzeros per warp task
+constexpr int kSpmmMaxS = 64;    // scenarios per launch (lane l: 2l, 2l+1)
+
+struct SpmmArgs {
+  const int32_t* row_ptr;
+  const int32_t* col;          // padded to whole chunks with the zero entry
+  const int32_t* chunk_row;    // [num_chunks + 1]: row holding the chunk's first nonzero
+  int32_t num_chunks;
+  int32_t n_rows;
+  int64_t m;
+  int32_t S;                   // padded scenario count (64)
+  const int32_t* active;       // [S]: 1 while a scenario still steps
+  const int32_t* done;         // nonzero: no scenario steps, skip the launch
+  double* gap_part;            // [warps][S]
+  float2* carry_head;          // [num_chunks][S/2] (FP32 products)
+  float2* carry_tail;
+  double2* carry_head64;       // FP64 products
+  double2* carry_tail64;
+};
+
+// Series step for S scenarios: t = mu_s * y_s, s_s += t (FP64), v_s = t / sigma_s.
+struct EpiSeriesS {
+  const float2* mu;     // [users][S/2]
+  const float2* isig;
+  double2* s64;         // [users][S/2] as double pairs
+  float2* v_new;        // [gathered][S/2]
+  int32_t nX;
+  __device__ __forceinline__ void row(int32_t r, int lane, float2 y, const int* act, double2& gap) const {
+    const int64_t o = (int64_t)r * 32 + lane;
+    const float2 m = mu[o];
+    float2 t = make_float2(act[0] ? m.x * y.x : 0.f, act[1] ? m.y * y.y : 0.f);
+    double2 s = s64[o];
+    s.x += (double)t.x;
+    s.y += (double)t.y;
+    s64[o] = s;
+    gap.x += fabs((double)t.x);
+    gap.y += fabs((double)t.y);
+    if (r < nX) {
+      const float2 is = isig[o];
+      v_new[o] = make_float2(t.x * is.x, t.y * is.y);
+    }
+  }
+};
+
+// FP64 step for S scenarios: s_new = c + mu*y, r = s_new - s, s = s_new, u_new = s_new/sigma,
+// v32 = r/sigma (start of the next series); inactive scenarios keep their state.
+struct EpiResidS {
+  const double2* c;
+  const double2* mu;
+  const double2* isig;
+  double2* s64;
+  double2* u_new;
+  float2* v32;
+  int32_t nX;
+  __device__ __forceinline__ void row(int32_t r, int lane, double2 y, const int* act, double2& gap) const {
+    const int64_t o = (int64_t)r * 32 + lane;
+    const double2 cc = c[o], mm = mu[o], s = s64[o];
+    double2 sn = make_double2(cc.x + mm.x * y.x, cc.y + mm.y * y.y);
+    if (!act[0]) sn.x = s.x;
+    if (!act[1]) sn.y = s.y;
+    const double2 rr = make_double2(sn.x - s.x, sn.y - s.y);
+    gap.x += fabs(rr.x);
+    gap.y += fabs(rr.y);
+    s64[o] = sn;
+    if (r < nX) {
+      const double2 is = isig[o];
+      u_new[o] = make_double2(sn.x * is.x, sn.y * is.y);
+      v32[o] = make_float2((float)(rr.x * is.x), (float)(rr.y * is.y));
+    }
+  }
+};
+
+// psi_s = (lambda_s * G(s_s) + d_s) / N for every scenario.
+struct EpiFinalS {
+  const double2* lam;
+  const double2* d;
+  double2* psi;
+  double n;
+  __device__ __forceinline__ void row(int32_t r, int lane, double2 y, const int*, double2&) const {
+    const int64_t o = (int64_t)r * 32 + lane;
+    const double2 l = lam[o], dd = d[o];
+    psi[o] = make_double2((l.x * y.x + dd.x) / n, (l.y * y.y + dd.y) / n);
+  }
+};
+
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 add2(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+template <typename V>
+__device__ __forceinline__ V zero2();
+template <>
+__device__ __forceinline__ float2 zero2<float2>() { return make_float2(0.f, 0.f); }
+template <>
+__device__ __forceinline__ double2 zero2<double2>() { return make_double2(0.0, 0.0); }
+
+__device__ __forceinline__ float2 ld_row(const float2* p, uint64_t pol) {
+  float2 v;
+  asm volatile("ld.global.nc.L2::cache_hint.v2.f32 {%0,%1}, [%2], %3;" : "=f"(v.x), "=f"(v.y) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ double2 ld_row(const double2* p, uint64_t pol) {
+  double2 v;
+  asm volatile("ld.global.nc.L2::cache_hint.v2.f64 {%0,%1}, [%2], %3;" : "=d"(v.x), "=d"(v.y) : "l"(p), "l"(pol));
+  return v;
+}
+
+template <typename V>
+__device__ __forceinline__ V* carry_of(const SpmmArgs& a, bool head);
+template <>
+__device__ __forceinline__ float2* carry_of<float2>(const SpmmArgs& a, bool head) {
+  return head ? a.carry_head : a.carry_tail;
+}
+template <>
+__device__ __forceinline__ double2* carry_of<double2>(const SpmmArgs& a, bool head) {
+  return head ? a.carry_head64 : a.carry_tail64;
+}
+
+// V = float2 (FP32 gathers) or double2 (FP64 gathers); u is [gathered + 1][S/2] pairs.
+template <typename V, typename Epi>
+__global__ void __launch_bounds__(256) k_spmm(SpmmArgs a, const V* __restrict__ u, Epi epi) {
+  if (*a.done) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp_id = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const uint64_t pol_s = policy_evict_first();
+  const uint64_t pol_k = policy_evict_last();
+  const int act[2] = {a.active[2 * lane], a.active[2 * lane + 1]};
+  V* ch = carry_of<V>(a, true);
+  V* ct = carry_of<V>(a, false);
+  double2 gap = make_double2(0.0, 0.0);
+  for (int64_t c = warp_id; c < a.num_chunks; c += n_warps) {
+    const int64_t p0 = c * kSpmmChunk;
+    const int64_t p1 = p0 + kSpmmChunk < a.m ? p0 + kSpmmChunk : a.m;
+    int32_t r = a.chunk_row[c];
+    const bool head_open = (int64_t)a.row_ptr[r] < p0;
+    int64_t next_end = a.row_ptr[r + 1];
+    bool first = true;
+    V acc = zero2<V>();
+    for (int64_t q = p0; q < p1; q += 32) {
+      const int cnt = (int)(p1 - q < 32 ? p1 - q : 32);
+      const int my_col = lane < cnt ? ld_stream(a.col + q + lane, pol_s) : 0;
+#pragma unroll 4
+      for (int i = 0; i < cnt; ++i) {
+        const int j = __shfl_sync(0xffffffffu, my_col, i);
+        acc = add2(acc, ld_row(u + (int64_t)j * 32 + lane, pol_k));
+        if (q + i + 1 == next_end) {  // row r ends at this nonzero (warp-uniform)
+          if (first && head_open) ch[c * 32 + lane] = acc;
+          else epi.row(r, lane, acc, act, gap);
+          first = false;
+          acc = zero2<V>();
+          ++r;
+          next_end = r < a.n_rows ? (int64_t)a.row_ptr[r + 1] : INT64_MAX;
+        }
+      }
+    }
+    ct[c * 32 + lane] = acc;  // the part of a row that continues into the next chunk
+  }
+  a.gap_part[warp_id * a.S + 2 * lane] = gap.x;
+  a.gap_part[warp_id * a.S + 2 * lane + 1] = gap.y;
+}
+
+// Rows that began in an earlier chunk: y = carries of the chunks in order + head partial.
+template <typename V, typename Epi>
+__global__ void __launch_bounds__(256) k_spmm_fixup(SpmmArgs a, const int32_t* __restrict__ fix_chunk,
+                                                   int32_t num_fix, double* gap_fix, Epi epi) {
+  if (*a.done) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp_id = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int act[2] = {a.active[2 * lane], a.active[2 * lane + 1]};
+  const V* ch = carry_of<V>(a, true);
+  const V* ct = carry_of<V>(a, false);
+  double2 gap = make_double2(0.0, 0.0);
+  for (int64_t q = warp_id; q < num_fix; q += n_warps) {
+    const int32_t c = fix_chunk[q];
+    const int32_t r = a.chunk_row[c];
+    const int32_t cs = a.row_ptr[r] / kSpmmChunk;
+    V acc = zero2<V>();
+    for (int32_t k = cs; k < c; ++k) acc = add2(acc, ct[(int64_t)k * 32 + lane]);
+    acc = add2(acc, ch[(int64_t)c * 32 + lane]);
+    epi.row(r, lane, acc, act, gap);
+  }
+  gap_fix[warp_id * a.S + 2 * lane] = gap.x;
+  gap_fix[warp_id * a.S + 2 * lane + 1] = gap.y;
+}
+
+}  // namespace psi

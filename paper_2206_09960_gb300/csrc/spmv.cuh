@@ -19,6 +19,38 @@
 
 namespace psi {
 
+// ------------------------------------------------------------------ value types
+// A pair of FP64 sums carried through one product (16-byte gathers).
+struct D2 {
+  double a, b;
+  D2() = default;
+  __device__ __forceinline__ D2(int z) : a(z), b(z) {}
+  __device__ __forceinline__ D2(double x, double y) : a(x), b(y) {}
+};
+__device__ __forceinline__ D2 operator+(D2 x, D2 y) { return D2(x.a + y.a, x.b + y.b); }
+__device__ __forceinline__ D2& operator+=(D2& x, D2 y) {
+  x.a += y.a;
+  x.b += y.b;
+  return x;
+}
+__device__ __forceinline__ D2 ld_gather(const D2* p, uint64_t pol) {
+  double x, y;
+  asm volatile("ld.global.nc.L2::cache_hint.v2.f64 {%0,%1}, [%2], %3;" : "=d"(x), "=d"(y) : "l"(p), "l"(pol));
+  return D2(x, y);
+}
+template <typename T>
+__device__ __forceinline__ T shfl_up_t(T v, int o) { return __shfl_up_sync(0xffffffffu, v, o); }
+template <>
+__device__ __forceinline__ D2 shfl_up_t<D2>(D2 v, int o) {
+  return D2(__shfl_up_sync(0xffffffffu, v.a, o), __shfl_up_sync(0xffffffffu, v.b, o));
+}
+template <typename T>
+__device__ __forceinline__ T shfl_xor_t(T v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+template <>
+__device__ __forceinline__ D2 shfl_xor_t<D2>(D2 v, int o) {
+  return D2(__shfl_xor_sync(0xffffffffu, v.a, o), __shfl_xor_sync(0xffffffffu, v.b, o));
+}
+
 // ------------------------------------------------------------------ epilogues
 // row(r, y, gap): y = G(.)_r for row r (a user with followers); add |change| to gap.
 
@@ -92,14 +124,18 @@ struct EpiFinal {
   }
 };
 
-// Plain product output: out[user] = y, with row r standing for user r < nX ? r : r + skip
-// (used to form per-user sums over a CSR whose rows skip a block of users).
-struct EpiStore {
-  double* out;
+// Plain product output of a pair of sums: out_a[user] = y.a, out_b[user] = y.b, with row r
+// standing for user r < nX ? r : r + skip (per-user sums over a CSR whose rows skip a
+// block of users).
+struct EpiStore2 {
+  double* out_a;
+  double* out_b;
   int32_t nX;
   int32_t skip;
-  __device__ __forceinline__ void row(int32_t r, double y, double&, uint64_t, uint64_t) const {
-    out[r < nX ? r : r + skip] = y;
+  __device__ __forceinline__ void row(int32_t r, D2 y, double&, uint64_t, uint64_t) const {
+    const int32_t user = r < nX ? r : r + skip;
+    out_a[user] = y.a;
+    out_b[user] = y.b;
   }
 };
 
@@ -217,12 +253,12 @@ __global__ void __launch_bounds__(kSpmvThreads) k_spmv(SpmvArgs a, const T* __re
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       int fu = __shfl_up_sync(0xffffffffu, f, o);
-      T vu = __shfl_up_sync(0xffffffffu, v, o);
+      T vu = shfl_up_t(v, o);
       if (lane >= o) seg_join(fu, vu, f, v);
     }
     if (lane == 31) { wf[warp] = f; wv[warp] = v; }
     int fe = __shfl_up_sync(0xffffffffu, f, 1);  // exclusive within the warp
-    T ve = __shfl_up_sync(0xffffffffu, v, 1);
+    T ve = shfl_up_t(v, 1);
     if (lane == 0) { fe = 0; ve = T(0); }
     __syncthreads();
     int fw = 0;  // inclusive prefix of the warps before this one
@@ -284,7 +320,7 @@ __global__ void __launch_bounds__(kFixWarps * 32) k_fixup(FixArgs a, Epi epi) {
     T acc = T(0);
     for (int32_t kk = ks + lane; kk < k; kk += 32) acc += ct[kk];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    for (int o = 16; o > 0; o >>= 1) acc += shfl_xor_t(acc, o);
     if (lane == 0) epi.row(r0, acc + ch[k], gap, pol_s, pol_k);
   }
   if (lane == 0) gsh[warp] = gap;

@@ -124,9 +124,11 @@ __global__ void k_emit(const uint64_t* __restrict__ p, const uint32_t* __restric
 
 void topk(const Graph& gc, int32_t k, int32_t* d_ids, double* d_vals) {
   Graph& g = const_cast<Graph&>(gc);
-  cudaStream_t s = g.stream;
-  Allocator& al = g.al;
-  const int64_t n = g.n;
+  topk_raw(g.psi64.get(), g.perm.get(), g.n, k, d_ids, d_vals, g.al, g.stream);
+}
+
+void topk_raw(const double* psi, const int32_t* perm, int64_t n, int32_t k, int32_t* d_ids, double* d_vals,
+              Allocator& al, cudaStream_t s) {
   DBuf<SelectState> st(al, 1);
   DBuf<uint32_t> hist(al, 256);
   SelectState h{};
@@ -137,14 +139,14 @@ void topk(const Graph& gc, int32_t k, int32_t* d_ids, double* d_vals) {
   const int64_t cap = num_sms() * 8;
   if (blocks > cap) blocks = cap;
   for (int level = 0; level < 12; ++level) {
-    k_select_histo<<<(int)blocks, 256, 0, s>>>(g.psi64.get(), g.perm.get(), n, st.get(), level, hist.get());
+    k_select_histo<<<(int)blocks, 256, 0, s>>>(psi, perm, n, st.get(), level, hist.get());
     PSI_LAUNCHED();
     k_select_choose<<<1, 32, 0, s>>>(st.get(), hist.get(), level);
     PSI_LAUNCHED();
   }
   DBuf<uint64_t> p0(al, (size_t)k), p1(al, (size_t)k);
   DBuf<uint32_t> q0(al, (size_t)k), q1(al, (size_t)k), i0(al, (size_t)k), i1(al, (size_t)k);
-  k_select_collect<<<(int)blocks, 256, 0, s>>>(g.psi64.get(), g.perm.get(), n, st.get(), (uint32_t)k, p0.get(), q0.get());
+  k_select_collect<<<(int)blocks, 256, 0, s>>>(psi, perm, n, st.get(), (uint32_t)k, p0.get(), q0.get());
   PSI_LAUNCHED();
   // stable LSD order: by q, then by p (payload = position)
   const int eb = (int)ceil_div(k, 256);
