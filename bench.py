@@ -153,6 +153,68 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args, S=64, plain_sample=8):
+    """64 activity scenarios (lambda, mu ~ LogNormal(0, 1) each) on one R-MAT graph (default
+    scale 22, edge factor 16): one batched solve against the plain form (one graph and one
+    solve per scenario, timed on `plain_sample` scenarios and scaled to S)."""
+    import numpy as np
+    import torch
+
+    import psigen
+    import paper_2206_09960_gb300 as psi
+
+    scale = 22 if args.scale == 25 else args.scale
+    psi.load(build_if_missing=False)
+    n = 1 << scale
+    f, l = psigen.rmat_graph(scale, 16, *psigen.RMAT_ABC, args.seed, relabel=True)
+    lam = np.stack([psigen.lognormal_rates(n, 0.0, 1.0, 1e-3, 1e3, args.seed * 1000 + q, 301) for q in range(S)])
+    mu = np.stack([psigen.lognormal_rates(n, 0.0, 1.0, 1e-3, 1e3, args.seed * 1000 + q, 302) for q in range(S)])
+    f_d, l_d = torch.from_numpy(f).cuda(), torch.from_numpy(l).cuda()
+    lam_d, mu_d = torch.from_numpy(lam).cuda(), torch.from_numpy(mu).cuda()
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        outs = [fn() for _ in range(reps)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / reps, outs[-1]
+
+    def batched():
+        with psi.Batch(n, f_d, l_d, lam_d, mu_d, stream=stream) as b:
+            status, infos = b.solve(args.eps, 100000)
+            st = b.stats()
+        return status, infos, st
+
+    def plain():
+        infos = []
+        for q in range(plain_sample):
+            with psi.Graph(n, f_d, l_d, lam_d[q], mu_d[q], stream=stream) as g:
+                infos.append(g.solve(args.eps, 100000))
+        return infos
+
+    t_batch, (status, infos, st) = timed(batched, args.steps)
+    t_plain, pinfos = timed(plain, 1)
+    t_plain_all = t_plain * S / plain_sample
+    solve_batch = infos[0]["ms"] / 1e3
+    solve_plain = sum(i["ms"] for i in pinfos) / 1e3 * S / plain_sample
+    line = {"metric": "batched Power-psi: 64 activity scenarios on one graph, time to L1<1e-8 for all",
+            "value": t_batch, "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": False, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"rmat_scale{scale}_ef16_64_scenarios_lognormal1", "n": n, "scenarios": S,
+                       "m_unique": st["m_unique"], "eps": args.eps},
+            "status": status, "iters_max": max(i["iters"] for i in infos),
+            "iters_mean": sum(i["iters"] for i in infos) / S,
+            "batch_solve_s": solve_batch, "plain_s_for_64": t_plain_all, "plain_solve_s_for_64": solve_plain,
+            "speedup_total": t_plain_all / t_batch, "speedup_solve": solve_plain / solve_batch,
+            "plain_sample": plain_sample}
+    print(json.dumps(line), flush=True)
+
+
 def workload_config(args, stats):
     cfg = {"workload": f"rmat_scale{args.scale}_ef16_a.57_b.19_c.19_relabel_lognormal1.5",
            "n": 1 << args.scale, "edge_draws": 16 << args.scale, "eps": args.eps,
@@ -176,10 +238,15 @@ def main():
     ap.add_argument("--eps", type=float, default=1e-8)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="rmat", choices=["rmat", "batch"],
+                    help="rmat: the single-graph step (default); batch: 64 activity scenarios on one graph")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "batch":
+        run_batch(args)
         return
 
     import numpy as np

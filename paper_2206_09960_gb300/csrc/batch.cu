@@ -306,7 +306,9 @@ void batch_buffers(Batch& b) {
   b.carry_tail.reset(al, nc * 32);
   b.carry_head64.reset(al, nc * 32);
   b.carry_tail64.reset(al, nc * 32);
-  b.grid = (int)num_sms() * 4;
+  int per_sm = 0;
+  PSI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmm<float2, EpiSeriesS>, 256, 0));
+  b.grid = (int)num_sms() * (per_sm > 0 ? per_sm : 1);
   b.fgrid = (int)num_sms() * 2;
   b.gap_part.reset(al, (size_t)b.grid * 8 * kSp);
   b.gap_fix.reset(al, (size_t)b.fgrid * 8 * kSp);

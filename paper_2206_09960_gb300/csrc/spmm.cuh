@@ -17,7 +17,7 @@
 
 namespace psi {
 
-constexpr int kSpmmChunk = 128;  // nonzeros per warp task
+constexpr int kSpmmChunk = 512;  // nonzeros per warp task (a divisor of the 2048-nonzero tiles)
 constexpr int kSpmmMaxS = 64;    // scenarios per launch (lane l: 2l, 2l+1)
 
 struct SpmmArgs {
@@ -113,12 +113,12 @@ __device__ __forceinline__ double2 zero2<double2>() { return make_double2(0.0, 0
 
 __device__ __forceinline__ float2 ld_row(const float2* p, uint64_t pol) {
   float2 v;
-  asm volatile("ld.global.nc.L2::cache_hint.v2.f32 {%0,%1}, [%2], %3;" : "=f"(v.x), "=f"(v.y) : "l"(p), "l"(pol));
+  asm("ld.global.nc.L2::cache_hint.v2.f32 {%0,%1}, [%2], %3;" : "=f"(v.x), "=f"(v.y) : "l"(p), "l"(pol));
   return v;
 }
 __device__ __forceinline__ double2 ld_row(const double2* p, uint64_t pol) {
   double2 v;
-  asm volatile("ld.global.nc.L2::cache_hint.v2.f64 {%0,%1}, [%2], %3;" : "=d"(v.x), "=d"(v.y) : "l"(p), "l"(pol));
+  asm("ld.global.nc.L2::cache_hint.v2.f64 {%0,%1}, [%2], %3;" : "=d"(v.x), "=d"(v.y) : "l"(p), "l"(pol));
   return v;
 }
 
@@ -154,20 +154,28 @@ __global__ void __launch_bounds__(256) k_spmm(SpmmArgs a, const V* __restrict__ 
     int64_t next_end = a.row_ptr[r + 1];
     bool first = true;
     V acc = zero2<V>();
+    // col is padded to whole chunks with the zero entry, so groups of 8 never run short
     for (int64_t q = p0; q < p1; q += 32) {
-      const int cnt = (int)(p1 - q < 32 ? p1 - q : 32);
-      const int my_col = lane < cnt ? ld_stream(a.col + q + lane, pol_s) : 0;
-#pragma unroll 4
-      for (int i = 0; i < cnt; ++i) {
-        const int j = __shfl_sync(0xffffffffu, my_col, i);
-        acc = add2(acc, ld_row(u + (int64_t)j * 32 + lane, pol_k));
-        if (q + i + 1 == next_end) {  // row r ends at this nonzero (warp-uniform)
-          if (first && head_open) ch[c * 32 + lane] = acc;
-          else epi.row(r, lane, acc, act, gap);
-          first = false;
-          acc = zero2<V>();
-          ++r;
-          next_end = r < a.n_rows ? (int64_t)a.row_ptr[r + 1] : INT64_MAX;
+      const int my_col = ld_stream(a.col + q + lane, pol_s);
+#pragma unroll 1
+      for (int i0 = 0; i0 < 32 && q + i0 < p1; i0 += 8) {
+        V x[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {  // eight row gathers in flight per lane
+          const int j = __shfl_sync(0xffffffffu, my_col, i0 + i);
+          x[i] = ld_row(u + (int64_t)j * 32 + lane, pol_k);
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          acc = add2(acc, x[i]);
+          if (q + i0 + i + 1 == next_end) {  // row r ends at this nonzero (warp-uniform)
+            if (first && head_open) ch[c * 32 + lane] = acc;
+            else epi.row(r, lane, acc, act, gap);
+            first = false;
+            acc = zero2<V>();
+            ++r;
+            next_end = r < a.n_rows ? (int64_t)a.row_ptr[r + 1] : INT64_MAX;
+          }
         }
       }
     }
@@ -194,6 +202,7 @@ __global__ void __launch_bounds__(256) k_spmm_fixup(SpmmArgs a, const int32_t* _
     const int32_t r = a.chunk_row[c];
     const int32_t cs = a.row_ptr[r] / kSpmmChunk;
     V acc = zero2<V>();
+#pragma unroll 8
     for (int32_t k = cs; k < c; ++k) acc = add2(acc, ct[(int64_t)k * 32 + lane]);
     acc = add2(acc, ch[(int64_t)c * 32 + lane]);
     epi.row(r, lane, acc, act, gap);

@@ -72,7 +72,10 @@ def test_batch_matches_single_graph_path():
     for q in range(S):
         one = gpu_solve(n, w["follower"], w["leader"], lam[q], mu[q], 1e-9)
         assert rel_l1(out["psi"][q], one["psi"]) <= 1e-8
-        assert abs(out["infos"][q]["iters"] - one["info"]["iters"]) <= 1
+        # FP32 term sums round differently in the two kernels (chunk order vs tile tree): a
+        # scenario whose first FP64 check narrowly fails takes one more series step and one
+        # more FP64 step
+        assert abs(out["infos"][q]["iters"] - one["info"]["iters"]) <= 2
 
 
 def test_batch_homogeneous_scenario_is_pagerank_and_modes():
