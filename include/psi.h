@@ -207,6 +207,41 @@ psi_status psi_batch_topk(const psi_batch* b, int32_t k, int32_t* ids_out, doubl
 psi_status psi_batch_get_stats(const psi_batch* b, psi_graph_stats* stats);
 void psi_batch_destroy(psi_batch* b);
 
+/* ------------------------------------------------------------------------------------
+ * Learned warm start.  The paper starts Algorithm 2 from s_0 = c (Eq. 14) and notes that
+ * the fixed point does not depend on the start; here a small network predicts log s_i of
+ * the converged iterate from per-user features and s_0 = exp(prediction) is used instead,
+ * so only the number of steps can change.
+ */
+
+/* 8 features per user ([n][8] FP32, host or device, input user ids): log(1 + followers),
+ * log(1 + leaders), log lambda, log mu, then the mean of each of these four over the user's
+ * followers (0 for a user without followers).  Needs a built graph. */
+psi_status psi_features(const psi_graph* g, float* feat_out);
+
+typedef struct psi_mlp psi_mlp; /* 8 -> 64 -> 64 -> 1 network, GELU, 4801 parameters */
+
+/* Parameters are kept in FP32 (Adam master copy) and BF16 (used by every forward/backward);
+ * inputs are normalised with the model's (mean, std) per feature and rounded to BF16; all
+ * sums are FP32.  Initial weights: uniform(+-sqrt(6/fan_in)) from a SplitMix64 seed. */
+psi_status psi_mlp_create(uint64_t seed, void* stream, psi_mlp** out);
+/* params: 4801 FP32 (W1[8][64], b1[64], W2[64][64], b2[64], W3[64], b3); norm: 18 FP32
+ * (feature means[8], feature stds[8], target mean, target std); either may be NULL. */
+psi_status psi_mlp_set_params(psi_mlp* m, const float* params, const float* norm);
+psi_status psi_mlp_get_params(const psi_mlp* m, float* params, float* norm);
+/* y[r] = predicted log s for x[r][0..8); device pointers. */
+psi_status psi_mlp_forward(const psi_mlp* m, int64_t rows, const float* x, float* y);
+/* Gradient of mean((yhat - t)^2) in normalised target units over the rows (device x, t);
+ * kept for psi_mlp_adam_step, optionally copied to grad_out[4801]; loss_out (nullable). */
+psi_status psi_mlp_grad(psi_mlp* m, int64_t rows, const float* x, const float* target, float* grad_out,
+                        double* loss_out);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) with the last gradient. */
+psi_status psi_mlp_adam_step(psi_mlp* m, float lr);
+void psi_mlp_destroy(psi_mlp* m);
+
+/* psi_solve from s_0 = exp(network prediction) (users without followers: s_0 = c). */
+psi_status psi_solve_warm(psi_graph* g, const psi_mlp* m, double eps, int32_t max_iter, psi_solve_info* info);
+
 /*
  * psi_topk_noalloc -- the ranking of psi_topk (psi descending, equal psi by ascending
  * user id) for a psi vector the caller holds in its own device memory, with no device

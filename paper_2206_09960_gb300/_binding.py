@@ -29,7 +29,9 @@ SELF_LOOPS = {"reject": PSI_REJECT, "drop": PSI_DROP}
 EXPORTS = ["psi_options_default", "psi_graph_create", "psi_solve", "psi_scores", "psi_topk",
            "psi_get_iterate", "psi_graph_get_stats", "psi_graph_destroy", "psi_status_string",
            "psi_last_error", "psi_kernel_launches", "psi_version", "psi_topk_noalloc", "psi_batch_create",
-           "psi_batch_solve", "psi_batch_scores", "psi_batch_topk", "psi_batch_get_stats", "psi_batch_destroy"]
+           "psi_batch_solve", "psi_batch_scores", "psi_batch_topk", "psi_batch_get_stats", "psi_batch_destroy",
+           "psi_features", "psi_mlp_create", "psi_mlp_set_params", "psi_mlp_get_params", "psi_mlp_forward",
+           "psi_mlp_grad", "psi_mlp_adam_step", "psi_mlp_destroy", "psi_solve_warm"]
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -123,6 +125,24 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.psi_batch_get_stats.restype = i32
         lib.psi_batch_destroy.argtypes = [vp]
         lib.psi_batch_destroy.restype = None
+        lib.psi_features.argtypes = [vp, vp]
+        lib.psi_features.restype = i32
+        lib.psi_mlp_create.argtypes = [ctypes.c_uint64, vp, ctypes.POINTER(vp)]
+        lib.psi_mlp_create.restype = i32
+        lib.psi_mlp_set_params.argtypes = [vp, vp, vp]
+        lib.psi_mlp_set_params.restype = i32
+        lib.psi_mlp_get_params.argtypes = [vp, vp, vp]
+        lib.psi_mlp_get_params.restype = i32
+        lib.psi_mlp_forward.argtypes = [vp, i64, vp, vp]
+        lib.psi_mlp_forward.restype = i32
+        lib.psi_mlp_grad.argtypes = [vp, i64, vp, vp, vp, ctypes.POINTER(dbl)]
+        lib.psi_mlp_grad.restype = i32
+        lib.psi_mlp_adam_step.argtypes = [vp, ctypes.c_float]
+        lib.psi_mlp_adam_step.restype = i32
+        lib.psi_mlp_destroy.argtypes = [vp]
+        lib.psi_mlp_destroy.restype = None
+        lib.psi_solve_warm.argtypes = [vp, vp, dbl, i32, ctypes.POINTER(psi_solve_info)]
+        lib.psi_solve_warm.restype = i32
         lib.psi_topk_noalloc.argtypes = [vp, i64, i32, vp, vp, vp]
         lib.psi_topk_noalloc.restype = i32
         lib.psi_kernel_launches.argtypes = []
@@ -228,6 +248,49 @@ def psi_batch_get_stats(h) -> psi_graph_stats:
 
 def psi_batch_destroy(h):
     load().psi_batch_destroy(h)
+
+
+def psi_features(h, out_ptr):
+    _check(load().psi_features(h, out_ptr))
+
+
+def psi_mlp_create(seed, stream_ptr=None):
+    h = ctypes.c_void_p()
+    _check(load().psi_mlp_create(int(seed), stream_ptr, ctypes.byref(h)))
+    return h
+
+
+def psi_mlp_set_params(h, params_ptr, norm_ptr):
+    _check(load().psi_mlp_set_params(h, params_ptr, norm_ptr))
+
+
+def psi_mlp_get_params(h, params_ptr, norm_ptr):
+    _check(load().psi_mlp_get_params(h, params_ptr, norm_ptr))
+
+
+def psi_mlp_forward(h, rows, x_ptr, y_ptr):
+    _check(load().psi_mlp_forward(h, int(rows), x_ptr, y_ptr))
+
+
+def psi_mlp_grad(h, rows, x_ptr, t_ptr, grad_ptr=None):
+    loss = ctypes.c_double()
+    _check(load().psi_mlp_grad(h, int(rows), x_ptr, t_ptr, grad_ptr, ctypes.byref(loss)))
+    return loss.value
+
+
+def psi_mlp_adam_step(h, lr):
+    _check(load().psi_mlp_adam_step(h, float(lr)))
+
+
+def psi_mlp_destroy(h):
+    load().psi_mlp_destroy(h)
+
+
+def psi_solve_warm(g, m, eps, max_iter):
+    info = psi_solve_info()
+    st = load().psi_solve_warm(g, m, float(eps), int(max_iter), ctypes.byref(info))
+    _check(st, (PSI_OK, PSI_ERR_NOT_CONVERGED))
+    return st, info
 
 
 def psi_kernel_launches() -> int:

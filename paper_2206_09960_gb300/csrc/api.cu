@@ -143,10 +143,6 @@ psi_status guarded(F&& f) {
 using psi::Graph;
 using psi::PsiError;
 
-struct psi_graph {
-  Graph g;
-};
-
 extern "C" {
 
 void psi_options_default(psi_options* opt) {

@@ -165,6 +165,14 @@ __global__ void k_permute_rates(const double* __restrict__ lam, const double* __
   }
 }
 
+// leaders of every user from the follower-grouped CSR (rows: X then U, compact)
+__global__ void k_leader_counts(const int32_t* __restrict__ rp_f, int32_t n_f, int32_t nX, int32_t nR, int32_t* cnt) {
+  GRID_STRIDE(r, n_f) {
+    const int64_t user = r < nX ? r : r + nR;
+    cnt[user] = rp_f[r + 1] - rp_f[r];
+  }
+}
+
 // w[k] = (lambda_k + mu_k, lambda_k), with the pad entry w[n] = (0, 0)
 __global__ void k_leader_weights(const double* __restrict__ lam_i, const double* __restrict__ mu_i, int64_t n,
                                  D2* w) {
@@ -497,6 +505,8 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
   lam_buf.release();
   mu_buf.release();
   DBuf<double> sigma(al, (size_t)n), beta(al, (size_t)n);
+  g.n_leaders.reset(al, (size_t)n);
+  PSI_CUDA(cudaMemsetAsync(g.n_leaders.get(), 0, sizeof(int32_t) * n, s));
   PSI_CUDA(cudaMemsetAsync(sigma.get(), 0, sizeof(double) * n, s));
   PSI_CUDA(cudaMemsetAsync(beta.get(), 0, sizeof(double) * n, s));
   if (mu_count > 0) {
@@ -543,6 +553,8 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
     PSI_LAUNCHED();
     run_store_product(rp_f.get(), reinterpret_cast<const int32_t*>(ls), sch, n_f, mc, w.get(),
                       EpiStore2{sigma.get(), beta.get(), g.nX, g.nR}, al, s);
+    k_leader_counts<<<grid_for(n_f), 256, 0, s>>>(rp_f.get(), n_f, g.nX, g.nR, g.n_leaders.get());
+    PSI_LAUNCHED();
     if (hook) {
       FollowerCsr fc{rp_f.get(), reinterpret_cast<const int32_t*>(ls), &sch, n_f, mc};
       hook->on_follower_csr(g, fc);

@@ -203,6 +203,7 @@ struct Graph {
   double bnorm_inf = 0.0, rho_inf = 0.0, build_ms = 0.0;
 
   DBuf<int32_t> perm;       // internal -> input id [n]
+  DBuf<int32_t> n_leaders;  // leaders of each user (internal order), for model features
   DBuf<int32_t> row_ptr;    // [n_rows + 1]
   DBuf<int32_t> col;        // [m padded to a tile multiple]: internal follower id, pad = n
   DBuf<int32_t> tile_row;   // [num_tiles + 1]: row holding the tile's first nnz
@@ -229,7 +230,7 @@ struct Graph {
 };
 
 int64_t num_sms();
-inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+__host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 // copy n elements to device memory `dst` from a host or device pointer
 void copy_in(void* dst, const void* src, size_t bytes, cudaStream_t s);

@@ -19,3 +19,8 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
                  const double* lambda, const double* mu, BuildHook* hook = nullptr);
 
 }  // namespace psi
+
+// the C ABI's opaque graph handle
+struct psi_graph {
+  psi::Graph g;
+};
