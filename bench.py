@@ -215,6 +215,65 @@ def run_batch(args, S=64, plain_sample=8):
     print(json.dumps(line), flush=True)
 
 
+def run_warmstart(args, n_train=200, eval_scale=23, train_steps=1500):
+    """Train the warm-start network on solves of `n_train` seeded R-MAT graphs of scale 16-20
+    (the benchmark's rate law), then time Power-psi to eps on a held-out R-MAT graph of scale
+    `eval_scale` from s_0 = c and from the network's start."""
+    import numpy as np
+    import torch
+
+    import psigen
+    import paper_2206_09960_gb300 as psi
+    from paper_2206_09960_gb300.warmstart import train, training_rows
+
+    psi.load(build_if_missing=False)
+    t0 = time.perf_counter()
+    x_parts, t_parts = [], []
+    for k in range(n_train):  # generated and solved in chunks to bound host memory
+        w = psigen.workload("rmat", seed=1000 + k, scale=16 + k % 5)
+        x, t = training_rows([w], rows_per_graph=1 << 14, seed=k)
+        x_parts.append(x)
+        t_parts.append(t)
+    x, t = torch.cat(x_parts), torch.cat(t_parts)
+    t_data = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    model, losses = train(x, t, steps=train_steps, batch=1 << 16, lr=3e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    w = psigen.workload("rmat", seed=7777, scale=eval_scale)
+    args_d = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (w["follower"], w["leader"], w["lam"], w["mu"])]
+    stream = torch.cuda.current_stream()
+    res = {}
+    with psi.Graph(w["n"], *args_d, stream=stream) as g:
+        for name in ("cold", "warm"):
+            ts, its = [], []
+            for rep in range(args.warmup + args.steps):
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                info = g.solve(args.eps, 100000) if name == "cold" else model.solve(g, args.eps, 100000)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if rep >= args.warmup:
+                    ts.append(e0.elapsed_time(e1) / 1e3)
+                    its.append(info["iters"])
+            res[name] = (statistics.mean(ts), its[-1], info["converged"])
+        psi_warm = g.scores().cpu().numpy()
+        g.solve(args.eps, 100000)
+        psi_cold = g.scores().cpu().numpy()
+    rel = float(np.abs(psi_warm - psi_cold).sum() / np.abs(psi_cold).sum())
+    line = {"metric": "warm start: Power-psi time and steps to L1<1e-8 from the network's s_0 vs s_0 = c",
+            "value": res["warm"][0], "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": False, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"train: {n_train} R-MAT graphs scale 16-20; eval: R-MAT scale {eval_scale}",
+                       "eps": args.eps, "train_rows": int(x.shape[0]), "train_steps": train_steps},
+            "cold_s": res["cold"][0], "cold_iters": res["cold"][1], "warm_s": res["warm"][0],
+            "warm_iters": res["warm"][1], "converged": [res["cold"][2], res["warm"][2]],
+            "psi_rel_l1_warm_vs_cold": rel, "loss_first": float(np.mean(losses[:10])),
+            "loss_last": float(np.mean(losses[-50:])), "data_s": t_data, "train_s": t_train}
+    print(json.dumps(line), flush=True)
+
+
 def workload_config(args, stats):
     cfg = {"workload": f"rmat_scale{args.scale}_ef16_a.57_b.19_c.19_relabel_lognormal1.5",
            "n": 1 << args.scale, "edge_draws": 16 << args.scale, "eps": args.eps,
@@ -238,8 +297,9 @@ def main():
     ap.add_argument("--eps", type=float, default=1e-8)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="rmat", choices=["rmat", "batch"],
-                    help="rmat: the single-graph step (default); batch: 64 activity scenarios on one graph")
+    ap.add_argument("--workload", default="rmat", choices=["rmat", "batch", "warmstart"],
+                    help="rmat: the single-graph step (default); batch: 64 activity scenarios on one graph; "
+                         "warmstart: train the start-vector network and compare steps and time to eps")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -247,6 +307,9 @@ def main():
         return
     if args.workload == "batch":
         run_batch(args)
+        return
+    if args.workload == "warmstart":
+        run_warmstart(args)
         return
 
     import numpy as np

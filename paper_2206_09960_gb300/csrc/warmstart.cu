@@ -614,8 +614,12 @@ psi_status psi_solve_warm(psi_graph* g, const psi_mlp* h, double eps, int32_t ma
     DBuf<float> xi(gg.al, (size_t)n * kIn), yhat(gg.al, (size_t)n);
     compute_features(gg, xi.get());
     const Mlp& m = h->m;
-    k_mlp_forward<<<wgrid(n), 256, 0, gg.stream>>>(m.wb.get(), m.norm.get(), n, xi.get(), yhat.get());
-    PSI_LAUNCHED();
+    // only users with followers need a prediction (rows [0, n_rows)); the others have s = c
+    if (gg.n_rows > 0) {
+      k_mlp_forward<<<wgrid(gg.n_rows), 256, 0, gg.stream>>>(m.wb.get(), m.norm.get(), gg.n_rows, xi.get(),
+                                                            yhat.get());
+      PSI_LAUNCHED();
+    }
     DBuf<double> s0i(gg.al, (size_t)n), s0(gg.al, (size_t)n);
     k_warm_s0<<<wgrid(n), 256, 0, gg.stream>>>(yhat.get(), xi.get(), gg.lam64.get(), gg.mu64.get(), n, s0i.get());
     PSI_LAUNCHED();
