@@ -215,6 +215,75 @@ def run_batch(args, S=64, plain_sample=8):
     print(json.dumps(line), flush=True)
 
 
+def run_multi(args, G=256, plain_sample=32):
+    """256 independent Chung-Lu graphs (N ~ U{1000..100000}, 12 draws per user, exponent
+    2.1, lambda, mu ~ LogNormal(0, 1)) built and solved together in one object (psi_multi,
+    steps replayed from a CUDA graph), against the plain form (one graph object and solve per
+    graph, timed on `plain_sample` graphs and scaled by their share of the edges)."""
+    import numpy as np
+    import torch
+
+    import psigen
+    import paper_2206_09960_gb300 as psi
+
+    psi.load(build_if_missing=False)
+    w = psigen.multi_workload(G, seed=args.seed)
+    n_g, m_g = w["n_g"], w["m_g"]
+    dev = [torch.from_numpy(np.ascontiguousarray(w[k])).cuda() for k in ("follower", "leader", "lam", "mu")]
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        outs = [fn() for _ in range(reps)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / reps, outs[-1]
+
+    def together():
+        with psi.Multi(n_g, m_g, *dev, stream=stream) as mg:
+            status, infos = mg.solve(args.eps, 100000)
+            ids, _ = mg.topk(100)
+            st = mg.stats()
+        return status, infos, st
+
+    eo = np.concatenate([[0], np.cumsum(m_g)])
+    no = np.concatenate([[0], np.cumsum(n_g)])
+    sample = list(range(0, G, max(1, G // plain_sample)))[:plain_sample]
+
+    def plain():
+        infos = []
+        for q in sample:
+            with psi.Graph(int(n_g[q]), dev[0][eo[q]:eo[q + 1]], dev[1][eo[q]:eo[q + 1]], dev[2][no[q]:no[q + 1]],
+                           dev[3][no[q]:no[q + 1]], stream=stream) as g:
+                infos.append(g.solve(args.eps, 100000))
+                g.topk(100)
+        return infos
+
+    launches0 = psi._binding.load().psi_kernel_launches()
+    t_multi, (status, infos, st) = timed(together, args.steps)
+    launches = (psi._binding.load().psi_kernel_launches() - launches0) / (args.warmup + args.steps)
+    t_plain, pinfos = timed(plain, 1)
+    share = float(m_g[sample].sum()) / float(m_g.sum())
+    t_plain_all = t_plain / share
+    solve_multi = infos[0]["ms"] / 1e3
+    solve_plain = sum(i["ms"] for i in pinfos) / 1e3 / share
+    iters = [i["iters"] for i in infos]
+    line = {"metric": "independent graphs: 256 Chung-Lu graphs, build + Power-psi to L1<1e-8 + top-100 for all",
+            "value": t_multi, "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": False, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "256 Chung-Lu graphs, N~U{1000..100000}, 12 draws/user, gamma 2.1, lognormal1",
+                       "n_total": int(n_g.sum()), "m_unique": st["m_unique"], "eps": args.eps},
+            "status": status, "iters_min": min(iters), "iters_max": max(iters), "iters_mean": sum(iters) / G,
+            "multi_solve_s": solve_multi, "plain_s_for_256": t_plain_all, "plain_solve_s_for_256": solve_plain,
+            "speedup_total": t_plain_all / t_multi, "speedup_solve": solve_plain / solve_multi,
+            "plain_sample": len(sample), "gpu_launches": launches, "build_ms": st["build_ms"]}
+    print(json.dumps(line), flush=True)
+
+
 def run_warmstart(args, n_train=200, eval_scale=23, train_steps=1500):
     """Train the warm-start network on solves of `n_train` seeded R-MAT graphs of scale 16-20
     (the benchmark's rate law), then time Power-psi to eps on a held-out R-MAT graph of scale
@@ -297,7 +366,7 @@ def main():
     ap.add_argument("--eps", type=float, default=1e-8)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="rmat", choices=["rmat", "batch", "warmstart"],
+    ap.add_argument("--workload", default="rmat", choices=["rmat", "batch", "warmstart", "multi"],
                     help="rmat: the single-graph step (default); batch: 64 activity scenarios on one graph; "
                          "warmstart: train the start-vector network and compare steps and time to eps")
     args = ap.parse_args()
@@ -310,6 +379,9 @@ def main():
         return
     if args.workload == "warmstart":
         run_warmstart(args)
+        return
+    if args.workload == "multi":
+        run_multi(args)
         return
 
     import numpy as np

@@ -208,6 +208,45 @@ psi_status psi_batch_get_stats(const psi_batch* b, psi_graph_stats* stats);
 void psi_batch_destroy(psi_batch* b);
 
 /* ------------------------------------------------------------------------------------
+ * Independent graphs: G follower graphs of their own (own users, N_g, edges, rates), each
+ * solved as its own Power-psi problem (Algorithm 2 with its own N_g in psi = (.)/N_g and in
+ * the psi tolerance, its own gap, stop test, step count and FP64 confirming step), all in
+ * one object: the graphs are built together as one block-diagonal graph and stepped
+ * together, graphs that have met their test skipping their part of each product, from a
+ * CUDA graph of captured steps.  Precision is always PSI_FP32_REFINE.
+ */
+typedef struct psi_multi psi_multi; /* opaque; owns all of its device memory */
+
+/*
+ * 1 <= G <= 1024.  n_g[G], m_g[G]: host arrays, n_g >= 1, m_g >= 0, sums below 2^31 - 1.
+ * follower/leader: sum(m_g) int32 ids, graph by graph (graph q's edges at
+ * [m_0 + .. + m_{q-1}, +m_q)), each id LOCAL to its graph, in [0, n_g); host or device.
+ * lambda/mu: sum(n_g) FP64 rates, graph by graph, host or device.  Errors as in
+ * psi_graph_create (an id outside its own graph: PSI_ERR_OUT_OF_RANGE_ID).
+ */
+psi_status psi_multi_create(int32_t G, const int64_t* n_g, const int64_t* m_g, const int32_t* follower,
+                            const int32_t* leader, const double* lambda, const double* mu, const psi_options* opt,
+                            psi_multi** out);
+
+/* Power-psi for every graph to eps (scaled per opt->tol_mode / bnorm_mode with the graph's
+ * own N_g and ||B||_inf), at most max_iter steps each.  info may be NULL or hold G entries.
+ * Returns OK when every graph converged, else NOT_CONVERGED (psi still computed). */
+psi_status psi_multi_solve(psi_multi* mg, double eps, int32_t max_iter, psi_solve_info* info);
+
+/* psi of every graph (psi = (.)/N_g with the graph's own N_g): sum(n_g) FP64 values, graph
+ * by graph, local user order. */
+psi_status psi_multi_scores(const psi_multi* mg, double* psi_out);
+
+/* The k highest psi of every graph (psi descending, equal psi by ascending local id):
+ * ids_out[G * k] local ids, vals_out[G * k] (may be NULL), graph-major.
+ * 1 <= k <= min(1024, smallest n_g). */
+psi_status psi_multi_topk(const psi_multi* mg, int32_t k, int32_t* ids_out, double* vals_out);
+
+/* Statistics of the block-diagonal union (n = sum of n_g, ...). */
+psi_status psi_multi_get_stats(const psi_multi* mg, psi_graph_stats* stats);
+void psi_multi_destroy(psi_multi* mg);
+
+/* ------------------------------------------------------------------------------------
  * Learned warm start.  The paper starts Algorithm 2 from s_0 = c (Eq. 14) and notes that
  * the fixed point does not depend on the start; here a small network predicts log s_i of
  * the converged iterate from per-user features and s_0 = exp(prediction) is used instead,

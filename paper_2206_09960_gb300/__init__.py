@@ -17,7 +17,7 @@ from ._binding import (PsiError, psi_get_iterate, psi_graph_create, psi_graph_de
                        psi_graph_get_stats, psi_kernel_launches, psi_options_default, psi_scores, psi_solve,
                        psi_topk, psi_version)
 
-__all__ = ["Graph", "Batch", "PsiError", "psi_graph_create", "psi_solve", "psi_scores", "psi_topk",
+__all__ = ["Graph", "Batch", "Multi", "PsiError", "psi_graph_create", "psi_solve", "psi_scores", "psi_topk",
            "psi_get_iterate", "psi_graph_get_stats", "psi_graph_destroy", "psi_options_default",
            "psi_kernel_launches", "psi_version", "load"]
 
@@ -220,3 +220,79 @@ class Batch:
 
     def stats(self) -> dict:
         return B.psi_batch_get_stats(self._h).as_dict()
+
+
+class Multi:
+    """G independent follower graphs solved together (one block-diagonal build, per-graph
+    N_g, stop tests and step counts, steps replayed from a CUDA graph).
+
+    ``n_g``, ``m_g``: per-graph user and edge counts; ``follower``/``leader``: the graphs'
+    edge lists one after another, ids local to each graph; ``lam``/``mu``: the graphs' rates
+    one after another (sum of n_g values).  Host (numpy) or device (torch) arrays."""
+
+    def __init__(self, n_g, m_g, follower, leader, lam, mu, tol_mode="psi", bnorm_mode="none",
+                 self_loops="reject", reorder=True, stream=None, allocator="torch"):
+        import torch
+
+        B.load()
+        self.n_g = np.ascontiguousarray(n_g, dtype=np.int64)
+        self.m_g = np.ascontiguousarray(m_g, dtype=np.int64)
+        self.G = int(self.n_g.shape[0])
+        self.n = int(self.n_g.sum())
+        opt = psi_options_default()
+        opt.precision = B.PSI_FP32_REFINE
+        opt.tol_mode = B.TOL_MODE[tol_mode]
+        opt.bnorm_mode = B.BNORM_MODE[bnorm_mode]
+        opt.self_loops = B.SELF_LOOPS[self_loops]
+        opt.reorder = 1 if reorder else 0
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        opt.stream = ctypes.c_void_p(stream.cuda_stream)
+        self._alloc = None
+        if allocator == "torch":
+            self._alloc = _TorchAllocator(torch.cuda.current_device())
+            opt.allocator = ctypes.pointer(self._alloc.struct)
+        self._opt = opt
+        self._h = B.psi_multi_create(self.G, _ptr(self.n_g), _ptr(self.m_g), _ptr(follower), _ptr(leader),
+                                     _ptr(lam), _ptr(mu), opt)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            B.psi_multi_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def solve(self, eps, max_iter=10000):
+        st, infos = B.psi_multi_solve(self._h, eps, max_iter, self.G)
+        return B.status_name(st), [i.as_dict() for i in infos]
+
+    def scores(self, out=None):
+        import torch
+
+        if out is None:
+            out = torch.empty(self.n, dtype=torch.float64, device="cuda")
+        B.psi_multi_scores(self._h, _ptr(out))
+        return out
+
+    def topk(self, k):
+        import torch
+
+        ids = torch.empty((self.G, k), dtype=torch.int32, device="cuda")
+        vals = torch.empty((self.G, k), dtype=torch.float64, device="cuda")
+        B.psi_multi_topk(self._h, k, _ptr(ids), _ptr(vals))
+        return ids, vals
+
+    def stats(self) -> dict:
+        return B.psi_multi_get_stats(self._h).as_dict()

@@ -31,7 +31,8 @@ EXPORTS = ["psi_options_default", "psi_graph_create", "psi_solve", "psi_scores",
            "psi_last_error", "psi_kernel_launches", "psi_version", "psi_topk_noalloc", "psi_batch_create",
            "psi_batch_solve", "psi_batch_scores", "psi_batch_topk", "psi_batch_get_stats", "psi_batch_destroy",
            "psi_features", "psi_mlp_create", "psi_mlp_set_params", "psi_mlp_get_params", "psi_mlp_forward",
-           "psi_mlp_grad", "psi_mlp_adam_step", "psi_mlp_destroy", "psi_solve_warm"]
+           "psi_mlp_grad", "psi_mlp_adam_step", "psi_mlp_destroy", "psi_solve_warm", "psi_multi_create",
+           "psi_multi_solve", "psi_multi_scores", "psi_multi_topk", "psi_multi_get_stats", "psi_multi_destroy"]
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -125,6 +126,19 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.psi_batch_get_stats.restype = i32
         lib.psi_batch_destroy.argtypes = [vp]
         lib.psi_batch_destroy.restype = None
+        lib.psi_multi_create.argtypes = [i32, vp, vp, vp, vp, vp, vp, ctypes.POINTER(psi_options),
+                                         ctypes.POINTER(vp)]
+        lib.psi_multi_create.restype = i32
+        lib.psi_multi_solve.argtypes = [vp, dbl, i32, vp]
+        lib.psi_multi_solve.restype = i32
+        lib.psi_multi_scores.argtypes = [vp, vp]
+        lib.psi_multi_scores.restype = i32
+        lib.psi_multi_topk.argtypes = [vp, i32, vp, vp]
+        lib.psi_multi_topk.restype = i32
+        lib.psi_multi_get_stats.argtypes = [vp, ctypes.POINTER(psi_graph_stats)]
+        lib.psi_multi_get_stats.restype = i32
+        lib.psi_multi_destroy.argtypes = [vp]
+        lib.psi_multi_destroy.restype = None
         lib.psi_features.argtypes = [vp, vp]
         lib.psi_features.restype = i32
         lib.psi_mlp_create.argtypes = [ctypes.c_uint64, vp, ctypes.POINTER(vp)]
@@ -248,6 +262,38 @@ def psi_batch_get_stats(h) -> psi_graph_stats:
 
 def psi_batch_destroy(h):
     load().psi_batch_destroy(h)
+
+
+def psi_multi_create(G, n_g_ptr, m_g_ptr, follower_ptr, leader_ptr, lambda_ptr, mu_ptr, opt):
+    h = ctypes.c_void_p()
+    _check(load().psi_multi_create(int(G), n_g_ptr, m_g_ptr, follower_ptr, leader_ptr, lambda_ptr, mu_ptr,
+                                   ctypes.byref(opt) if opt is not None else None, ctypes.byref(h)))
+    return h
+
+
+def psi_multi_solve(h, eps, max_iter, G):
+    infos = (psi_solve_info * int(G))()
+    st = load().psi_multi_solve(h, float(eps), int(max_iter), infos)
+    _check(st, (PSI_OK, PSI_ERR_NOT_CONVERGED))
+    return st, infos
+
+
+def psi_multi_scores(h, out_ptr):
+    _check(load().psi_multi_scores(h, out_ptr))
+
+
+def psi_multi_topk(h, k, ids_ptr, vals_ptr):
+    _check(load().psi_multi_topk(h, int(k), ids_ptr, vals_ptr))
+
+
+def psi_multi_get_stats(h) -> psi_graph_stats:
+    s = psi_graph_stats()
+    _check(load().psi_multi_get_stats(h, ctypes.byref(s)))
+    return s
+
+
+def psi_multi_destroy(h):
+    load().psi_multi_destroy(h)
 
 
 def psi_features(h, out_ptr):

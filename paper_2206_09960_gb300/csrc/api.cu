@@ -16,6 +16,7 @@ std::atomic<int64_t> g_launches{0};
 }
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 void set_last_error(const std::string& msg) { g_last_error = msg; }
 

@@ -69,9 +69,12 @@ __global__ void k_edges(const int32_t* __restrict__ f, const int32_t* __restrict
 }
 
 // key = class (2 bits) | rank (23 bits); value = user id.  A stable sort gives ties by id.
+// With groups (independent graphs solved together), the key is class | group (10 bits) |
+// rank (13 bits), so each group's users stay contiguous inside every class.
 __global__ void k_node_keys(const uint8_t* __restrict__ has_fol, const uint8_t* __restrict__ has_lead,
                             const uint32_t* __restrict__ in_deg, const uint32_t* __restrict__ out_deg, int64_t n,
-                            int reorder, uint32_t* key, uint32_t* val, uint32_t* class_count) {
+                            int reorder, const int32_t* __restrict__ group, uint32_t* key, uint32_t* val,
+                            uint32_t* class_count) {
   __shared__ uint32_t cc[4];
   if (threadIdx.x < 4) cc[threadIdx.x] = 0;
   __syncthreads();
@@ -81,8 +84,13 @@ __global__ void k_node_keys(const uint8_t* __restrict__ has_fol, const uint8_t* 
     // rows (X, R) by row length (in-degree, which in these graphs also tracks how often a
     // user is gathered); U by how often it is gathered (out-degree)
     uint32_t deg = cls <= 1 ? di : (cls == 2 ? dout : 0u);
-    uint32_t rank = reorder ? (deg >= 0x7FFFFFu ? 0u : 0x7FFFFFu - deg) : 0u;
-    key[i] = (cls << 23) | rank;
+    if (group) {
+      const uint32_t r13 = reorder ? (deg >= 0x1FFFu ? 0u : 0x1FFFu - deg) : 0u;
+      key[i] = (cls << 23) | ((uint32_t)group[i] << 13) | r13;
+    } else {
+      const uint32_t rank = reorder ? (deg >= 0x7FFFFFu ? 0u : 0x7FFFFFu - deg) : 0u;
+      key[i] = (cls << 23) | rank;
+    }
     val[i] = (uint32_t)i;
     atomicAdd(&cc[cls], 1u);
   }
@@ -409,7 +417,8 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
   {
     DBuf<uint32_t> k0(al, (size_t)n), k1(al, (size_t)n), v0(al, (size_t)n), v1(al, (size_t)n);
     k_node_keys<<<grid_for(n), 256, 0, s>>>(has_fol.get(), has_lead.get(), in_deg.get(), out_deg.get(), n,
-                                            g.opt.reorder ? 1 : 0, k0.get(), v0.get(), err.get() + 1);
+                                            g.opt.reorder ? 1 : 0, hook ? hook->user_group() : nullptr, k0.get(),
+                                            v0.get(), err.get() + 1);
     PSI_LAUNCHED();
     bool alt = radix_sort<uint32_t>(k0.get(), k1.get(), v0.get(), v1.get(), n, 25, al, s);
     perm32 = alt ? std::move(v1) : std::move(v0);

@@ -35,6 +35,9 @@ struct FollowerCsr {
 struct BuildHook {
   virtual ~BuildHook() = default;
   virtual void on_follower_csr(Graph& g, const FollowerCsr& fc) = 0;
+  // device array of a group id (< 1024) per input user, or nullptr: users of one group stay
+  // contiguous inside each class of the renumbering
+  virtual const int32_t* user_group() const { return nullptr; }
 };
 
 }  // namespace psi

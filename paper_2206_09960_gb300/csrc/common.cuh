@@ -33,6 +33,7 @@ void set_last_error(const std::string& msg);
 
 // after every kernel launch: count it and surface launch errors
 void count_launch();
+void count_launches(int64_t k);  // k launches at once (a CUDA graph replay)
 #define PSI_LAUNCHED()                                                     \
   do {                                                                     \
     ::psi::count_launch();                                                 \

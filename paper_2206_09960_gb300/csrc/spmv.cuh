@@ -172,8 +172,22 @@ __device__ __forceinline__ void seg_join(int lf, T lv, int& rf, T& rv) {  // R <
   rf |= lf;
 }
 
+// An epilogue may declare `static constexpr bool kTileSkip = true` and a member
+// `bool tile_on(int32_t tile) const`: tiles it turns off are neither gathered nor reduced
+// (their rows get no epilogue call).  Used when several independent graphs share one
+// product and some of them have stopped stepping.
+template <typename E, typename = void>
+struct tile_skip_of {
+  static constexpr bool value = false;
+};
+template <typename E>
+struct tile_skip_of<E, decltype((void)E::kTileSkip)> {
+  static constexpr bool value = E::kTileSkip;
+};
+
 template <typename T, typename Epi>
 __global__ void __launch_bounds__(kSpmvThreads) k_spmv(SpmvArgs a, const T* __restrict__ u, Epi epi) {
+  constexpr bool kSkip = tile_skip_of<Epi>::value;
   if (a.state->done) return;
   __shared__ int32_t rp[kSpmvTile + 2];  // row_ptr slice of the tile's rows
   __shared__ T ys[kSpmvTile + 1];        // G(.) of every row that ends in the tile
@@ -200,22 +214,26 @@ __global__ void __launch_bounds__(kSpmvThreads) k_spmv(SpmvArgs a, const T* __re
     }
   };
   T xn[kSpmvItems];
-  if ((int32_t)blockIdx.x < a.num_tiles) gather_tile(blockIdx.x, xn);
+  if (!kSkip && (int32_t)blockIdx.x < a.num_tiles) gather_tile(blockIdx.x, xn);
 
   for (int32_t tile = blockIdx.x; tile < a.num_tiles; tile += gridDim.x) {
+    if constexpr (kSkip) {
+      if (!epi.tile_on(tile)) continue;  // uniform over the block
+    }
     const int64_t nnz0 = (int64_t)tile * kSpmvTile;
     const int64_t nnz1 = nnz0 + kSpmvTile < a.m ? nnz0 + kSpmvTile : a.m;
     const int32_t r0 = a.tile_row[tile];
     const int32_t r_hi = a.tile_row[tile + 1];
     const int32_t nr = r_hi - r0 + 1;  // rows touching [nnz0, nnz0 + tile)
     __syncthreads();                    // shared buffers are reused across tiles
+    if constexpr (kSkip) gather_tile(tile, xn);
     for (int i = threadIdx.x; i <= nr; i += kSpmvThreads) rp[i] = ld_stream(a.row_ptr + r0 + i, pol_s);
     const int64_t p0 = nnz0 + (int64_t)threadIdx.x * kSpmvItems;
     T x[kSpmvItems];
 #pragma unroll
     for (int i = 0; i < kSpmvItems; ++i) x[i] = xn[i];
     const int32_t next = tile + gridDim.x;
-    if (kSpmvPrefetch) {
+    if (kSpmvPrefetch && !kSkip) {
       if (next < a.num_tiles) gather_tile(next, xn);
     } else {
       (void)next;
@@ -285,7 +303,7 @@ __global__ void __launch_bounds__(kSpmvThreads) k_spmv(SpmvArgs a, const T* __re
       if (i == 0 && head_open) carry_head[tile] = ys[0];
       else epi.row(r0 + i, ys[i], gap, pol_s, pol_k);
     }
-    if (!kSpmvPrefetch && next < a.num_tiles) gather_tile(next, xn);
+    if (!kSpmvPrefetch && !kSkip && next < a.num_tiles) gather_tile(next, xn);
   }
   // per-CTA gap partial, fixed order
 #pragma unroll

@@ -25,6 +25,7 @@ _lib = None
 # stream ids used for rates (graph streams live inside psigen.c)
 STREAM_LAMBDA = 101
 STREAM_MU = 102
+STREAM_SIZES = 103
 
 
 def build(force: bool = False) -> str:
@@ -181,3 +182,26 @@ def workload(name: str, seed: int = 0, scale: int | None = None):
         return dict(name=name, n=n, follower=f, leader=l, lam=lam, mu=mu, eps=1e-8,
                     precision="fp32_refine", tol_mode="psi")
     raise ValueError(f"unknown workload {name!r}")
+
+
+def multi_workload(G: int, seed: int = 0, n_lo: int = 1000, n_hi: int = 100_000, mean_degree: float = 12.0,
+                   gamma: float = 2.1):
+    """G independent Chung-Lu graphs: N_q ~ U{n_lo..n_hi}, round(mean_degree * N_q) draws
+    with exponent ``gamma`` (duplicates kept), lambda, mu ~ LogNormal(0, 1) clipped to
+    [1e-3, 1e3].  Graph q uses the seed ``seed * 65536 + q``.  Edge lists (ids local to each
+    graph) and rates are concatenated graph by graph."""
+    u = uniform(seed, STREAM_SIZES, G)
+    n_g = np.minimum(n_lo + np.floor(u * (n_hi - n_lo + 1)).astype(np.int64), n_hi)
+    fs, ls, lams, mus, m_g = [], [], [], [], []
+    for q in range(G):
+        n = int(n_g[q])
+        sq = seed * 65536 + q
+        f, l = chung_lu_graph(n, gamma, int(round(mean_degree * n)), sq)
+        fs.append(f)
+        ls.append(l)
+        m_g.append(len(f))
+        lams.append(lognormal_rates(n, 0.0, 1.0, 1e-3, 1e3, sq, STREAM_LAMBDA))
+        mus.append(lognormal_rates(n, 0.0, 1.0, 1e-3, 1e3, sq, STREAM_MU))
+    return dict(name="multi", G=G, n_g=n_g, m_g=np.asarray(m_g, np.int64),
+                follower=np.concatenate(fs).astype(np.int32), leader=np.concatenate(ls).astype(np.int32),
+                lam=np.concatenate(lams), mu=np.concatenate(mus), eps=1e-8, tol_mode="psi")

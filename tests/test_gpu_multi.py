@@ -1,0 +1,200 @@
+"""Independent graphs solved together (psi_multi_*): every graph must match the FP64 oracle run
+on that graph alone (relative L1 <= 1e-6, top-k identical up to near-ties, the same psi sum)
+and the single-graph GPU path; graphs stop on their own tests (a graph's N enters its psi and
+its tolerance), results are bit-reproducible, and edge cases (no edges, one user, G = 1, the
+step cap) behave as Algorithm 2 says."""
+import numpy as np
+import pytest
+
+import oracle
+import psigen
+
+pytestmark = pytest.mark.gpu
+
+
+def _split(w):
+    """Per-graph (n, follower, leader, lam, mu) of a concatenated workload."""
+    out, eo, no = [], 0, 0
+    for n, m in zip(w["n_g"], w["m_g"]):
+        n, m = int(n), int(m)
+        out.append((n, w["follower"][eo:eo + m], w["leader"][eo:eo + m], w["lam"][no:no + n], w["mu"][no:no + n]))
+        eo += m
+        no += n
+    return out
+
+
+def multi_solve(w, eps=1e-8, k=20, on_device=True, max_iter=20000, solves=1, **kw):
+    import torch
+    from paper_2206_09960_gb300 import Multi
+
+    arrs = [np.ascontiguousarray(w["follower"], np.int32), np.ascontiguousarray(w["leader"], np.int32),
+            np.ascontiguousarray(w["lam"], np.float64), np.ascontiguousarray(w["mu"], np.float64)]
+    if on_device:
+        arrs = [torch.from_numpy(x).cuda() for x in arrs]
+    with Multi(w["n_g"], w["m_g"], *arrs, **kw) as mg:
+        runs = []
+        for _ in range(solves):
+            status, infos = mg.solve(eps, max_iter)
+            psi = mg.scores().cpu().numpy()
+            kk = min(k, int(np.min(w["n_g"])))
+            ids, vals = mg.topk(kk)
+            runs.append(dict(status=status, infos=infos, psi=psi, ids=ids.cpu().numpy(), vals=vals.cpu().numpy()))
+        stats = mg.stats()
+    out = runs[-1]
+    out["stats"] = stats
+    out["runs"] = runs
+    return out
+
+
+def rel_l1(a, b):
+    return float(np.abs(a - b).sum() / np.abs(b).sum())
+
+
+def assert_same_ranking(gpu_ids, psi_ref, tol):
+    ref_ids, _ = oracle.topk(psi_ref, len(gpu_ids))
+    for pos in np.nonzero(gpu_ids != ref_ids)[0]:
+        a, b = psi_ref[gpu_ids[pos]], psi_ref[ref_ids[pos]]
+        assert abs(a - b) <= tol * max(abs(a), abs(b)), (pos, a, b)
+
+
+def _check_against_oracle(w, out, eps=1e-8, bnorm_mode=oracle.BNORM_NONE):
+    off = 0
+    for q, (n, f, l, lam, mu) in enumerate(_split(w)):
+        ref = oracle.solve(n, f, l, lam, mu, to_floor=True, max_iter=5000, bnorm_mode=bnorm_mode)
+        psi = out["psi"][off:off + n]
+        info = out["infos"][q]
+        assert info["converged"], q
+        assert info["gap_scaled"] <= eps, q
+        assert rel_l1(psi, ref["psi"]) <= 1e-6, q
+        # psi sums to the share of users with leaders (an empty wall holds no one's posts)
+        assert abs(info["psi_sum"] - ref["psi"].sum()) <= 1e-6, q
+        assert abs(psi.sum() - ref["psi"].sum()) <= 1e-6, q
+        assert_same_ranking(out["ids"][q], ref["psi"], 1e-6)
+        np.testing.assert_array_equal(out["vals"][q], psi[out["ids"][q]])
+        off += n
+
+
+def test_multi_matches_oracle_per_graph():
+    w = psigen.multi_workload(12, seed=1, n_lo=200, n_hi=3000)
+    out = multi_solve(w)
+    assert out["status"] == "PSI_OK"
+    assert out["stats"]["n"] == int(w["n_g"].sum())
+    _check_against_oracle(w, out)
+    # graphs stop on their own tests: step counts differ between graphs
+    assert len({i["iters"] for i in out["infos"]}) > 1
+
+
+def test_multi_host_inputs_and_bnorm_inf():
+    w = psigen.multi_workload(5, seed=2, n_lo=100, n_hi=2000, mean_degree=6.0)
+    out = multi_solve(w, on_device=False, bnorm_mode="inf")
+    _check_against_oracle(w, out, bnorm_mode=oracle.BNORM_INF)
+    for q, (n, f, l, lam, mu) in enumerate(_split(w)):
+        with oracle.Model(n, f, l, lam, mu) as g:
+            bn = g.bnorm_inf
+        i = out["infos"][q]
+        assert abs(i["gap_psi_bound"] - i["gap_s_l1"] * bn / n) <= 1e-12 * max(1.0, i["gap_psi_bound"])
+
+
+def test_multi_matches_single_graph_path():
+    from test_gpu_parity import gpu_solve
+
+    w = psigen.multi_workload(6, seed=3, n_lo=1000, n_hi=20000)
+    out = multi_solve(w, eps=1e-9)
+    off = 0
+    for q, (n, f, l, lam, mu) in enumerate(_split(w)):
+        one = gpu_solve(n, f, l, lam, mu, 1e-9)
+        assert rel_l1(out["psi"][off:off + n], one["psi"]) <= 1e-8, q
+        # FP32 term sums round differently in the union's tiles than in the graph's own: a
+        # graph whose FP64 check narrowly fails takes one more series and FP64 step
+        assert abs(out["infos"][q]["iters"] - one["info"]["iters"]) <= 2, q
+        off += n
+
+
+def test_multi_deterministic_and_resolve():
+    w = psigen.multi_workload(8, seed=4, n_lo=300, n_hi=5000)
+    out = multi_solve(w, solves=3)
+    a, b, c = out["runs"]
+    for r in (b, c):
+        np.testing.assert_array_equal(a["psi"], r["psi"])
+        np.testing.assert_array_equal(a["ids"], r["ids"])
+        assert [i["iters"] for i in a["infos"]] == [i["iters"] for i in r["infos"]]
+    again = multi_solve(w)
+    np.testing.assert_array_equal(a["psi"], again["psi"])
+
+
+def test_multi_edge_cases():
+    rng = np.random.default_rng(5)
+    # graph 0: no edges; graph 1: one user; graph 2: a two-cycle; graph 3: a small random graph
+    n_g = np.array([5, 1, 2, 300], np.int64)
+    f3 = rng.integers(0, 300, 2000).astype(np.int32)
+    l3 = rng.integers(0, 300, 2000).astype(np.int32)
+    keep = f3 != l3
+    f3, l3 = f3[keep], l3[keep]
+    follower = np.concatenate([np.array([0, 1], np.int32), f3])
+    leader = np.concatenate([np.array([1, 0], np.int32), l3])
+    m_g = np.array([0, 0, 2, len(f3)], np.int64)
+    lam = np.concatenate([psigen.lognormal_rates(int(n), 0.0, 1.0, 1e-3, 1e3, 50 + q, 101) for q, n in enumerate(n_g)])
+    mu = np.concatenate([psigen.lognormal_rates(int(n), 0.0, 1.0, 1e-3, 1e3, 50 + q, 102) for q, n in enumerate(n_g)])
+    w = dict(n_g=n_g, m_g=m_g, follower=follower, leader=leader, lam=lam, mu=mu)
+    out = multi_solve(w, eps=1e-10, k=1)
+    assert out["status"] == "PSI_OK"
+    _check_against_oracle(w, out, eps=1e-10)
+    # no edges: psi = d / N exactly; a graph without rows takes two steps (series + FP64)
+    np.testing.assert_allclose(out["psi"][:5], lam[:5] / (lam[:5] + mu[:5]) / 5, rtol=1e-15)
+    assert out["infos"][0]["iters"] == 2
+    assert out["psi"][5] == lam[5] / (lam[5] + mu[5])
+
+
+def test_multi_single_graph_and_step_cap():
+    from test_gpu_parity import gpu_solve
+
+    w1 = psigen.workload("rmat", seed=6, scale=12)
+    n = w1["n"]
+    w = dict(n_g=np.array([n], np.int64), m_g=np.array([len(w1["follower"])], np.int64),
+             follower=w1["follower"], leader=w1["leader"], lam=w1["lam"], mu=w1["mu"])
+    out = multi_solve(w)
+    one = gpu_solve(n, w1["follower"], w1["leader"], w1["lam"], w1["mu"], 1e-8)
+    assert rel_l1(out["psi"], one["psi"]) <= 1e-8
+    capped = multi_solve(w, max_iter=3)
+    assert capped["status"] == "PSI_ERR_NOT_CONVERGED"
+    assert capped["infos"][0]["iters"] == 3 and not capped["infos"][0]["converged"]
+    one_c = gpu_solve(n, w1["follower"], w1["leader"], w1["lam"], w1["mu"], 1e-8, max_iter=3)
+    assert one_c["info"]["iters"] == 3
+    assert rel_l1(capped["psi"], one_c["psi"]) <= 1e-6
+    # eps >= 1: Algorithm 2 does not enter its loop, psi from s_0 = c
+    flat = multi_solve(w, eps=2.0)
+    assert flat["infos"][0]["iters"] == 0 and flat["status"] == "PSI_OK"
+
+
+def test_multi_errors():
+    from paper_2206_09960_gb300 import PsiError, _binding as B
+
+    n_g = np.array([3, 4], np.int64)
+    m_g = np.array([1, 1], np.int64)
+    lam = np.ones(7)
+    mu = np.ones(7)
+    bad = dict(n_g=n_g, m_g=m_g, follower=np.array([0, 3], np.int32), leader=np.array([1, 4], np.int32),
+               lam=lam, mu=mu)  # graph 1's leader 4 is outside [0, 4)
+    with pytest.raises(PsiError) as e:
+        multi_solve(bad)
+    assert e.value.status == B.PSI_ERR_OUT_OF_RANGE_ID
+    neg = dict(bad, leader=np.array([1, 2], np.int32), lam=np.concatenate([lam[:6], [-1.0]]))
+    with pytest.raises(PsiError) as e:
+        multi_solve(neg)
+    assert e.value.status == B.PSI_ERR_BAD_RATE
+    empty = dict(bad, n_g=np.array([3, 0], np.int64))
+    with pytest.raises(PsiError) as e:
+        multi_solve(empty)
+    assert e.value.status == B.PSI_ERR_INVALID_ARG
+    from paper_2206_09960_gb300 import Multi
+
+    with Multi(n_g, m_g, np.array([0, 1], np.int32), np.array([1, 2], np.int32), lam, mu) as mg:
+        with pytest.raises(PsiError) as e:
+            mg.topk(1)  # before a solve
+        assert e.value.status == B.PSI_ERR_NOT_SOLVED
+        mg.solve(1e-8)
+        with pytest.raises(PsiError) as e:
+            mg.topk(4)  # k above the smallest graph
+        assert e.value.status == B.PSI_ERR_INVALID_ARG
+        ids, _ = mg.topk(3)
+        assert ids.shape == (2, 3)
