@@ -75,6 +75,20 @@ constexpr int kRsItems = 8;
 constexpr int kRsTile = kRsThreads * kRsItems;  // 2048 keys per tile
 constexpr int kRsPerWarp = 32 * kRsItems;       // 256 consecutive keys per warp
 
+// Lanes of the warp holding the same 9-bit digit (256 marks "no item"), from one ballot
+// per digit bit: the lanes that agree with this lane on every bit.  Ballots run on the ALU
+// pipe; the hardware match instruction would serialise on a narrow pipe here.
+__device__ __forceinline__ uint32_t digit_peers(int d) {
+  uint32_t peers = 0xffffffffu;
+#pragma unroll
+  for (int b = 0; b < 9; ++b) {
+    const bool bit = (d >> b) & 1;
+    const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+    peers &= bit ? bal : ~bal;
+  }
+  return peers;
+}
+
 template <typename K>
 __global__ void __launch_bounds__(kRsThreads) k_radix_histo(const K* __restrict__ keys, int64_t n, int shift,
                                                            int64_t num_tiles, uint32_t* __restrict__ counts) {
@@ -127,7 +141,7 @@ __global__ void __launch_bounds__(kRsThreads) k_radix_scatter(const K* __restric
     k[r] = ok ? keys[idx] : K(0);
     if (VALS) v[r] = ok ? vals[idx] : 0u;
     int d = ok ? (int)((uint32_t)(k[r] >> shift) & 0xFFu) : 256;
-    uint32_t peers = __match_any_sync(0xffffffffu, d);
+    uint32_t peers = digit_peers(d);
     uint32_t before = wh[warp][d];
     __syncwarp();
     if ((peers & lt_mask) == 0) wh[warp][d] = before + __popc(peers);
