@@ -284,6 +284,62 @@ def run_multi(args, G=256, plain_sample=32):
     print(json.dumps(line), flush=True)
 
 
+def run_pagerank(args, alpha=0.85, eps=1e-9):
+    """The comparison of the paper's Table IV on the benchmark graph: PageRank's power method
+    (Eq. 22, pi-tolerance eps) against Power-psi with heterogeneous activity and with the
+    homogeneous activity lambda = 0.15, mu = 0.85 that reduces psi to PageRank (both on the
+    s-tolerance eps, the paper's setting), all on one graph handle, solve times only."""
+    import numpy as np
+    import torch
+
+    import psigen
+    import paper_2206_09960_gb300 as psi
+
+    psi.load(build_if_missing=False)
+    w = psigen.workload("rmat", seed=args.seed, scale=args.scale)
+    n = w["n"]
+    dev = [torch.from_numpy(np.ascontiguousarray(w[k])).cuda() for k in ("follower", "leader", "lam", "mu")]
+    hom = [torch.full((n,), 0.15, dtype=torch.float64, device="cuda"),
+           torch.full((n,), 0.85, dtype=torch.float64, device="cuda")]
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        res = None
+        ts = []
+        for rep in range(args.warmup + args.steps):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if rep >= args.warmup:
+                ts.append(e0.elapsed_time(e1) / 1e3)
+        return sum(ts) / len(ts), res
+
+    out = {}
+    with psi.Graph(n, dev[0], dev[1], dev[2], dev[3], tol_mode="s_abs", stream=stream) as g:
+        out["psi_heterogeneous"] = timed(lambda: g.solve(eps, 100000))
+        out["pagerank"] = timed(lambda: g.pagerank(alpha, eps, 100000)[1])
+    with psi.Graph(n, dev[0], dev[1], hom[0], hom[1], tol_mode="s_abs", stream=stream) as g:
+        out["psi_homogeneous"] = timed(lambda: g.solve(eps, 100000))
+        psi_h = g.scores()
+        pi, _ = g.pagerank(alpha, eps, 100000)
+        diff = float((psi_h - pi).abs().sum() / pi.abs().sum())
+    line = {"metric": "Table IV comparison: solve time of PageRank (Eq. 22) and Power-psi at eps=1e-9",
+            "value": out["psi_heterogeneous"][0], "unit": "s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": False, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"rmat_scale{args.scale}_ef16_a.57_b.19_c.19_relabel_lognormal1.5", "n": n,
+                       "alpha": alpha, "eps": eps, "tolerance": "s-tolerance (psi), pi-tolerance (PageRank)"},
+            "psi_heterogeneous_s": out["psi_heterogeneous"][0],
+            "psi_heterogeneous_iters": out["psi_heterogeneous"][1]["iters"],
+            "pagerank_s": out["pagerank"][0], "pagerank_iters": out["pagerank"][1]["iters"],
+            "psi_homogeneous_s": out["psi_homogeneous"][0],
+            "psi_homogeneous_iters": out["psi_homogeneous"][1]["iters"],
+            "homogeneous_psi_vs_pagerank_rel_l1": diff}
+    print(json.dumps(line), flush=True)
+
+
 def run_warmstart(args, n_train=200, eval_scale=23, train_steps=1500):
     """Train the warm-start network on solves of `n_train` seeded R-MAT graphs of scale 16-20
     (the benchmark's rate law), then time Power-psi to eps on a held-out R-MAT graph of scale
@@ -366,7 +422,7 @@ def main():
     ap.add_argument("--eps", type=float, default=1e-8)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="rmat", choices=["rmat", "batch", "warmstart", "multi"],
+    ap.add_argument("--workload", default="rmat", choices=["rmat", "batch", "warmstart", "multi", "pagerank"],
                     help="rmat: the single-graph step (default); batch: 64 activity scenarios on one graph; "
                          "warmstart: train the start-vector network and compare steps and time to eps")
     args = ap.parse_args()
@@ -382,6 +438,9 @@ def main():
         return
     if args.workload == "multi":
         run_multi(args)
+        return
+    if args.workload == "pagerank":
+        run_pagerank(args)
         return
 
     import numpy as np

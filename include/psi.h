@@ -175,6 +175,24 @@ void psi_graph_destroy(psi_graph* g);
 const char* psi_status_string(psi_status s);
 const char* psi_last_error(void);
 
+/*
+ * psi_pagerank -- the PageRank power method of Eq. 22 on the graph's follower structure:
+ * pi_t = alpha * pi_{t-1} W + (1 - alpha)/N, with W the walk from a user to one of its
+ * leaders chosen uniformly (a user without leaders has a zero row: no dangling
+ * redistribution), pi_0 = 1/N, stopped when ||pi_t - pi_{t-1}||_1 <= eps (the paper's
+ * pi-tolerance) or after max_iter steps.  It runs the Power-psi kernels with c = (1-alpha)/N,
+ * mu = alpha, 1/sigma_j = 1/|L(j)| in the handle's precision mode; the graph's rates are not
+ * used.  When every user has the same lambda and mu, psi_solve's psi equals this pi with
+ * alpha = mu/(lambda+mu) (Sec. III).
+ *   alpha: damping factor in [0, 1).  pi_out: n FP64 values in input order, host or device
+ *   (may be NULL).  info: may be NULL; iters, converged, gap_s_l1 = the last pi gap,
+ *   psi_sum = sum of pi.
+ * The handle's psi scores are left as they were; its iterate (psi_get_iterate) is pi's.
+ * Returns OK, NOT_CONVERGED (pi still written) or an error (INVALID_ARG for alpha).
+ */
+psi_status psi_pagerank(psi_graph* g, double alpha, double eps, int32_t max_iter, double* pi_out,
+                        psi_solve_info* info);
+
 /* ------------------------------------------------------------------------------------
  * Scenario batches: S sets of activity rates (lambda, mu) on one follower graph, solved
  * together.  Each scenario is an independent Power-psi problem (Algorithm 2 with its own

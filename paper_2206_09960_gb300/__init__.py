@@ -120,6 +120,18 @@ class Graph:
         out["status"] = B.status_name(st)
         return out
 
+    def pagerank(self, alpha=0.85, eps=1e-9, max_iter=10000, out=None):
+        """PageRank power method (Eq. 22) on this graph's follower structure: returns
+        (pi in input order, info dict).  The graph's psi scores are left as they were."""
+        import torch
+
+        if out is None:
+            out = torch.empty(self.n, dtype=torch.float64, device="cuda")
+        st, info = B.psi_pagerank(self._h, alpha, eps, max_iter, _ptr(out))
+        d = info.as_dict()
+        d["status"] = B.status_name(st)
+        return out, d
+
     def scores(self, out=None):
         """psi of every user (FP64) into ``out`` (tensor/array, host or device) or a new CUDA tensor."""
         import torch

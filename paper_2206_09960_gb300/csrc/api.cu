@@ -214,6 +214,19 @@ psi_status psi_solve(psi_graph* g, double eps, int32_t max_iter, const double* i
   return result;
 }
 
+psi_status psi_pagerank(psi_graph* g, double alpha, double eps, int32_t max_iter, double* pi_out,
+                        psi_solve_info* info) {
+  if (!g) {
+    psi::set_last_error("graph is NULL");
+    return PSI_ERR_INVALID_ARG;
+  }
+  psi_status result = PSI_OK;
+  psi_status st = psi::guarded([&] { result = psi::pagerank(g->g, alpha, eps, max_iter, pi_out, info); });
+  if (st != PSI_OK) return st;
+  if (result == PSI_ERR_NOT_CONVERGED) psi::set_last_error("max_iter reached before the pi-tolerance was met");
+  return result;
+}
+
 psi_status psi_scores(const psi_graph* g, double* psi_out) {
   if (!g || !psi_out) {
     psi::set_last_error("graph or output is NULL");

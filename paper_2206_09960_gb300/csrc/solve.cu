@@ -281,12 +281,11 @@ void ensure_iteration_buffers(Graph& g) {
   g.allocated_iter = true;
 }
 
-static void init_state(Graph& g, cudaStream_t s, double eps, int32_t max_iter) {
+static void init_state(Graph& g, cudaStream_t s, double eps, int32_t max_iter, double scale) {
   DevState h{};
   h.max_iter = max_iter;
   h.eps = eps;
-  const double bn = g.opt.bnorm_mode == PSI_BNORM_INF ? g.bnorm_inf : 1.0;
-  h.scale = bn * (g.opt.tol_mode == PSI_TOL_PSI ? 1.0 / (double)g.n : 1.0);
+  h.scale = scale;
   g.host_state[0] = h;
   PSI_CUDA(cudaMemcpyAsync(g.state.get(), g.host_state, sizeof(DevState), cudaMemcpyHostToDevice, s));
   PSI_CUDA(cudaStreamSynchronize(s));  // the pinned slot is reused below
@@ -303,23 +302,24 @@ static void load_init(Graph& g, cudaStream_t s, const double* init_s, double* s_
 
 // Users without followers have s_t = c for t >= 1; with a warm start their change
 // |c - s_0| belongs to the first step's gap.  Sets s to c there and queues that change.
-static void nonrow_start(Graph& g, cudaStream_t s, double* s64) {
+static void nonrow_start(Graph& g, cudaStream_t s, double* s64, const double* c64) {
   const int64_t n = g.n;
   if (g.n_rows >= n) return;
   const int blocks = 64;
   DBuf<double> part(g.al, blocks);
-  k_nonrow_start<<<blocks, 256, 0, s>>>(s64, g.c64.get(), g.n_rows, n, part.get());
+  k_nonrow_start<<<blocks, 256, 0, s>>>(s64, c64, g.n_rows, n, part.get());
   PSI_LAUNCHED();
   k_set_extra_gap<<<1, 1, 0, s>>>(g.state.get(), part.get(), blocks);
   PSI_LAUNCHED();
 }
 
-psi_status solve(Graph& g, double eps, int32_t max_iter, const double* init_s, psi_solve_info* info) {
+psi_status solve_with(Graph& g, const SolveConsts& K, const SolveTarget& T, double eps, int32_t max_iter,
+                      const double* init_s, psi_solve_info* info) {
   PSI_REQUIRE(max_iter >= 0, PSI_ERR_INVALID_ARG, "max_iter must be >= 0");
   PSI_REQUIRE(!std::isnan(eps), PSI_ERR_INVALID_ARG, "eps is NaN");
   cudaStream_t s = g.stream;
   ensure_iteration_buffers(g);
-  g.solved = false;
+  if (T.final_psi) g.solved = false;
   const int64_t n = g.n;
   const int32_t nX = g.nX;
   const int32_t nR = g.nR;
@@ -331,7 +331,7 @@ psi_status solve(Graph& g, double eps, int32_t max_iter, const double* init_s, p
   cudaEvent_t t0, t1;
   PSI_CUDA(cudaEventCreate(&t0));
   PSI_CUDA(cudaEventCreate(&t1));
-  init_state(g, s, eps, max_iter);
+  init_state(g, s, eps, max_iter, T.scale);
   PSI_CUDA(cudaEventRecord(t0, s));
 
   std::vector<cudaEvent_t> ev;
@@ -353,7 +353,7 @@ psi_status solve(Graph& g, double eps, int32_t max_iter, const double* init_s, p
     double* ub[2] = {g.u64a.get(), g.u64b.get()};
     for (int b = 0; b < 2; ++b) {  // X from s_0 = c, U = c/sigma (s_t = c there for t >= 1)
       fill<double>(ub[b], nu + 1, 0.0, s);
-      k_to_u<double, double><<<eg, 256, 0, s>>>(ub[b], g.c64.get(), g.isig64.get(), nX, nR, 0, nu);
+      k_to_u<double, double><<<eg, 256, 0, s>>>(ub[b], K.c64, K.isig64, nX, nR, 0, nu);
       PSI_LAUNCHED();
     }
     const double* u_first = ub[0];
@@ -361,19 +361,19 @@ psi_status solve(Graph& g, double eps, int32_t max_iter, const double* init_s, p
       load_init(g, s, init_s, sb[0]);
       u0_64.reset(g.al, (size_t)nu + 1);
       fill<double>(u0_64.get(), nu + 1, 0.0, s);
-      k_to_u<double, double><<<eg, 256, 0, s>>>(u0_64.get(), sb[0], g.isig64.get(), nX, nR, 0, nu);
+      k_to_u<double, double><<<eg, 256, 0, s>>>(u0_64.get(), sb[0], K.isig64, nX, nR, 0, nu);
       PSI_LAUNCHED();
-      if (iterate) nonrow_start(g, s, sb[0]);
+      if (iterate) nonrow_start(g, s, sb[0], K.c64);
       u_first = u0_64.get();
     } else {
-      PSI_CUDA(cudaMemcpyAsync(sb[0], g.c64.get(), sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+      PSI_CUDA(cudaMemcpyAsync(sb[0], K.c64, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     }
     PSI_CUDA(cudaMemcpyAsync(sb[1], sb[0], sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     int steps = 0;
     if (iterate) {
       size_t first = ev_phase.size();
       steps = run_phase(g, s, st, [&](int k) {
-        EpiPlain<double> e{g.c64.get(), g.mu64.get(), g.isig64.get(), sb[k & 1], sb[(k + 1) & 1], ub[(k + 1) & 1], nX};
+        EpiPlain<double> e{K.c64, K.mu64, K.isig64, sb[k & 1], sb[(k + 1) & 1], ub[(k + 1) & 1], nX};
         st.step<double>(k == 0 ? u_first : ub[k & 1], e);
       }, batch);
       timed.push_back({first, steps, false});
@@ -385,7 +385,7 @@ psi_status solve(Graph& g, double eps, int32_t max_iter, const double* init_s, p
     float* ub[2] = {g.u32a.get(), g.u32b.get()};
     for (int b = 0; b < 2; ++b) {
       fill<float>(ub[b], nu + 1, 0.0f, s);
-      k_to_u<float, float><<<eg, 256, 0, s>>>(ub[b], g.c32.get(), g.isig32.get(), nX, nR, 0, nu);
+      k_to_u<float, float><<<eg, 256, 0, s>>>(ub[b], K.c32, K.isig32, nX, nR, 0, nu);
       PSI_LAUNCHED();
     }
     const float* u_first = ub[0];
@@ -394,17 +394,17 @@ psi_status solve(Graph& g, double eps, int32_t max_iter, const double* init_s, p
       load_init(g, s, init_s, s0.get());
       DBuf<double> u0(g.al, (size_t)nu + 1);
       fill<double>(u0.get(), nu + 1, 0.0, s);
-      k_to_u<double, double><<<eg, 256, 0, s>>>(u0.get(), s0.get(), g.isig64.get(), nX, nR, 0, nu);
+      k_to_u<double, double><<<eg, 256, 0, s>>>(u0.get(), s0.get(), K.isig64, nX, nR, 0, nu);
       PSI_LAUNCHED();
       u0_32.reset(g.al, (size_t)nu + 1);
       k_convert<float, double><<<eg, 256, 0, s>>>(u0_32.get(), u0.get(), nu + 1);
       PSI_LAUNCHED();
-      if (iterate) nonrow_start(g, s, s0.get());
+      if (iterate) nonrow_start(g, s, s0.get(), K.c64);
       k_convert<float, double><<<eg, 256, 0, s>>>(sb[0], s0.get(), n);
       PSI_LAUNCHED();
       u_first = u0_32.get();
     } else {
-      k_convert<float, double><<<eg, 256, 0, s>>>(sb[0], g.c64.get(), n);
+      k_convert<float, double><<<eg, 256, 0, s>>>(sb[0], K.c64, n);
       PSI_LAUNCHED();
     }
     PSI_CUDA(cudaMemcpyAsync(sb[1], sb[0], sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
@@ -412,7 +412,7 @@ psi_status solve(Graph& g, double eps, int32_t max_iter, const double* init_s, p
     if (iterate) {
       size_t first = ev_phase.size();
       steps = run_phase(g, s, st, [&](int k) {
-        EpiPlain<float> e{g.c32.get(), g.mu32.get(), g.isig32.get(), sb[k & 1], sb[(k + 1) & 1], ub[(k + 1) & 1], nX};
+        EpiPlain<float> e{K.c32, K.mu32, K.isig32, sb[k & 1], sb[(k + 1) & 1], ub[(k + 1) & 1], nX};
         st.step<float>(k == 0 ? u_first : ub[k & 1], e);
       }, batch);
       timed.push_back({first, steps, false});
@@ -426,7 +426,7 @@ psi_status solve(Graph& g, double eps, int32_t max_iter, const double* init_s, p
     float* vb[2] = {g.u32a.get(), g.u32b.get()};
     for (int b = 0; b < 2; ++b) {
       fill<double>(ub[b], nu + 1, 0.0, s);  // U = c/sigma in both FP64 gathered buffers
-      k_to_u<double, double><<<eg, 256, 0, s>>>(ub[b], g.c64.get(), g.isig64.get(), nX, nR, nX, nu);
+      k_to_u<double, double><<<eg, 256, 0, s>>>(ub[b], K.c64, K.isig64, nX, nR, nX, nu);
       PSI_LAUNCHED();
       fill<float>(vb[b], nu + 1, 0.0f, s);  // series terms of U users vanish after the first
     }
@@ -439,15 +439,15 @@ psi_status solve(Graph& g, double eps, int32_t max_iter, const double* init_s, p
       load_init(g, s, init_s, s64);
       u0_64.reset(g.al, (size_t)nu + 1);
       fill<double>(u0_64.get(), nu + 1, 0.0, s);
-      k_to_u<double, double><<<eg, 256, 0, s>>>(u0_64.get(), s64, g.isig64.get(), nX, nR, 0, nu);
+      k_to_u<double, double><<<eg, 256, 0, s>>>(u0_64.get(), s64, K.isig64, nX, nR, 0, nu);
       PSI_LAUNCHED();
-      if (iterate) nonrow_start(g, s, s64);
+      if (iterate) nonrow_start(g, s, s64, K.c64);
       u_resid_in = u0_64.get();  // the first step is an FP64 step from s_0
       resid_first = true;
     } else {
-      PSI_CUDA(cudaMemcpyAsync(s64, g.c64.get(), sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+      PSI_CUDA(cudaMemcpyAsync(s64, K.c64, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
       // the first series term is c itself: v0 = c/sigma on X and U
-      k_to_u<float, float><<<eg, 256, 0, s>>>(v0, g.c32.get(), g.isig32.get(), nX, nR, 0, nu);
+      k_to_u<float, float><<<eg, 256, 0, s>>>(v0, K.c32, K.isig32, nX, nR, 0, nu);
       PSI_LAUNCHED();
     }
     bool v0_u_cleared = false;
@@ -458,7 +458,7 @@ psi_status solve(Graph& g, double eps, int32_t max_iter, const double* init_s, p
           size_t first = ev_phase.size();
           int steps = run_phase(g, s, st, [&](int k) {
             const float* vin = (k == 0) ? v0 : vb[(k + 1) & 1];
-            EpiSeries e{g.mu32.get(), g.isig32.get(), s64, vb[k & 1], nX};
+            EpiSeries e{K.mu32, K.isig32, s64, vb[k & 1], nX};
             st.step<float>(vin, e);
           }, batch);
           timed.push_back({first, steps, false});
@@ -466,7 +466,7 @@ psi_status solve(Graph& g, double eps, int32_t max_iter, const double* init_s, p
           DevState h = read_state(g, s);
           if (!h.converged) break;  // the step cap came first
           // FP64 gathered vector of the series' s64 (X users; U hold c/sigma)
-          k_to_u<double, double><<<eg, 256, 0, s>>>(ub[cur_u], s64, g.isig64.get(), nX, nR, 0, nX);
+          k_to_u<double, double><<<eg, 256, 0, s>>>(ub[cur_u], s64, K.isig64, nX, nR, 0, nX);
           PSI_LAUNCHED();
           u_current = true;
           u_resid_in = ub[cur_u];
@@ -480,7 +480,7 @@ psi_status solve(Graph& g, double eps, int32_t max_iter, const double* init_s, p
         size_t first = ev_phase.size();
         double* u_out = ub[cur_u ^ 1];
         DevState h = run_single(g, s, st, [&]() {
-          EpiResid e{g.c64.get(), g.mu64.get(), g.isig64.get(), s64, u_out, v0, nX};
+          EpiResid e{K.c64, K.mu64, K.isig64, s64, u_out, v0, nX};
           st.step<double>(u_resid_in, e);
         });
         timed.push_back({first, h.phase_iters, true});
@@ -492,7 +492,7 @@ psi_status solve(Graph& g, double eps, int32_t max_iter, const double* init_s, p
       }
     }
     if (!u_current) {  // psi from the current s64 (after a capped series, or no loop)
-      k_to_u<double, double><<<eg, 256, 0, s>>>(ub[cur_u], s64, g.isig64.get(), nX, nR, 0, nX);
+      k_to_u<double, double><<<eg, 256, 0, s>>>(ub[cur_u], s64, K.isig64, nX, nR, 0, nX);
       PSI_LAUNCHED();
     }
     g.last_s_kind = 0;
@@ -510,20 +510,29 @@ psi_status solve(Graph& g, double eps, int32_t max_iter, const double* init_s, p
     PSI_CUDA(cudaMemcpyAsync(g.state.get(), &g.host_state[1], sizeof(DevState), cudaMemcpyHostToDevice, s));
   }
   st.phase_step = 0;
-  if (u_final64) {
-    EpiFinal<double> e{g.lam64.get(), g.d64.get(), g.psi64.get(), (double)n};
-    st.step<double>(u_final64, e);
+  if (T.final_psi) {
+    if (u_final64) {
+      EpiFinal<double> e{K.lam64, K.d64, T.out, (double)n};
+      st.step<double>(u_final64, e);
+    } else {
+      EpiFinal<float> e{K.lam64, K.d64, T.out, (double)n};
+      st.step<float>(u_final32, e);
+    }
+    if (g.n_rows < n) {
+      k_psi_nonrow<<<elementwise_grid(n - g.n_rows), 256, 0, s>>>(T.out, K.d64, g.n_rows, n);
+      PSI_LAUNCHED();
+    }
+  } else if (g.last_s_kind <= 1) {  // the result is the iterate itself
+    const double* sp = g.last_s_kind == 0 ? g.s64.get() : g.s64b.get();
+    PSI_CUDA(cudaMemcpyAsync(T.out, sp, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   } else {
-    EpiFinal<float> e{g.lam64.get(), g.d64.get(), g.psi64.get(), (double)n};
-    st.step<float>(u_final32, e);
-  }
-  if (g.n_rows < n) {
-    k_psi_nonrow<<<elementwise_grid(n - g.n_rows), 256, 0, s>>>(g.psi64.get(), g.d64.get(), g.n_rows, n);
+    const float* sp = g.last_s_kind == 2 ? g.s32a.get() : g.s32b.get();
+    k_convert<double, float><<<eg, 256, 0, s>>>(T.out, sp, n);
     PSI_LAUNCHED();
   }
   PSI_CUDA(cudaEventRecord(t1, s));
   DBuf<double> dsum(g.al, 1);
-  sum_f64(g.psi64.get(), n, dsum.get(), g.al, s);
+  sum_f64(T.out, n, dsum.get(), g.al, s);
   PSI_CUDA(cudaMemcpyAsync(&g.host_state[0].gap, dsum.get(), sizeof(double), cudaMemcpyDeviceToHost, s));
   PSI_CUDA(cudaStreamSynchronize(s));
   const double psi_sum = g.host_state[0].gap;
@@ -549,7 +558,7 @@ psi_status solve(Graph& g, double eps, int32_t max_iter, const double* init_s, p
   for (auto e : ev) cudaEventDestroy(e);
   cudaEventDestroy(t0);
   cudaEventDestroy(t1);
-  g.solved = true;
+  if (T.final_psi) g.solved = true;
   if (info) {
     info->iters = h.total_iters;
     info->converged = iterate ? h.converged : 1;
@@ -557,7 +566,7 @@ psi_status solve(Graph& g, double eps, int32_t max_iter, const double* init_s, p
     info->spmv_launches = h.total_iters + 1;
     info->gap_s_l1 = h.gap;
     info->gap_scaled = h.gap_scaled;
-    info->gap_psi_bound = h.gap * g.bnorm_inf / (double)n;
+    info->gap_psi_bound = T.final_psi ? h.gap * g.bnorm_inf / (double)n : h.gap;
     info->psi_sum = psi_sum;
     info->ms = ms;
     info->spmv_ms = spmv_ms;
@@ -567,6 +576,18 @@ psi_status solve(Graph& g, double eps, int32_t max_iter, const double* init_s, p
   }
   if (!iterate) return PSI_OK;  // Algorithm 2 with gap = 1 <= eps: psi from s_0
   return h.converged ? PSI_OK : PSI_ERR_NOT_CONVERGED;
+}
+
+SolveConsts graph_consts(const Graph& g) {
+  return SolveConsts{g.c64.get(), g.mu64.get(), g.isig64.get(), g.lam64.get(), g.d64.get(),
+                     g.c32.get(), g.mu32.get(), g.isig32.get()};
+}
+
+psi_status solve(Graph& g, double eps, int32_t max_iter, const double* init_s, psi_solve_info* info) {
+  ensure_iteration_buffers(g);
+  const double bn = g.opt.bnorm_mode == PSI_BNORM_INF ? g.bnorm_inf : 1.0;
+  const SolveTarget T{bn * (g.opt.tol_mode == PSI_TOL_PSI ? 1.0 / (double)g.n : 1.0), g.psi64.get(), true};
+  return solve_with(g, graph_consts(g), T, eps, max_iter, init_s, info);
 }
 
 }  // namespace psi

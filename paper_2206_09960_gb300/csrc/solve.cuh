@@ -7,6 +7,25 @@ namespace psi {
 
 void ensure_iteration_buffers(Graph& g);
 psi_status solve(Graph& g, double eps, int32_t max_iter, const double* init_s, psi_solve_info* info);
+
+// The per-user constants one run of the iteration uses (internal order, device): c, mu,
+// 1/sigma in FP64 and FP32, lambda and d for the final product.
+struct SolveConsts {
+  const double *c64, *mu64, *isig64, *lam64, *d64;
+  const float *c32, *mu32, *isig32;
+};
+// scale: the stop test is scale * ||s_t - s_{t-1}||_1 <= eps.  final_psi: out = the final
+// product of Algorithm 2 (and the handle's scores are replaced); otherwise out = s itself.
+struct SolveTarget {
+  double scale;
+  double* out;  // internal order, n values
+  bool final_psi;
+};
+SolveConsts graph_consts(const Graph& g);
+// PageRank power method (Eq. 22) on the graph's follower structure (pagerank.cu)
+psi_status pagerank(Graph& g, double alpha, double eps, int32_t max_iter, double* pi_out, psi_solve_info* info);
+psi_status solve_with(Graph& g, const SolveConsts& K, const SolveTarget& T, double eps, int32_t max_iter,
+                      const double* init_s, psi_solve_info* info);
 // top k of psi64 by (psi desc, input id asc); ids/vals device buffers of k entries
 void topk(const Graph& g, int32_t k, int32_t* d_ids, double* d_vals);
 // the same ranking of any psi vector in internal order (ids reported through perm)
