@@ -13,8 +13,10 @@
 //     load-balanced product over that follower-grouped CSR;
 //  5. per-user constants c, d, 1/sigma in FP64 and FP32; ||B||_inf = max_j beta_j/sigma_j;
 //  6. the merge-path tile schedule of the sparse product.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "primitives.cuh"
 #include "solve.cuh"
@@ -50,9 +52,11 @@ __global__ void k_check_rates(const double* __restrict__ lam, const double* __re
 // Validates every edge and marks, exactly, who has followers (has_fol) and who has leaders
 // (has_lead) with plain byte stores.  Degrees are only an ordering key for locality: they
 // are counted on every `stride`-th edge (all edges when stride == 1).
-__global__ void k_edges(const int32_t* __restrict__ f, const int32_t* __restrict__ l, int64_t m, int64_t n,
-                        int drop_self, int64_t stride, uint8_t* has_fol, uint8_t* has_lead, uint32_t* in_deg,
-                        uint32_t* out_deg, uint32_t* err) {
+// Runs on edges [e_base, e_base + m) (f and l point at edge e_base), so that the edges can
+// be validated chunk by chunk as they arrive; the sample rule uses the global edge index.
+__global__ void k_edges(const int32_t* __restrict__ f, const int32_t* __restrict__ l, int64_t m, int64_t e_base,
+                        int64_t n, int drop_self, int64_t stride, uint8_t* has_fol, uint8_t* has_lead,
+                        uint32_t* in_deg, uint32_t* out_deg, uint32_t* err) {
   uint32_t bits = 0;
   GRID_STRIDE(e, m) {
     int32_t a = f[e], b = l[e];
@@ -60,7 +64,7 @@ __global__ void k_edges(const int32_t* __restrict__ f, const int32_t* __restrict
     if (a == b) { if (!drop_self) bits |= kErrSelf; continue; }
     has_lead[a] = 1;
     has_fol[b] = 1;
-    if (e % stride == 0) {
+    if ((e_base + e) % stride == 0) {
       atomicAdd(&out_deg[a], 1u);
       atomicAdd(&in_deg[b], 1u);
     }
@@ -361,32 +365,75 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
   PSI_CUDA(cudaEventCreate(&t1));
   PSI_CUDA(cudaEventRecord(t0, s));
 
-  // ---- stage inputs (host pointers are copied; device pointers are read in place)
+  // ---- stage inputs (host pointers are copied; device pointers are read in place).  Host
+  //      copies run on a private stream, the rates first, then the edges in chunks; the
+  //      validation pass (step 1) takes each chunk as soon as it has arrived, so it overlaps
+  //      the transfer.
   DBuf<int32_t> fbuf, lbuf;
   DBuf<double> lam_buf, mu_buf;
   const int32_t* df = follower;
   const int32_t* dl = leader;
   const double* dlam = lambda;
   const double* dmu = mu;
-  if (m > 0 && !is_device_pointer(follower)) {
+  const bool f_host = m > 0 && !is_device_pointer(follower);
+  const bool l_host = m > 0 && !is_device_pointer(leader);
+  const bool lam_host = !is_device_pointer(lambda);
+  const bool mu_host = !is_device_pointer(mu);
+  if (f_host) {
     fbuf.reset(al, (size_t)m);
-    copy_in(fbuf.get(), follower, sizeof(int32_t) * m, s);
     df = fbuf.get();
   }
-  if (m > 0 && !is_device_pointer(leader)) {
+  if (l_host) {
     lbuf.reset(al, (size_t)m);
-    copy_in(lbuf.get(), leader, sizeof(int32_t) * m, s);
     dl = lbuf.get();
   }
-  if (!is_device_pointer(lambda)) {
+  if (lam_host) {
     lam_buf.reset(al, (size_t)n);
-    copy_in(lam_buf.get(), lambda, sizeof(double) * n, s);
     dlam = lam_buf.get();
   }
-  if (!is_device_pointer(mu)) {
+  if (mu_host) {
     mu_buf.reset(al, (size_t)n);
-    copy_in(mu_buf.get(), mu, sizeof(double) * n, s);
     dmu = mu_buf.get();
+  }
+  const bool any_host = f_host || l_host || lam_host || mu_host;
+  cudaStream_t cs = nullptr;
+  std::vector<cudaEvent_t> arrived;  // [0]: buffers ready, [1]: rates arrived, [2 + c]: edge chunk c
+  const int64_t chunk = (int64_t)1 << 25;
+  const int64_t n_chunks = m > 0 ? ceil_div(m, chunk) : 0;
+  auto release_copies = [&]() {
+    if (cs) cudaStreamSynchronize(cs);
+    for (cudaEvent_t e : arrived) cudaEventDestroy(e);
+    arrived.clear();
+    if (cs) cudaStreamDestroy(cs);
+    cs = nullptr;
+  };
+  struct CopyGuard {
+    decltype(release_copies)& f;
+    ~CopyGuard() { f(); }
+  } copy_guard{release_copies};  // waits for the copies before the staging buffers go
+  if (any_host) {
+    PSI_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaEvent_t ready;
+    PSI_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    arrived.push_back(ready);  // the staging buffers exist (stream-ordered allocation on s)
+    PSI_CUDA(cudaEventRecord(ready, s));
+    PSI_CUDA(cudaStreamWaitEvent(cs, ready, 0));
+    if (lam_host) PSI_CUDA(cudaMemcpyAsync(lam_buf.get(), lambda, sizeof(double) * n, cudaMemcpyHostToDevice, cs));
+    if (mu_host) PSI_CUDA(cudaMemcpyAsync(mu_buf.get(), mu, sizeof(double) * n, cudaMemcpyHostToDevice, cs));
+    cudaEvent_t ev;
+    PSI_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    arrived.push_back(ev);
+    PSI_CUDA(cudaEventRecord(ev, cs));
+    for (int64_t c = 0; c < n_chunks; ++c) {
+      const int64_t e0 = c * chunk, len = std::min(chunk, m - e0);
+      if (f_host)
+        PSI_CUDA(cudaMemcpyAsync(fbuf.get() + e0, follower + e0, sizeof(int32_t) * len, cudaMemcpyHostToDevice, cs));
+      if (l_host)
+        PSI_CUDA(cudaMemcpyAsync(lbuf.get() + e0, leader + e0, sizeof(int32_t) * len, cudaMemcpyHostToDevice, cs));
+      PSI_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+      arrived.push_back(ev);
+      PSI_CUDA(cudaEventRecord(ev, cs));
+    }
   }
 
   // ---- 1. validation and raw degrees
@@ -398,14 +445,19 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
   PSI_CUDA(cudaMemsetAsync(out_deg.get(), 0, sizeof(uint32_t) * n, s));
   PSI_CUDA(cudaMemsetAsync(has_fol.get(), 0, n, s));
   PSI_CUDA(cudaMemsetAsync(has_lead.get(), 0, n, s));
+  if (any_host) PSI_CUDA(cudaStreamWaitEvent(s, arrived[1], 0));
   k_check_rates<<<grid_for(n), 256, 0, s>>>(dlam, dmu, n, err.get());
   PSI_LAUNCHED();
   if (m > 0) {
     // degree sample: every edge up to 2^26 edges, then a fixed 1-in-k subset
     const int64_t stride = m > ((int64_t)1 << 26) ? (m >> 26) + 1 : 1;
-    k_edges<<<grid_for(m), 256, 0, s>>>(df, dl, m, n, g.opt.self_loops == PSI_DROP ? 1 : 0, stride, has_fol.get(),
-                                        has_lead.get(), in_deg.get(), out_deg.get(), err.get());
-    PSI_LAUNCHED();
+    for (int64_t c = 0; c < n_chunks; ++c) {
+      const int64_t e0 = c * chunk, len = std::min(chunk, m - e0);
+      if (any_host) PSI_CUDA(cudaStreamWaitEvent(s, arrived[2 + c], 0));
+      k_edges<<<grid_for(len), 256, 0, s>>>(df + e0, dl + e0, len, e0, n, g.opt.self_loops == PSI_DROP ? 1 : 0, stride,
+                                            has_fol.get(), has_lead.get(), in_deg.get(), out_deg.get(), err.get());
+      PSI_LAUNCHED();
+    }
   }
   const uint32_t ebits = read1(err.get(), s);
   PSI_REQUIRE(!(ebits & kErrId), PSI_ERR_OUT_OF_RANGE_ID, "an edge endpoint is outside [0, n)");
