@@ -71,9 +71,9 @@ __global__ void k_scan_down(const uint32_t* in, uint32_t* out, int64_t n,
 // ---------------------------------------------------------------- radix sort
 constexpr int kRsThreads = 256;
 constexpr int kRsWarps = kRsThreads / 32;
-constexpr int kRsItems = 8;
-constexpr int kRsTile = kRsThreads * kRsItems;  // 2048 keys per tile
-constexpr int kRsPerWarp = 32 * kRsItems;       // 256 consecutive keys per warp
+constexpr int kRsItems = 12;                    // measured: 12 beats 8 and 16 on the 537M-key edge sort
+constexpr int kRsTile = kRsThreads * kRsItems;  // 3072 keys per tile
+constexpr int kRsPerWarp = 32 * kRsItems;       // 384 consecutive keys per warp
 
 // Lanes of the warp holding the same 9-bit digit (256 marks "no item"), from one ballot
 // per digit bit: the lanes that agree with this lane on every bit.  Ballots run on the ALU
