@@ -448,6 +448,7 @@ def main():
 
     import psigen
     import paper_2206_09960_gb300 as psi
+    from paper_2206_09960_gb300 import shard
 
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
@@ -485,11 +486,7 @@ def main():
         torch.cuda.synchronize()
 
     def max_over_ranks(x):
-        if ws == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
+        return shard.max_over_ranks(x, device="cuda")
 
     dev_in = (f_d, l_d, lam_d, mu_d)
     host_in = (f_h, l_h, lam_h, mu_h)
