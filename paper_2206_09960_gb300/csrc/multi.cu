@@ -11,8 +11,9 @@
 //   * every step pair is one series product (rows of SERIES graphs) and one FP64 product
 //     (rows of CONFIRM graphs); tiles holding no row of a graph in the product's phase are
 //     skipped, so a graph that is waiting or done costs nothing;
-//   * the epilogues write one gap entry per row, one block per graph sums its rows in a
-//     fixed order and moves the graph between phases (bit-reproducible);
+//   * the epilogues write one gap entry per row; fixed slices of each graph's rows are summed
+//     by their own blocks and one block adds each graph's slice sums in order and moves the
+//     graph between phases (bit-reproducible);
 //   * the step pairs are captured once into a CUDA graph and replayed until every graph is
 //     DONE, with no host work between steps.
 #include <algorithm>
@@ -47,7 +48,7 @@ struct MState {
   int32_t n_series;
   int32_t n_confirm;
   int32_t max_iter;
-  uint32_t ticket;  // blocks of the current k_group_step that have finished
+  int32_t pad0_;
   double eps;
   int32_t all_done;
   int32_t pad_;
@@ -134,94 +135,100 @@ struct EpiFinalM {
 };
 
 // ---------------------------------------------------------------- per-graph stop test
-// One block per graph.  A graph in the step's phase sums its gap entries over its X and
-// R row ranges (fixed order), counts the step and moves on:
+// Two kernels per step.  k_group_partial: kGapSlices blocks per graph; block (g, b) sums
+// the gap entries of slice b of graph g's rows (its X range, then its R range, cut into
+// kGapSlices equal slices) with several loads in flight per thread.  k_group_step: one
+// block; thread g adds graph g's slice sums in order, counts the step and moves the graph:
 //   series (mode 0): test met and steps < max_iter -> CONFIRM; steps >= max_iter -> DONE;
-//   FP64   (mode 1): test met -> DONE, converged; steps >= max_iter -> DONE; else SERIES.
-// The last block to finish recounts the phases into the prefix counts and the gates.
-__global__ void __launch_bounds__(256) k_group_step(int mode, MState* st, DevState* gate, const int4* __restrict__ ranges,
-                                                   const double* __restrict__ gap_row, int32_t* phase, int32_t* iters,
-                                                   int32_t* converged, int32_t* refinements, double* gap_last,
-                                                   const double* __restrict__ scale, int32_t* cnt_series,
-                                                   int32_t* cnt_confirm, int G) {
-  if (gate[mode].done) return;  // uniform: the gates change only in the last block below
+//   FP64   (mode 1): test met -> DONE, converged; steps >= max_iter -> DONE; else SERIES;
+// then the block recounts the phases into the prefix counts and the gates.
+constexpr int kGapSlices = 8;
+
+__global__ void __launch_bounds__(256) k_group_partial(int mode, const DevState* gate, const int4* __restrict__ ranges,
+                                                      const double* __restrict__ gap_row,
+                                                      const int32_t* __restrict__ phase, double* part) {
+  if (gate[mode].done) return;
+  const int g = blockIdx.x / kGapSlices, b = blockIdx.x % kGapSlices;
+  if (phase[g] != (mode == 0 ? kSeries : kConfirm)) return;
   __shared__ double sh[256];
-  __shared__ int32_t last;
-  const int g = blockIdx.x;
-  const int32_t want = mode == 0 ? kSeries : kConfirm;
-  if (phase[g] == want) {
-    const int4 rg = ranges[g];
-    double acc = 0.0;
-    for (int32_t r = rg.x + threadIdx.x; r < rg.y; r += blockDim.x) acc += gap_row[r];
-    for (int32_t r = rg.z + threadIdx.x; r < rg.w; r += blockDim.x) acc += gap_row[r];
-    sh[threadIdx.x] = acc;
+  const int4 rg = ranges[g];
+  const int64_t nx = rg.y - rg.x, total = nx + (rg.w - rg.z);
+  const int64_t lo = total * b / kGapSlices, hi = total * (b + 1) / kGapSlices;
+  auto at = [&](int64_t v) { return v < nx ? gap_row[rg.x + v] : gap_row[rg.z + (v - nx)]; };
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int64_t v = lo + threadIdx.x;
+  for (; v + 768 < hi; v += 1024) {
+    a0 += at(v);
+    a1 += at(v + 256);
+    a2 += at(v + 512);
+    a3 += at(v + 768);
+  }
+  for (; v < hi; v += 256) a0 += at(v);
+  sh[threadIdx.x] = (a0 + a1) + (a2 + a3);
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
     __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-      if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-      const double gap = sh[0];
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void __launch_bounds__(1024) k_group_step(int mode, MState* st, DevState* gate,
+                                                    const double* __restrict__ part, int32_t* phase, int32_t* iters,
+                                                    int32_t* converged, int32_t* refinements, double* gap_last,
+                                                    const double* __restrict__ scale, int32_t* cnt_series,
+                                                    int32_t* cnt_confirm, int G) {
+  if (gate[mode].done) return;
+  __shared__ int32_t ws[2][32];
+  const int g = threadIdx.x;
+  int32_t p = kDone;
+  if (g < G) {
+    p = phase[g];
+    if (p == (mode == 0 ? kSeries : kConfirm)) {
+      double gap = 0.0;
+      for (int b = 0; b < kGapSlices; ++b) gap += part[g * kGapSlices + b];
       gap_last[g] = gap;
       const int32_t it = iters[g] + 1;
       iters[g] = it;
       const bool met = gap * scale[g] <= st->eps;
-      int32_t next;
       if (mode == 0) {
-        next = (met && it < st->max_iter) ? kConfirm : (it >= st->max_iter ? kDone : kSeries);
+        p = (met && it < st->max_iter) ? kConfirm : (it >= st->max_iter ? kDone : kSeries);
       } else {
         refinements[g] += 1;
         if (met) converged[g] = 1;
-        next = met || it >= st->max_iter ? kDone : kSeries;
+        p = met || it >= st->max_iter ? kDone : kSeries;
       }
-      phase[g] = next;
+      phase[g] = p;
     }
   }
-  // last block: prefix counts of the new phases and the gates
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    last = atomicAdd(&st->ticket, 1u) == (uint32_t)G - 1 ? 1 : 0;
-  }
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  __shared__ int32_t ws[2][8];
-  const int per = (G + 255) / 256;  // G <= 1024: at most 4 graphs per thread
-  const int lo = threadIdx.x * per;
-  int32_t a = 0, b = 0;
-  int32_t pa[4], pb[4];
-  for (int q = 0; q < per; ++q) {
-    const int gg = lo + q;
-    int32_t p = kDone;
-    if (gg < G) p = ((volatile int32_t*)phase)[gg];
-    pa[q] = a;
-    pb[q] = b;
-    a += p == kSeries;
-    b += p == kConfirm;
-  }
-  // block-wide exclusive scan of (a, b)
+  // exclusive prefix counts of the new phases over the graphs, block-wide
+  const int32_t a = p == kSeries, c = p == kConfirm;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int32_t ia = a, ib = b;
+  int32_t ia = a, ic = c;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const int32_t ua = __shfl_up_sync(0xffffffffu, ia, o), ub = __shfl_up_sync(0xffffffffu, ib, o);
-    if (lane >= o) { ia += ua; ib += ub; }
-  }
-  if (lane == 31) { ws[0][warp] = ia; ws[1][warp] = ib; }
-  __syncthreads();
-  int32_t oa = 0, ob = 0;
-  for (int w = 0; w < warp; ++w) { oa += ws[0][w]; ob += ws[1][w]; }
-  const int32_t ea = oa + ia - a, eb = ob + ib - b;  // exclusive prefix of this thread
-  for (int q = 0; q < per; ++q) {
-    const int gg = lo + q;
-    if (gg < G) {
-      cnt_series[gg] = ea + pa[q];
-      cnt_confirm[gg] = eb + pb[q];
+    const int32_t ua = __shfl_up_sync(0xffffffffu, ia, o), uc = __shfl_up_sync(0xffffffffu, ic, o);
+    if (lane >= o) {
+      ia += ua;
+      ic += uc;
     }
   }
-  if (threadIdx.x == 255) {
-    const int32_t ns = oa + ia, nc = ob + ib;
+  if (lane == 31) {
+    ws[0][warp] = ia;
+    ws[1][warp] = ic;
+  }
+  __syncthreads();
+  int32_t oa = 0, oc = 0;
+  for (int w = 0; w < warp; ++w) {
+    oa += ws[0][w];
+    oc += ws[1][w];
+  }
+  if (g < G) {
+    cnt_series[g] = oa + ia - a;
+    cnt_confirm[g] = oc + ic - c;
+  }
+  if (g == (int)blockDim.x - 1) {
+    const int32_t ns = oa + ia, nc = oc + ic;
     cnt_series[G] = ns;
     cnt_confirm[G] = nc;
     st->n_series = ns;
@@ -229,7 +236,6 @@ __global__ void __launch_bounds__(256) k_group_step(int mode, MState* st, DevSta
     st->all_done = (ns == 0 && nc == 0) ? 1 : 0;
     gate[0].done = ns == 0 ? 1 : 0;
     gate[1].done = nc == 0 ? 1 : 0;
-    st->ticket = 0;
   }
 }
 
@@ -391,6 +397,7 @@ struct Multi {
   // loop state
   DBuf<int32_t> phase, iters, converged, refinements, cnt_series, cnt_confirm;
   DBuf<double> gap_last;
+  DBuf<double> gap_part;               // [G][kGapSlices] slice sums of the per-row gaps
   DBuf<MState> st;
   DBuf<DevState> gate;                 // [3]
   MState* host = nullptr;              // pinned, 2 slots
@@ -539,6 +546,7 @@ void multi_buffers(Multi& M) {
   M.cnt_series.reset(al, G + 1);
   M.cnt_confirm.reset(al, G + 1);
   M.gap_last.reset(al, G);
+  M.gap_part.reset(al, G * kGapSlices);
   M.st.reset(al, 1);
   M.gate.reset(al, 3);
   if (!M.host) PSI_CUDA(cudaMallocHost((void**)&M.host, 2 * sizeof(MState)));
@@ -611,11 +619,16 @@ int multi_product(Multi& M, cudaStream_t s, const T* u, const Epi& epi, const De
 }
 
 int group_step(Multi& M, cudaStream_t s, int mode) {
-  k_group_step<<<M.G, 256, 0, s>>>(mode, M.st.get(), M.gate.get(), M.ranges.get(), M.gap_row.get(), M.phase.get(),
-                                   M.iters.get(), M.converged.get(), M.refinements.get(), M.gap_last.get(),
-                                   M.scale.get(), M.cnt_series.get(), M.cnt_confirm.get(), M.G);
+  k_group_partial<<<M.G * kGapSlices, 256, 0, s>>>(mode, M.gate.get(), M.ranges.get(), M.gap_row.get(), M.phase.get(),
+                                                   M.gap_part.get());
   PSI_LAUNCHED();
-  return 1;
+  // gate[mode] is read before any thread writes a gate (only the last thread does, after
+  // the block's barrier), and all threads of the block see the same value
+  k_group_step<<<1, 1024, 0, s>>>(mode, M.st.get(), M.gate.get(), M.gap_part.get(), M.phase.get(), M.iters.get(),
+                                  M.converged.get(), M.refinements.get(), M.gap_last.get(), M.scale.get(),
+                                  M.cnt_series.get(), M.cnt_confirm.get(), M.G);
+  PSI_LAUNCHED();
+  return 2;
 }
 
 // One step pair: a series step of the SERIES graphs reading v_in and writing v_out, their
