@@ -265,6 +265,14 @@ def run_multi(args, G=256, plain_sample=32):
 
     launches0 = psi._binding.load().psi_kernel_launches()
     t_multi, (status, infos, st) = timed(together, args.steps)
+    if args.profile_solve:  # one more solve of the built object inside a profiler range (for ncu)
+        with psi.Multi(n_g, m_g, *dev, stream=stream) as mg:
+            mg.solve(args.eps, 100000)
+            torch.cuda.synchronize()
+            torch.cuda.profiler.start()
+            mg.solve(args.eps, 100000)
+            torch.cuda.synchronize()
+            torch.cuda.profiler.stop()
     launches = (psi._binding.load().psi_kernel_launches() - launches0) / (args.warmup + args.steps)
     t_plain, pinfos = timed(plain, 1)
     share = float(m_g[sample].sum()) / float(m_g.sum())
@@ -421,6 +429,8 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--eps", type=float, default=1e-8)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--profile-solve", action="store_true",
+                    help="multi workload: run one extra solve between cudaProfilerStart/Stop (ncu --profile-from-start off)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="rmat", choices=["rmat", "batch", "warmstart", "multi", "pagerank"],
                     help="rmat: the single-graph step (default); batch: 64 activity scenarios on one graph; "
