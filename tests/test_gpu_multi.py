@@ -145,6 +145,19 @@ def test_multi_edge_cases():
     assert out["psi"][5] == lam[5] / (lam[5] + mu[5])
 
 
+def test_multi_all_graphs_without_edges():
+    n_g = np.array([3, 1, 7], np.int64)
+    lam = psigen.lognormal_rates(11, 0.0, 1.0, 1e-3, 1e3, 77, 101)
+    mu = psigen.lognormal_rates(11, 0.0, 1.0, 1e-3, 1e3, 77, 102)
+    w = dict(n_g=n_g, m_g=np.zeros(3, np.int64), follower=np.zeros(0, np.int32), leader=np.zeros(0, np.int32),
+             lam=lam, mu=mu)
+    out = multi_solve(w, k=1)
+    assert out["status"] == "PSI_OK"
+    nn = np.repeat(n_g, n_g).astype(np.float64)
+    np.testing.assert_allclose(out["psi"], lam / (lam + mu) / nn, rtol=1e-15)
+    assert [i["iters"] for i in out["infos"]] == [2, 2, 2]
+
+
 def test_multi_single_graph_and_step_cap():
     from test_gpu_parity import gpu_solve
 
