@@ -67,6 +67,8 @@ class Graph:
     ``follower[k]`` follows ``leader[k]`` (int32, host or device); ``lam``/``mu`` are FP64
     per-user rates.  Options mirror ``psi_options`` (precision ``fp32 | fp32_refine | fp64``,
     tol_mode ``psi | s_abs``, bnorm_mode ``none | inf``, self_loops ``reject | drop``).
+    ``allocator``: "torch" (the caching allocator), None (the library's stream-ordered
+    cudaMallocAsync) or an object whose ``struct`` is a ``psi_allocator``.
     """
 
     def __init__(self, n, follower, leader, lam, mu, precision="fp32_refine", tol_mode="psi",
@@ -92,6 +94,9 @@ class Graph:
         if allocator == "torch":
             self._alloc = _TorchAllocator(torch.cuda.current_device())
             opt.allocator = ctypes.pointer(self._alloc.struct)
+        elif allocator is not None:  # any object holding a psi_allocator in .struct
+            self._alloc = allocator
+            opt.allocator = ctypes.pointer(allocator.struct)
         self._opt = opt
         m = int(follower.shape[0]) if follower is not None else 0
         self._h = psi_graph_create(self.n, m, _ptr(follower), _ptr(leader), _ptr(lam), _ptr(mu), opt)

@@ -7,6 +7,7 @@
 #include <string>
 
 #include "solve.cuh"
+#include "trace.cuh"
 
 namespace psi {
 
@@ -161,6 +162,7 @@ void psi_options_default(psi_options* opt) {
 
 psi_status psi_graph_create(int64_t n, int64_t m, const int32_t* follower, const int32_t* leader,
                             const double* lambda, const double* mu, const psi_options* opt, psi_graph** out) {
+  psi::NvtxRange nvtx_range("psi_graph_create");
   if (out) *out = nullptr;
   psi_graph* h = nullptr;
   psi_status st = psi::guarded([&] {
@@ -203,6 +205,7 @@ psi_status psi_graph_create(int64_t n, int64_t m, const int32_t* follower, const
 }
 
 psi_status psi_solve(psi_graph* g, double eps, int32_t max_iter, const double* init_s, psi_solve_info* info) {
+  psi::NvtxRange nvtx_range("psi_solve");
   if (!g) {
     psi::set_last_error("graph is NULL");
     return PSI_ERR_INVALID_ARG;
@@ -216,6 +219,7 @@ psi_status psi_solve(psi_graph* g, double eps, int32_t max_iter, const double* i
 
 psi_status psi_pagerank(psi_graph* g, double alpha, double eps, int32_t max_iter, double* pi_out,
                         psi_solve_info* info) {
+  psi::NvtxRange nvtx_range("psi_pagerank");
   if (!g) {
     psi::set_last_error("graph is NULL");
     return PSI_ERR_INVALID_ARG;
@@ -228,6 +232,7 @@ psi_status psi_pagerank(psi_graph* g, double alpha, double eps, int32_t max_iter
 }
 
 psi_status psi_scores(const psi_graph* g, double* psi_out) {
+  psi::NvtxRange nvtx_range("psi_scores");
   if (!g || !psi_out) {
     psi::set_last_error("graph or output is NULL");
     return PSI_ERR_INVALID_ARG;
@@ -243,6 +248,7 @@ psi_status psi_scores(const psi_graph* g, double* psi_out) {
 }
 
 psi_status psi_topk(const psi_graph* g, int32_t k, int32_t* ids_out, double* vals_out) {
+  psi::NvtxRange nvtx_range("psi_topk");
   if (!g || !ids_out) {
     psi::set_last_error("graph or ids_out is NULL");
     return PSI_ERR_INVALID_ARG;

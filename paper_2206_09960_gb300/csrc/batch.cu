@@ -7,6 +7,7 @@
 #include <cstring>
 
 #include "build.cuh"
+#include "trace.cuh"
 #include "primitives.cuh"
 #include "solve.cuh"
 #include "spmm.cuh"
@@ -376,6 +377,7 @@ void read_vec(std::vector<T>& h, const T* d, size_t k, cudaStream_t s) {
 }  // namespace
 
 psi_status batch_solve(Batch& b, double eps, int32_t max_iter, psi_solve_info* info) {
+  NvtxRange nvtx_range("psi_batch_solve");
   PSI_REQUIRE(max_iter >= 0 && !std::isnan(eps), PSI_ERR_INVALID_ARG, "bad eps or max_iter");
   Graph& g = b.g;
   cudaStream_t s = g.stream;

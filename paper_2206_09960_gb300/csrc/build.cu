@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "primitives.cuh"
+#include "trace.cuh"
 #include "solve.cuh"
 #include "spmv.cuh"
 #include "build.cuh"
@@ -365,6 +366,8 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
   PSI_CUDA(cudaEventCreate(&t1));
   PSI_CUDA(cudaEventRecord(t0, s));
 
+  NvtxPhases phases;
+  phases.next("psi build 0: staging");
   // ---- stage inputs (host pointers are copied; device pointers are read in place).  Host
   //      copies run on a private stream, the rates first, then the edges in chunks; the
   //      validation pass (step 1) takes each chunk as soon as it has arrived, so it overlaps
@@ -436,6 +439,7 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
     }
   }
 
+  phases.next("psi build 1: validation");
   // ---- 1. validation and raw degrees
   DBuf<uint32_t> err(al, 8);  // [0] error bits, [1..4] class counts, [5] rows seen, [6..7] spare
   PSI_CUDA(cudaMemsetAsync(err.get(), 0, 8 * sizeof(uint32_t), s));
@@ -464,6 +468,7 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
   PSI_REQUIRE(!(ebits & kErrSelf), PSI_ERR_SELF_LOOP, "a user follows itself (self_loops = PSI_REJECT)");
   PSI_REQUIRE(!(ebits & kErrRate), PSI_ERR_BAD_RATE, "lambda/mu must be finite, >= 0, with lambda + mu > 0");
 
+  phases.next("psi build 2: renumbering");
   // ---- 2. renumbering by class and degree
   DBuf<uint32_t> perm32;
   {
@@ -490,6 +495,7 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
   g.perm.reset(al, (size_t)n);
   PSI_CUDA(cudaMemcpyAsync(g.perm.get(), perm32.get(), sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
 
+  phases.next("psi build 3: edge sort and CSR");
   // ---- 3. sort, merge duplicates, transposed CSR.  Keys hold the leader row and the
   //         follower's gathered index: bits_for(n_rows - 1) + bits_for(nu) bits (the low
   //         field never reaches all ones, so the all-ones sentinel sorts last)
@@ -557,6 +563,7 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
     g.max_followers = read1(mx.get(), s);
   }
 
+  phases.next("psi build 4: sigma and beta");
   // ---- 4. leader sums per follower: (sigma, beta) = L (lambda + mu, lambda), one
   //         load-balanced product over the follower-grouped CSR (rows X then U)
   DBuf<double> lam_i(al, (size_t)n), mu_i(al, (size_t)n);
@@ -624,6 +631,7 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
     li.release();
   }
 
+  phases.next("psi build 5: constants");
   // ---- 5. per-user constants
   g.c64.reset(al, (size_t)n);
   g.d64.reset(al, (size_t)n);
@@ -649,6 +657,7 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
     g.rho_inf = v[1];
   }
 
+  phases.next("psi build 6: schedule");
   // ---- 6. tile schedule of the Power-psi product
   {
     Schedule sch = make_schedule(g.row_ptr.get(), g.n_rows, mu_count, al, s, kSpmvTile);

@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "build.cuh"
+#include "trace.cuh"
 #include "primitives.cuh"
 #include "solve.cuh"
 #include "spmv.cuh"
@@ -697,6 +698,7 @@ int capture_pairs(Multi& M) {
 }  // namespace
 
 psi_status multi_solve(Multi& M, double eps, int32_t max_iter, psi_solve_info* info) {
+  NvtxRange nvtx_range("psi_multi_solve");
   PSI_REQUIRE(max_iter >= 0 && !std::isnan(eps), PSI_ERR_INVALID_ARG, "bad eps or max_iter");
   Graph& g = M.g;
   cudaStream_t s = g.stream;

@@ -3,6 +3,7 @@
 #include <cmath>
 
 #include "primitives.cuh"
+#include "trace.cuh"
 #include "solve.cuh"
 #include "spmv.cuh"
 
@@ -200,6 +201,7 @@ struct Stepper {
 // and stops when the device reports done.  Returns the steps executed.
 template <typename F>
 static int run_phase(Graph& g, cudaStream_t s, Stepper& st, F&& step_k, int batch) {
+  NvtxRange range("psi solve: steps");
   k_phase_begin<<<1, 1, 0, s>>>(g.state.get());
   PSI_LAUNCHED();
   st.phase_step = 0;
@@ -234,6 +236,7 @@ static int run_phase(Graph& g, cudaStream_t s, Stepper& st, F&& step_k, int batc
 // One step outside the batched loop (the FP64 refinement step): run it and read the state.
 template <typename F>
 static DevState run_single(Graph& g, cudaStream_t s, Stepper& st, F&& step_0) {
+  NvtxRange range("psi solve: FP64 step");
   k_phase_begin<<<1, 1, 0, s>>>(g.state.get());
   PSI_LAUNCHED();
   st.phase_step = 0;
@@ -501,6 +504,7 @@ psi_status solve_with(Graph& g, const SolveConsts& K, const SolveTarget& T, doub
   }
 
   // final step of Algorithm 2: psi^T = (s^T B + d^T) / N, one more product
+  NvtxRange final_range("psi solve: final");
   const DevState h = read_state(g, s);
   {
     DevState run = h;

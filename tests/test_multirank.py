@@ -1,7 +1,8 @@
 """Multi-rank host logic on CPU ranks (torch.distributed, gloo, world size 2): the row
 partition balanced by nonzeros, a row-sharded Power-psi iteration with one exchange per
 step (allgather of the new s, allreduce of the L1 gap) that must reproduce the single-process
-oracle, and the max-over-ranks timing of replica runs.  No GPU."""
+oracle, the max-over-ranks timing of replica runs, and a rank that leaves before an exchange
+(the other rank's collective ends with an error within the process-group timeout).  No GPU."""
 import os
 import socket
 import tempfile
@@ -23,13 +24,17 @@ def _free_port():
 def _worker(rank, world, port, fn_name, out_dir):
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
+    from datetime import timedelta
+
     import torch.distributed as dist
 
-    dist.init_process_group("gloo", rank=rank, world_size=world)
+    # a short timeout: a collective whose peer is gone ends with an error, not a hang
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=timedelta(seconds=20))
     try:
         result = globals()[fn_name](rank, world)
     finally:
-        dist.destroy_process_group()
+        if dist.is_initialized():
+            dist.destroy_process_group()
     np.save(os.path.join(out_dir, "%s_%d.npy" % (fn_name, rank)), np.asarray(result, dtype=object),
             allow_pickle=True)
 
@@ -87,6 +92,26 @@ def _replica_timing(rank, world):
     return dict(step=shard.max_over_ranks(0.1 + 0.05 * rank), gap=shard.allreduce_sum(1.5 * (rank + 1)))
 
 
+def _dropped_rank(rank, world):
+    """Rank 1 leaves before the exchange of the first step; rank 0 must see an error."""
+    import time
+
+    import torch
+    import torch.distributed as dist
+
+    plan = shard.ShardPlan(np.array([0, 4, 8]), rank)
+    if rank == 1:
+        dist.destroy_process_group()
+        return dict(left=True)
+    t0 = time.monotonic()
+    try:
+        shard.allgather_rows(torch.ones(4, dtype=torch.float64), plan)
+        err = None
+    except Exception as e:  # the collective fails: the peer is gone
+        err = type(e).__name__
+    return dict(left=False, error=err, seconds=time.monotonic() - t0)
+
+
 def test_partition_balances_nonzeros():
     rng = np.random.default_rng(0)
     deg = rng.zipf(2.0, 5000).clip(max=4000)
@@ -126,3 +151,10 @@ def test_replica_timing_is_the_slowest_rank():
         assert r["step"] == pytest.approx(0.15)
         assert r["gap"] == pytest.approx(4.5)
     assert shard.max_over_ranks(0.3) == 0.3  # a single process is its own maximum
+
+
+def test_a_dropped_rank_is_an_error_not_a_hang():
+    res = _run("_dropped_rank")
+    assert res[1]["left"]
+    assert res[0]["error"] is not None
+    assert res[0]["seconds"] < 60
