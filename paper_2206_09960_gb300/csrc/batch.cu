@@ -40,11 +40,14 @@ __global__ void k_b_consts(const double* __restrict__ lam, const double* __restr
                            double* d, double* isig, unsigned long long* bnorm_bits) {
   double bn = 0.0;
   BGRID_STRIDE(k, n) {
+    // the single-graph build's formulas: two FP64 divisions per user
     const double x = lam[k], y = mu[k], sg = sigma[k];
-    c[k] = y / (x + y);
-    d[k] = x / (x + y);
-    isig[k] = sg > 0.0 ? 1.0 / sg : 0.0;
-    if (sg > 0.0) bn = fmax(bn, beta[k] / sg);
+    const double inv = 1.0 / (x + y);
+    const double is = sg > 0.0 ? 1.0 / sg : 0.0;
+    c[k] = y * inv;
+    d[k] = x * inv;
+    isig[k] = is;
+    if (sg > 0.0) bn = fmax(bn, beta[k] * is);
   }
   atomicMax(bnorm_bits, (unsigned long long)__double_as_longlong(bn));
 }

@@ -39,14 +39,52 @@ int grid_for(int64_t n, int threads = 256) {
 #define GRID_STRIDE(i, n) \
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
 
+// f(i) for every i in [0, n), four independent indices per thread per round: the grids are
+// capped at 16 blocks per SM, so a plain grid-stride loop keeps one load per thread in
+// flight and streaming kernels end up latency-bound.
+template <typename F>
+__device__ __forceinline__ void grid_stride4(int64_t n, F&& f) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + 3 * stride < n; i += 4 * stride) {
+    f(i);
+    f(i + stride);
+    f(i + 2 * stride);
+    f(i + 3 * stride);
+  }
+  for (; i < n; i += stride) f(i);
+}
+
+// block-wide reductions (blockDim.x a multiple of 32, at most 1024); every thread gets the result
+__device__ __forceinline__ double block_max(double v) {
+  __shared__ double sh[32];
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __syncthreads();  // sh may still be read by a previous call
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double r = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmax(r, sh[w]);
+  return r;
+}
+__device__ __forceinline__ uint32_t block_sum(uint32_t v) {
+  __shared__ uint32_t sh[32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  uint32_t r = 0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r += sh[w];
+  return r;
+}
+
 // lambda, mu finite, >= 0 and lambda + mu > 0 (the model needs c, d defined)
 __global__ void k_check_rates(const double* __restrict__ lam, const double* __restrict__ mu, int64_t n,
                               uint32_t* err) {
   uint32_t bad = 0;
-  GRID_STRIDE(i, n) {
-    double x = lam[i], y = mu[i];
+  grid_stride4(n, [&](int64_t i) {
+    const double x = lam[i], y = mu[i];
     if (!(isfinite(x) && isfinite(y) && x >= 0.0 && y >= 0.0 && x + y > 0.0)) bad = kErrRate;
-  }
+  });
   if (bad) atomicOr(err, bad);
 }
 
@@ -103,17 +141,17 @@ __global__ void k_node_keys(const uint8_t* __restrict__ has_fol, const uint8_t* 
   if (threadIdx.x < 4 && cc[threadIdx.x]) atomicAdd(&class_count[threadIdx.x], cc[threadIdx.x]);
 }
 
-__global__ void k_invert(const uint32_t* __restrict__ perm, int64_t n, int32_t* inv) {
-  GRID_STRIDE(k, n) inv[perm[k]] = (int32_t)k;
+__global__ void k_invert(const uint32_t* __restrict__ perm, int64_t n, int32_t* __restrict__ inv) {
+  grid_stride4(n, [&](int64_t k) { inv[perm[k]] = (int32_t)k; });
 }
 
 // key = (leader row << bf) | follower's gathered index (X: its id, U: id - nR); a dropped
 // self-loop becomes the sentinel
 __global__ void k_edge_keys(const int32_t* __restrict__ f, const int32_t* __restrict__ l, int64_t m,
                             const int32_t* __restrict__ inv, int32_t nX, int32_t nR, int bf, uint64_t sentinel,
-                            uint64_t* key) {
-  GRID_STRIDE(e, m) {
-    int32_t a = f[e], c = l[e];
+                            uint64_t* __restrict__ key) {
+  grid_stride4(m, [&](int64_t e) {
+    const int32_t a = f[e], c = l[e];
     if (a == c) {
       key[e] = sentinel;
     } else {
@@ -121,7 +159,7 @@ __global__ void k_edge_keys(const int32_t* __restrict__ f, const int32_t* __rest
       const uint32_t gi = fi < (uint32_t)nX ? fi : fi - (uint32_t)nR;
       key[e] = ((uint64_t)(uint32_t)inv[c] << bf) | (uint64_t)gi;
     }
-  }
+  });
 }
 
 __device__ __forceinline__ bool first_of_run(const uint64_t* key, int64_t e, uint64_t sentinel) {
@@ -129,33 +167,38 @@ __device__ __forceinline__ bool first_of_run(const uint64_t* key, int64_t e, uin
   return k != sentinel && (e == 0 || key[e - 1] != k);
 }
 
-__global__ void k_unique_flags(const uint64_t* __restrict__ key, int64_t m, uint64_t sentinel, uint32_t* flag) {
+__global__ void k_unique_flags(const uint64_t* __restrict__ key, int64_t m, uint64_t sentinel,
+                               uint32_t* __restrict__ flag) {
   GRID_STRIDE(e, m) flag[e] = first_of_run(key, e, sentinel) ? 1u : 0u;
 }
 
 __global__ void k_unique_compact(const uint64_t* __restrict__ key, int64_t m, uint64_t sentinel,
-                                 const uint32_t* __restrict__ pos, int b, int32_t* li, int32_t* fi) {
+                                 const uint32_t* __restrict__ pos, int b, int32_t* __restrict__ li,
+                                 int32_t* __restrict__ fi) {
   const uint64_t mask = ((uint64_t)1 << b) - 1;
-  GRID_STRIDE(e, m) {
+  grid_stride4(m, [&](int64_t e) {
     if (first_of_run(key, e, sentinel)) {
-      uint32_t p = pos[e];
-      uint64_t k = key[e];
+      const uint32_t p = pos[e];
+      const uint64_t k = key[e];
       li[p] = (int32_t)(k >> b);
       fi[p] = (int32_t)(k & mask);
     }
-  }
+  });
 }
 
 // row_ptr[r] = first unique edge of leader r; counts the rows seen
-__global__ void k_row_bounds(const int32_t* __restrict__ li, int64_t mu, int32_t* row_ptr, uint32_t* rows_seen) {
+__global__ void k_row_bounds(const int32_t* __restrict__ li, int64_t mu, int32_t* __restrict__ row_ptr,
+                             uint32_t* rows_seen) {
   uint32_t c = 0;
-  GRID_STRIDE(e, mu) {
-    if (e == 0 || li[e - 1] != li[e]) {
-      row_ptr[li[e]] = (int32_t)e;
+  grid_stride4(mu, [&](int64_t e) {
+    const int32_t r = li[e];
+    if (e == 0 || li[e - 1] != r) {
+      row_ptr[r] = (int32_t)e;
       ++c;
     }
-  }
-  if (c) atomicAdd(rows_seen, c);
+  });
+  c = block_sum(c);  // one atomic per block, not per thread
+  if (threadIdx.x == 0 && c) atomicAdd(rows_seen, c);
 }
 
 __global__ void k_set_i32(int32_t* p, int32_t v) { *p = v; }
@@ -170,12 +213,13 @@ __global__ void k_row_max(const int32_t* __restrict__ row_ptr, int32_t n_rows, i
 }
 
 __global__ void k_permute_rates(const double* __restrict__ lam, const double* __restrict__ mu,
-                                const uint32_t* __restrict__ perm, int64_t n, double* lam_i, double* mu_i) {
-  GRID_STRIDE(k, n) {
-    uint32_t o = perm[k];
+                                const uint32_t* __restrict__ perm, int64_t n, double* __restrict__ lam_i,
+                                double* __restrict__ mu_i) {
+  grid_stride4(n, [&](int64_t k) {
+    const uint32_t o = perm[k];
     lam_i[k] = lam[o];
     mu_i[k] = mu[o];
-  }
+  });
 }
 
 // leaders of every user from the follower-grouped CSR (rows: X then U, compact)
@@ -195,14 +239,17 @@ __global__ void k_leader_weights(const double* __restrict__ lam_i, const double*
 // c_j = mu_j/(lambda_j+mu_j), d_j = lambda_j/(lambda_j+mu_j), 1/sigma_j (0 without leaders)
 __global__ void k_user_vectors(const double* __restrict__ lam_i, const double* __restrict__ mu_i,
                                const double* __restrict__ sigma, const double* __restrict__ beta, int64_t n,
-                               double* c64, double* d64,
-                               double* isig64, float* c32, float* mu32, float* isig32,
+                               double* __restrict__ c64, double* __restrict__ d64, double* __restrict__ isig64,
+                               float* __restrict__ c32, float* __restrict__ mu32, float* __restrict__ isig32,
                                unsigned long long* bnorm_bits, unsigned long long* rho_bits) {
   double bn = 0.0, rho = 0.0;
-  GRID_STRIDE(k, n) {
-    double x = lam_i[k], y = mu_i[k], sg = sigma[k];
-    double c = y / (x + y), d = x / (x + y);
-    double is = sg > 0.0 ? 1.0 / sg : 0.0;
+  grid_stride4(n, [&](int64_t k) {
+    // two FP64 divisions per user (FP64 division is a long instruction sequence and FP64
+    // throughput is low on this part); c and d within an ulp of mu/(lambda+mu), lambda/(lambda+mu)
+    const double x = lam_i[k], y = mu_i[k], sg = sigma[k];
+    const double inv = 1.0 / (x + y);
+    const double c = y * inv, d = x * inv;
+    const double is = sg > 0.0 ? 1.0 / sg : 0.0;
     c64[k] = c;
     d64[k] = d;
     isig64[k] = is;
@@ -210,14 +257,19 @@ __global__ void k_user_vectors(const double* __restrict__ lam_i, const double* _
     mu32[k] = (float)y;
     isig32[k] = (float)is;
     if (sg > 0.0) {
-      double b = beta[k] / sg, r = (sg - beta[k]) / sg;
+      const double b = beta[k] * is, r = 1.0 - b;
       bn = b > bn ? b : bn;
       rho = r > rho ? r : rho;
     }
+  });
+  // one atomic per block (per-thread atomics on one address serialise); non-negative
+  // doubles order like their bit patterns
+  bn = block_max(bn);
+  rho = block_max(rho);
+  if (threadIdx.x == 0) {
+    atomicMax(bnorm_bits, (unsigned long long)__double_as_longlong(bn));
+    atomicMax(rho_bits, (unsigned long long)__double_as_longlong(rho));
   }
-  // non-negative doubles order like their bit patterns
-  atomicMax(bnorm_bits, (unsigned long long)__double_as_longlong(bn));
-  atomicMax(rho_bits, (unsigned long long)__double_as_longlong(rho));
 }
 
 // tile_row[k] = row holding nonzero k*T (largest r with row_ptr[r] <= k*T); last = n_rows-1
@@ -264,9 +316,6 @@ __global__ void k_fill_i32(int32_t* x, int64_t lo, int64_t hi, int32_t v) {
   GRID_STRIDE(i, hi - lo) x[lo + i] = v;
 }
 
-__global__ void k_copy_i32_to_u32(const int32_t* __restrict__ a, int64_t n, uint32_t* b) {
-  GRID_STRIDE(i, n) b[i] = (uint32_t)a[i];
-}
 
 
 template <typename T>
@@ -583,12 +632,12 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
     const int32_t tiles_f = (int32_t)ceil_div(mc, kSpmvTile);
     DBuf<uint32_t> fk0(al, (size_t)mc), fk1(al, (size_t)mc);
     DBuf<uint32_t> lv0(al, (size_t)tiles_f * kSpmvTile), lv1(al, (size_t)mc);
-    k_copy_i32_to_u32<<<grid_for(mc), 256, 0, s>>>(g.col.get(), mc, fk0.get());
-    PSI_LAUNCHED();
-    k_copy_i32_to_u32<<<grid_for(mc), 256, 0, s>>>(li.get(), mc, lv0.get());
-    PSI_LAUNCHED();
+    // keys: the followers' gathered indices (the transposed CSR's columns, left untouched);
+    // values: the leader rows (non-negative int32, read as uint32)
+    bool alt = radix_sort<uint32_t>(fk0.get(), fk1.get(), lv0.get(), lv1.get(), mc, b, al, s,
+                                    reinterpret_cast<const uint32_t*>(g.col.get()),
+                                    reinterpret_cast<const uint32_t*>(li.get()));
     li.release();
-    bool alt = radix_sort<uint32_t>(fk0.get(), fk1.get(), lv0.get(), lv1.get(), mc, b, al, s);
     uint32_t* fs = alt ? fk1.get() : fk0.get();
     uint32_t* ls = alt ? lv1.get() : lv0.get();
     DBuf<uint32_t> lpad;

@@ -248,13 +248,19 @@ void exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, Allocator&
 
 template <typename K>
 bool radix_sort(K* keys, K* keys_alt, uint32_t* vals, uint32_t* vals_alt, int64_t n, int bits, Allocator& al,
-                cudaStream_t s) {
-  if (n <= 1 || bits <= 0) return false;
+                cudaStream_t s, const K* keys_in, const uint32_t* vals_in) {
+  if (n <= 1 || bits <= 0) {
+    if (keys_in && n > 0) PSI_CUDA(cudaMemcpyAsync(keys, keys_in, sizeof(K) * n, cudaMemcpyDeviceToDevice, s));
+    if (vals && vals_in && n > 0)
+      PSI_CUDA(cudaMemcpyAsync(vals, vals_in, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
+    return false;
+  }
   const int64_t tiles = ceil_div(n, kRsTile);
   DBuf<uint32_t> counts(al, (size_t)(tiles * 256));
-  K* src = keys;
+  // the first pass reads the separate inputs when given (they are never written)
+  K* src = keys_in ? const_cast<K*>(keys_in) : keys;
   K* dst = keys_alt;
-  uint32_t* vsrc = vals;
+  uint32_t* vsrc = vals_in ? const_cast<uint32_t*>(vals_in) : vals;
   uint32_t* vdst = vals_alt;
   bool flipped = false;
   for (int shift = 0; shift < bits; shift += 8) {
@@ -263,6 +269,10 @@ bool radix_sort(K* keys, K* keys_alt, uint32_t* vals, uint32_t* vals_alt, int64_
     exclusive_scan_u32(counts.get(), counts.get(), tiles * 256, al, s, nullptr);
     if (vals) launch_scatter<K, true>(src, vsrc, dst, vdst, n, shift, tiles, counts.get(), s);
     else launch_scatter<K, false>(src, nullptr, dst, nullptr, n, shift, tiles, counts.get(), s);
+    if (shift == 0 && keys_in) {  // from now on the two buffers alternate
+      src = keys;
+      vsrc = vals;
+    }
     std::swap(src, dst);
     std::swap(vsrc, vdst);
     flipped = !flipped;
@@ -270,8 +280,10 @@ bool radix_sort(K* keys, K* keys_alt, uint32_t* vals, uint32_t* vals_alt, int64_
   return flipped;
 }
 
-template bool radix_sort<uint32_t>(uint32_t*, uint32_t*, uint32_t*, uint32_t*, int64_t, int, Allocator&, cudaStream_t);
-template bool radix_sort<uint64_t>(uint64_t*, uint64_t*, uint32_t*, uint32_t*, int64_t, int, Allocator&, cudaStream_t);
+template bool radix_sort<uint32_t>(uint32_t*, uint32_t*, uint32_t*, uint32_t*, int64_t, int, Allocator&, cudaStream_t,
+                                   const uint32_t*, const uint32_t*);
+template bool radix_sort<uint64_t>(uint64_t*, uint64_t*, uint32_t*, uint32_t*, int64_t, int, Allocator&, cudaStream_t,
+                                   const uint64_t*, const uint32_t*);
 
 void sum_f64(const double* x, int64_t n, double* d_out, Allocator& al, cudaStream_t s) {
   DBuf<double> part(al, kSumBlocks);

@@ -13,10 +13,12 @@ void exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, Allocator&
 
 // Stable LSD radix sort of keys on bits [0, bits), 8 bits per pass, carrying an optional
 // uint32 payload (vals may be null).  Sorts between (keys, vals) and (keys_alt,
-// vals_alt); returns true when the sorted data ended up in the *_alt buffers.
+// vals_alt); returns true when the sorted data ended up in the *_alt buffers.  When
+// keys_in (and vals_in) are given, the data to sort is read from them, which are left
+// untouched, and (keys, vals) only serve as buffers.
 template <typename K>
 bool radix_sort(K* keys, K* keys_alt, uint32_t* vals, uint32_t* vals_alt, int64_t n, int bits,
-                Allocator& al, cudaStream_t s);
+                Allocator& al, cudaStream_t s, const K* keys_in = nullptr, const uint32_t* vals_in = nullptr);
 
 // Deterministic FP64 sum of n values (fixed order for a given n) into *d_out.
 void sum_f64(const double* x, int64_t n, double* d_out, Allocator& al, cudaStream_t s);

@@ -295,7 +295,7 @@ __global__ void k_scatter_f64_w(const double* __restrict__ in, const int32_t* __
 __global__ void k_warm_s0(const float* __restrict__ yhat, const float* __restrict__ x, const double* __restrict__ lam,
                           const double* __restrict__ mu, int64_t n, double* s0) {
   WGRID_STRIDE(i, n) {
-    const double c = mu[i] / (lam[i] + mu[i]);
+    const double c = mu[i] * (1.0 / (lam[i] + mu[i]));  // as the build forms c
     const bool has_followers = x[i * kIn] > 0.f;
     double v = has_followers ? exp((double)yhat[i]) : c;
     s0[i] = v < c ? c : v;  // s_i >= c_i always holds at the fixed point

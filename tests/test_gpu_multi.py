@@ -142,7 +142,7 @@ def test_multi_edge_cases():
     # no edges: psi = d / N exactly; a graph without rows takes two steps (series + FP64)
     np.testing.assert_allclose(out["psi"][:5], lam[:5] / (lam[:5] + mu[:5]) / 5, rtol=1e-15)
     assert out["infos"][0]["iters"] == 2
-    assert out["psi"][5] == lam[5] / (lam[5] + mu[5])
+    assert out["psi"][5] == pytest.approx(lam[5] / (lam[5] + mu[5]), rel=1e-15)
 
 
 def test_multi_all_graphs_without_edges():
