@@ -51,6 +51,52 @@ __device__ __forceinline__ D2 shfl_xor_t<D2>(D2 v, int o) {
   return D2(__shfl_xor_sync(0xffffffffu, v.a, o), __shfl_xor_sync(0xffffffffu, v.b, o));
 }
 
+// A value carried as the unevaluated sum hi + lo of two floats (about 48 significant
+// bits).  Sums of such pairs take a dozen FP32 instructions (Knuth's two-sum on the high
+// parts, then the low parts and a renormalisation), several times cheaper than FP64 adds
+// on a part whose FP64 rate is a small fraction of its FP32 rate.  Used for the FP64
+// confirming step and the final product of the FP32-series mode; 8-byte gathers as FP64.
+struct DF {
+  float hi, lo;
+  DF() = default;
+  __device__ __forceinline__ DF(int z) : hi((float)z), lo(0.f) {}
+  __device__ __forceinline__ DF(float h, float l) : hi(h), lo(l) {}
+};
+__device__ __forceinline__ DF operator+(DF a, DF b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  float e = (a.hi - (s - bb)) + (b.hi - bb);
+  e += a.lo + b.lo;
+  const float h = s + e;
+  return DF(h, e - (h - s));
+}
+__device__ __forceinline__ DF& operator+=(DF& x, DF y) {
+  x = x + y;
+  return x;
+}
+__device__ __forceinline__ DF df_from(double x) {
+  const float h = (float)x;
+  return DF(h, (float)(x - (double)h));
+}
+__device__ __forceinline__ double df_value(DF a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ void st_keep(DF* p, DF v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1,%2}, %3;" ::"l"(p), "f"(v.hi), "f"(v.lo), "l"(pol)
+               : "memory");
+}
+__device__ __forceinline__ DF ld_gather(const DF* p, uint64_t pol) {
+  float x, y;
+  asm volatile("ld.global.nc.L2::cache_hint.v2.f32 {%0,%1}, [%2], %3;" : "=f"(x), "=f"(y) : "l"(p), "l"(pol));
+  return DF(x, y);
+}
+template <>
+__device__ __forceinline__ DF shfl_up_t<DF>(DF v, int o) {
+  return DF(__shfl_up_sync(0xffffffffu, v.hi, o), __shfl_up_sync(0xffffffffu, v.lo, o));
+}
+template <>
+__device__ __forceinline__ DF shfl_xor_t<DF>(DF v, int o) {
+  return DF(__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o));
+}
+
 // ------------------------------------------------------------------ epilogues
 // row(r, y, gap): y = G(.)_r for row r (a user with followers); add |change| to gap.
 
@@ -89,24 +135,26 @@ struct EpiSeries {
   }
 };
 
-// FP64 step from the FP64 iterate: s_new = c + mu*y, r = s_new - s, gap += |r|, s = s_new,
-// u_new = s_new/sigma (next FP64 gather), v32 = r/sigma (start of an FP32 correction series).
+// Confirming step from the FP64 iterate: s_new = c + mu*y, r = s_new - s, gap += |r|,
+// s = s_new, u_new = s_new/sigma (next gather, as a float pair), v32 = r/sigma (start of an
+// FP32 correction series).  The product sums float pairs; the row's update is FP64.
 struct EpiResid {
   const double* c;
   const double* mu;
   const double* isig;
   double* s64;
-  double* u_new;
+  DF* u_new;
   float* v32;
   int32_t nX;
-  __device__ __forceinline__ void row(int32_t r, double y, double& gap, uint64_t pol_s, uint64_t pol_k) const {
+  __device__ __forceinline__ void row(int32_t r, DF yp, double& gap, uint64_t pol_s, uint64_t pol_k) const {
+    const double y = df_value(yp);
     double sn = ld_stream(c + r, pol_s) + ld_stream(mu + r, pol_s) * y;
     double rr = sn - s64[r];
     gap += fabs(rr);
     s64[r] = sn;
     if (r < nX) {
       double is = ld_stream(isig + r, pol_s);
-      st_keep(u_new + r, sn * is, pol_k);
+      st_keep(u_new + r, df_from(sn * is), pol_k);
       v32[r] = (float)(rr * is);
     }
   }
@@ -114,13 +162,21 @@ struct EpiResid {
 
 // Final step of Algorithm 2: psi_r = (lambda_r * G(s)_r + d_r) / N.
 template <typename T>
+__device__ __forceinline__ double as_double(T y) {
+  return (double)y;
+}
+template <>
+__device__ __forceinline__ double as_double<DF>(DF y) {
+  return df_value(y);
+}
+template <typename T>
 struct EpiFinal {
   const double* lam;
   const double* d;
   double* psi;
   double n;
   __device__ __forceinline__ void row(int32_t r, T y, double& gap, uint64_t pol_s, uint64_t) const {
-    psi[r] = (ld_stream(lam + r, pol_s) * (double)y + ld_stream(d + r, pol_s)) / n;
+    psi[r] = (ld_stream(lam + r, pol_s) * as_double(y) + ld_stream(d + r, pol_s)) / n;
   }
 };
 
