@@ -83,6 +83,17 @@ __global__ void k_b_to_u(T* dst, const S* s, const T* isig, int32_t nX, int32_t 
   }
 }
 
+// the same into the float-pair gathered matrix of the confirming and final products
+__global__ void k_b_to_u_df(DF* dst, const double* s, const double* isig, int32_t nX, int32_t nR, int64_t lo,
+                            int64_t hi, int Sp) {
+  BGRID_STRIDE(idx, (hi - lo) * Sp) {
+    const int64_t i = lo + idx / Sp;
+    const int c = (int)(idx % Sp);
+    const int64_t user = i < nX ? i : i + nR;
+    dst[i * Sp + c] = df_from(s[user * Sp + c] * isig[user * Sp + c]);
+  }
+}
+
 template <typename T>
 __global__ void k_b_fill(T* x, int64_t n, T v) {
   BGRID_STRIDE(i, n) x[i] = v;
@@ -404,11 +415,11 @@ psi_status batch_solve(Batch& b, double eps, int32_t max_iter, psi_solve_info* i
   PSI_LAUNCHED();
   k_b_to_u<float, float><<<bgrid(nu * kSp), 256, 0, s>>>(b.v0.get(), b.c32.get(), b.isig32.get(), nX, nR, 0, nu, kSp);
   PSI_LAUNCHED();
-  k_b_to_u<double, double><<<bgrid(nu * kSp), 256, 0, s>>>(b.u64a.get(), b.c64.get(), b.isig64.get(), nX, nR, nX, nu,
-                                                          kSp);
+  k_b_to_u_df<<<bgrid(nu * kSp), 256, 0, s>>>(reinterpret_cast<DF*>(b.u64a.get()), b.c64.get(), b.isig64.get(), nX,
+                                              nR, nX, nu, kSp);
   PSI_LAUNCHED();
-  k_b_to_u<double, double><<<bgrid(nu * kSp), 256, 0, s>>>(b.u64b.get(), b.c64.get(), b.isig64.get(), nX, nR, nX, nu,
-                                                          kSp);
+  k_b_to_u_df<<<bgrid(nu * kSp), 256, 0, s>>>(reinterpret_cast<DF*>(b.u64b.get()), b.c64.get(), b.isig64.get(), nX,
+                                              nR, nX, nu, kSp);
   PSI_LAUNCHED();
   std::vector<int32_t> act(kSp, 0);
   for (int q = 0; q < S; ++q) act[q] = 1;
@@ -451,8 +462,8 @@ psi_status batch_solve(Batch& b, double eps, int32_t max_iter, psi_solve_info* i
     for (int q = 0; q < S; ++q)
       if (h_ok[q] && !h_conv[q]) { next[q] = 1; any = true; }
     if (!any) break;
-    k_b_to_u<double, double><<<bgrid(nX * kSp), 256, 0, s>>>(ub[cur_u], b.s64.get(), b.isig64.get(), nX, nR, 0, nX,
-                                                            kSp);
+    k_b_to_u_df<<<bgrid(nX * kSp), 256, 0, s>>>(reinterpret_cast<DF*>(ub[cur_u]), b.s64.get(), b.isig64.get(), nX,
+                                                nR, 0, nX, kSp);
     PSI_LAUNCHED();
     if (!v0_u_cleared && g.nU > 0) {
       k_b_fill<float><<<bgrid((int64_t)g.nU * kSp), 256, 0, s>>>(b.v0.get() + (int64_t)nX * kSp, (int64_t)g.nU * kSp,
@@ -464,8 +475,8 @@ psi_status batch_solve(Batch& b, double eps, int32_t max_iter, psi_solve_info* i
     set_state(b, 1, max_iter, eps);
     EpiResidS e{reinterpret_cast<const double2*>(b.c64.get()), reinterpret_cast<const double2*>(b.mu64.get()),
                 reinterpret_cast<const double2*>(b.isig64.get()), reinterpret_cast<double2*>(b.s64.get()),
-                reinterpret_cast<double2*>(ub[cur_u ^ 1]), reinterpret_cast<float2*>(b.v0.get()), nX};
-    batch_step<double2, EpiResidS>(b, reinterpret_cast<const double2*>(ub[cur_u]), e);
+                reinterpret_cast<DF2*>(ub[cur_u ^ 1]), reinterpret_cast<float2*>(b.v0.get()), nX};
+    batch_step<DF2, EpiResidS>(b, reinterpret_cast<const DF2*>(ub[cur_u]), e);
     ++refinements;
     cur_u ^= 1;
     u_current = true;
@@ -480,8 +491,8 @@ psi_status batch_solve(Batch& b, double eps, int32_t max_iter, psi_solve_info* i
     PSI_CUDA(cudaMemcpyAsync(b.active.get(), next.data(), sizeof(int32_t) * kSp, cudaMemcpyHostToDevice, s));
   }
   if (!u_current) {
-    k_b_to_u<double, double><<<bgrid(nX * kSp), 256, 0, s>>>(ub[cur_u], b.s64.get(), b.isig64.get(), nX, nR, 0, nX,
-                                                            kSp);
+    k_b_to_u_df<<<bgrid(nX * kSp), 256, 0, s>>>(reinterpret_cast<DF*>(ub[cur_u]), b.s64.get(), b.isig64.get(), nX,
+                                                nR, 0, nX, kSp);
     PSI_LAUNCHED();
   }
   // final step of Algorithm 2 for every scenario: psi = (s B + d) / N
@@ -494,7 +505,7 @@ psi_status batch_solve(Batch& b, double eps, int32_t max_iter, psi_solve_info* i
   set_state(b, 1, INT32_MAX, -1.0);
   EpiFinalS ef{reinterpret_cast<const double2*>(b.lam64.get()), reinterpret_cast<const double2*>(b.d64.get()),
                reinterpret_cast<double2*>(b.psi.get()), (double)n};
-  batch_step<double2, EpiFinalS>(b, reinterpret_cast<const double2*>(ub[cur_u]), ef);
+  batch_step<DF2, EpiFinalS>(b, reinterpret_cast<const DF2*>(ub[cur_u]), ef);
   if (g.n_rows < n) {
     k_b_psi_nonrow<<<bgrid((n - g.n_rows) * kSp), 256, 0, s>>>(b.psi.get(), b.d64.get(), g.n_rows, n, kSp);
     PSI_LAUNCHED();

@@ -14,6 +14,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "df.cuh"
 
 namespace psi {
 
@@ -61,18 +62,20 @@ struct EpiSeriesS {
   }
 };
 
-// FP64 step for S scenarios: s_new = c + mu*y, r = s_new - s, s = s_new, u_new = s_new/sigma,
-// v32 = r/sigma (start of the next series); inactive scenarios keep their state.
+// Confirming step for S scenarios: s_new = c + mu*y, r = s_new - s, s = s_new,
+// u_new = s_new/sigma (next gather, float pairs), v32 = r/sigma (start of the next series);
+// inactive scenarios keep their state.  The product sums float pairs; the update is FP64.
 struct EpiResidS {
   const double2* c;
   const double2* mu;
   const double2* isig;
   double2* s64;
-  double2* u_new;
+  DF2* u_new;
   float2* v32;
   int32_t nX;
-  __device__ __forceinline__ void row(int32_t r, int lane, double2 y, const int* act, double2& gap) const {
+  __device__ __forceinline__ void row(int32_t r, int lane, DF2 yp, const int* act, double2& gap) const {
     const int64_t o = (int64_t)r * 32 + lane;
+    const double2 y = make_double2(df_value(yp.a), df_value(yp.b));
     const double2 cc = c[o], mm = mu[o], s = s64[o];
     double2 sn = make_double2(cc.x + mm.x * y.x, cc.y + mm.y * y.y);
     if (!act[0]) sn.x = s.x;
@@ -83,7 +86,7 @@ struct EpiResidS {
     s64[o] = sn;
     if (r < nX) {
       const double2 is = isig[o];
-      u_new[o] = make_double2(sn.x * is.x, sn.y * is.y);
+      u_new[o] = DF2{df_from(sn.x * is.x), df_from(sn.y * is.y)};
       v32[o] = make_float2((float)(rr.x * is.x), (float)(rr.y * is.y));
     }
   }
@@ -95,8 +98,9 @@ struct EpiFinalS {
   const double2* d;
   double2* psi;
   double n;
-  __device__ __forceinline__ void row(int32_t r, int lane, double2 y, const int*, double2&) const {
+  __device__ __forceinline__ void row(int32_t r, int lane, DF2 yp, const int*, double2&) const {
     const int64_t o = (int64_t)r * 32 + lane;
+    const double2 y = make_double2(df_value(yp.a), df_value(yp.b));
     const double2 l = lam[o], dd = d[o];
     psi[o] = make_double2((l.x * y.x + dd.x) / n, (l.y * y.y + dd.y) / n);
   }
@@ -104,12 +108,15 @@ struct EpiFinalS {
 
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ double2 add2(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ DF2 add2(DF2 a, DF2 b) { return DF2{a.a + b.a, a.b + b.b}; }
 template <typename V>
 __device__ __forceinline__ V zero2();
 template <>
 __device__ __forceinline__ float2 zero2<float2>() { return make_float2(0.f, 0.f); }
 template <>
 __device__ __forceinline__ double2 zero2<double2>() { return make_double2(0.0, 0.0); }
+template <>
+__device__ __forceinline__ DF2 zero2<DF2>() { return DF2{DF(0), DF(0)}; }
 
 __device__ __forceinline__ float2 ld_row(const float2* p, uint64_t pol) {
   float2 v;
@@ -119,6 +126,13 @@ __device__ __forceinline__ float2 ld_row(const float2* p, uint64_t pol) {
 __device__ __forceinline__ double2 ld_row(const double2* p, uint64_t pol) {
   double2 v;
   asm("ld.global.nc.L2::cache_hint.v2.f64 {%0,%1}, [%2], %3;" : "=d"(v.x), "=d"(v.y) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ DF2 ld_row(const DF2* p, uint64_t pol) {
+  DF2 v;
+  asm("ld.global.nc.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;"
+      : "=f"(v.a.hi), "=f"(v.a.lo), "=f"(v.b.hi), "=f"(v.b.lo)
+      : "l"(p), "l"(pol));
   return v;
 }
 
@@ -132,8 +146,12 @@ template <>
 __device__ __forceinline__ double2* carry_of<double2>(const SpmmArgs& a, bool head) {
   return head ? a.carry_head64 : a.carry_tail64;
 }
+template <>
+__device__ __forceinline__ DF2* carry_of<DF2>(const SpmmArgs& a, bool head) {  // the 16-byte carries
+  return reinterpret_cast<DF2*>(head ? a.carry_head64 : a.carry_tail64);
+}
 
-// V = float2 (FP32 gathers) or double2 (FP64 gathers); u is [gathered + 1][S/2] pairs.
+// V = float2 (FP32 gathers) or DF2 (float-pair gathers); u is [gathered + 1][S/2] pairs.
 template <typename V, typename Epi>
 __global__ void __launch_bounds__(256) k_spmm(SpmmArgs a, const V* __restrict__ u, Epi epi) {
   if (*a.done) return;

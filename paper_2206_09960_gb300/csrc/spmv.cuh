@@ -16,6 +16,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "df.cuh"
 
 namespace psi {
 
@@ -51,43 +52,6 @@ __device__ __forceinline__ D2 shfl_xor_t<D2>(D2 v, int o) {
   return D2(__shfl_xor_sync(0xffffffffu, v.a, o), __shfl_xor_sync(0xffffffffu, v.b, o));
 }
 
-// A value carried as the unevaluated sum hi + lo of two floats (about 48 significant
-// bits).  Sums of such pairs take a dozen FP32 instructions (Knuth's two-sum on the high
-// parts, then the low parts and a renormalisation), several times cheaper than FP64 adds
-// on a part whose FP64 rate is a small fraction of its FP32 rate.  Used for the FP64
-// confirming step and the final product of the FP32-series mode; 8-byte gathers as FP64.
-struct DF {
-  float hi, lo;
-  DF() = default;
-  __device__ __forceinline__ DF(int z) : hi((float)z), lo(0.f) {}
-  __device__ __forceinline__ DF(float h, float l) : hi(h), lo(l) {}
-};
-__device__ __forceinline__ DF operator+(DF a, DF b) {
-  const float s = a.hi + b.hi;
-  const float bb = s - a.hi;
-  float e = (a.hi - (s - bb)) + (b.hi - bb);
-  e += a.lo + b.lo;
-  const float h = s + e;
-  return DF(h, e - (h - s));
-}
-__device__ __forceinline__ DF& operator+=(DF& x, DF y) {
-  x = x + y;
-  return x;
-}
-__device__ __forceinline__ DF df_from(double x) {
-  const float h = (float)x;
-  return DF(h, (float)(x - (double)h));
-}
-__device__ __forceinline__ double df_value(DF a) { return (double)a.hi + (double)a.lo; }
-__device__ __forceinline__ void st_keep(DF* p, DF v, uint64_t pol) {
-  asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1,%2}, %3;" ::"l"(p), "f"(v.hi), "f"(v.lo), "l"(pol)
-               : "memory");
-}
-__device__ __forceinline__ DF ld_gather(const DF* p, uint64_t pol) {
-  float x, y;
-  asm volatile("ld.global.nc.L2::cache_hint.v2.f32 {%0,%1}, [%2], %3;" : "=f"(x), "=f"(y) : "l"(p), "l"(pol));
-  return DF(x, y);
-}
 template <>
 __device__ __forceinline__ DF shfl_up_t<DF>(DF v, int o) {
   return DF(__shfl_up_sync(0xffffffffu, v.hi, o), __shfl_up_sync(0xffffffffu, v.lo, o));
