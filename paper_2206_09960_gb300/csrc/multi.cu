@@ -94,8 +94,9 @@ struct EpiSeriesM {
   }
 };
 
-// FP64 step (Eq. 14) for the rows of CONFIRM graphs: s_new = c + mu * y, r = s_new - s,
-// s = s_new; v_next = r / sigma starts the graph's next series if the test fails.
+// Confirming step (Eq. 14) for the rows of CONFIRM graphs: s_new = c + mu * y, r = s_new - s,
+// s = s_new; v_next = r / sigma starts the graph's next series if the test fails.  The
+// product sums float pairs (as in the single-graph path); the row update is FP64.
 struct EpiResidM {
   static constexpr bool kTileSkip = true;
   const double* c;
@@ -109,11 +110,12 @@ struct EpiResidM {
   double* gap_row;
   TileGate gate;
   __device__ __forceinline__ bool tile_on(int32_t tile) const { return gate.on(tile); }
-  __device__ __forceinline__ void row(int32_t r, double y, double&, uint64_t pol_s, uint64_t) const {
+  __device__ __forceinline__ void row(int32_t r, DF yp, double&, uint64_t pol_s, uint64_t) const {
     if (phase[gid[r]] != kConfirm) {
       gap_row[r] = 0.0;
       return;
     }
+    const double y = df_value(yp);
     const double s = s64[r];
     const double sn = ld_stream(c + r, pol_s) + ld_stream(mu + r, pol_s) * y;
     const double rr = sn - s;
@@ -130,8 +132,8 @@ struct EpiFinalM {
   double* psi;
   const int32_t* gid;
   const double* n_of;
-  __device__ __forceinline__ void row(int32_t r, double y, double&, uint64_t pol_s, uint64_t) const {
-    psi[r] = (ld_stream(lam + r, pol_s) * y + ld_stream(d + r, pol_s)) / n_of[gid[r]];
+  __device__ __forceinline__ void row(int32_t r, DF y, double&, uint64_t pol_s, uint64_t) const {
+    psi[r] = (ld_stream(lam + r, pol_s) * df_value(y) + ld_stream(d + r, pol_s)) / n_of[gid[r]];
   }
 };
 
@@ -243,10 +245,20 @@ __global__ void __launch_bounds__(1024) k_group_step(int mode, MState* st, DevSt
 // FP64 gathered vector of the CONFIRM graphs' X users: u = s / sigma (other graphs' entries
 // are read only by their own rows, which ignore them in this step)
 __global__ void k_confirm_u(const DevState* gate, const double* __restrict__ s64, const double* __restrict__ isig,
-                            const int32_t* __restrict__ gid, const int32_t* __restrict__ phase, int32_t nX, double* u) {
+                            const int32_t* __restrict__ gid, const int32_t* __restrict__ phase, int32_t nX, DF* u) {
   if (gate[1].done) return;
   MGRID_STRIDE(j, nX) {
-    if (phase[gid[j]] == kConfirm) u[j] = s64[j] * isig[j];
+    if (phase[gid[j]] == kConfirm) u[j] = df_from(s64[j] * isig[j]);
+  }
+}
+
+// float-pair gathered vector: dst[j] = s[user(j)] * isig[user(j)] for j in [lo, hi)
+__global__ void k_to_gathered_df(DF* dst, const double* __restrict__ s, const double* __restrict__ isig, int32_t nX,
+                                 int32_t nR, int64_t lo, int64_t hi) {
+  MGRID_STRIDE(i, hi - lo) {
+    const int64_t j = lo + i;
+    const int64_t user = j < nX ? j : j + nR;
+    dst[j] = df_from(s[user] * isig[user]);
   }
 }
 
@@ -403,7 +415,8 @@ struct Multi {
   DBuf<DevState> gate;                 // [3]
   MState* host = nullptr;              // pinned, 2 slots
   // vectors
-  DBuf<double> s64, u64, gap_row, psi, psi_sum;
+  DBuf<double> s64, u64, gap_row, psi, psi_sum;  // u64 holds float pairs (8 bytes per entry)
+  DF* u64df() const { return reinterpret_cast<DF*>(u64.get()); }
   DBuf<float> v0, va, vb;
   // graph-build scratch of the hook
   DBuf<unsigned long long> bnorm_bits;
@@ -643,12 +656,12 @@ int step_pair(Multi& M, cudaStream_t s, const float* v_in, float* v_out) {
   launches += multi_product<float>(M, s, v_in, es, M.gate.get() + 0);
   launches += group_step(M, s, 0);
   k_confirm_u<<<mgrid(g.nX), 256, 0, s>>>(M.gate.get(), M.s64.get(), g.isig64.get(), M.gid.get(), M.phase.get(), g.nX,
-                                          M.u64.get());
+                                          M.u64df());
   PSI_LAUNCHED();
   ++launches;
   EpiResidM er{g.c64.get(), g.mu64.get(), g.isig64.get(), M.s64.get(), v_out, g.nX, M.gid.get(), M.phase.get(),
                M.gap_row.get(), TileGate{M.tile_g.get(), M.cnt_confirm.get()}};
-  launches += multi_product<double>(M, s, M.u64.get(), er, M.gate.get() + 1);
+  launches += multi_product<DF>(M, s, M.u64df(), er, M.gate.get() + 1);
   launches += group_step(M, s, 1);
   return launches;
 }
@@ -727,7 +740,7 @@ psi_status multi_solve(Multi& M, double eps, int32_t max_iter, psi_solve_info* i
     PSI_LAUNCHED();
   }
   if (g.nU > 0) {
-    k_to_gathered<double><<<mgrid(g.nU), 256, 0, s>>>(M.u64.get(), g.c64.get(), g.isig64.get(), nX, nR, nX, nu);
+    k_to_gathered_df<<<mgrid(g.nU), 256, 0, s>>>(M.u64df(), g.c64.get(), g.isig64.get(), nX, nR, nX, nu);
     PSI_LAUNCHED();
   }
   const bool iterate = (1.0 > eps) && max_iter > 0;  // Algorithm 2's loop test with gap = 1
@@ -794,11 +807,11 @@ psi_status multi_solve(Multi& M, double eps, int32_t max_iter, psi_solve_info* i
   }
   // final step of Algorithm 2 for every graph: psi = (s B + d) / N_g, one more product
   if (nX > 0) {
-    k_to_gathered<double><<<mgrid(nX), 256, 0, s>>>(M.u64.get(), M.s64.get(), g.isig64.get(), nX, nR, 0, nX);
+    k_to_gathered_df<<<mgrid(nX), 256, 0, s>>>(M.u64df(), M.s64.get(), g.isig64.get(), nX, nR, 0, nX);
     PSI_LAUNCHED();
   }
   EpiFinalM ef{g.lam64.get(), g.d64.get(), M.psi.get(), M.gid.get(), M.n_of.get()};
-  multi_product<double>(M, s, M.u64.get(), ef, M.gate.get() + 2);
+  multi_product<DF>(M, s, M.u64df(), ef, M.gate.get() + 2);
   if (g.n_rows < n) {
     k_psi_nonrow_m<<<mgrid(n - g.n_rows), 256, 0, s>>>(M.psi.get(), g.d64.get(), M.gid.get(), M.n_of.get(), g.n_rows, n);
     PSI_LAUNCHED();
