@@ -235,6 +235,11 @@ __global__ void k_leader_weights(const double* __restrict__ lam_i, const double*
                                  D2* w) {
   GRID_STRIDE(k, n + 1) w[k] = k < n ? D2(lam_i[k] + mu_i[k], lam_i[k]) : D2(0.0, 0.0);
 }
+// the same weights as float pairs
+__global__ void k_leader_weights_df(const double* __restrict__ lam_i, const double* __restrict__ mu_i, int64_t n,
+                                    DF2* w) {
+  GRID_STRIDE(k, n + 1) w[k] = k < n ? DF2(df_from(lam_i[k] + mu_i[k]), df_from(lam_i[k])) : DF2(0);
+}
 
 // c_j = mu_j/(lambda_j+mu_j), d_j = lambda_j/(lambda_j+mu_j), 1/sigma_j (0 without leaders)
 __global__ void k_user_vectors(const double* __restrict__ lam_i, const double* __restrict__ mu_i,
@@ -358,17 +363,18 @@ Schedule make_schedule(const int32_t* row_ptr, int32_t n_rows, int64_t m, Alloca
 }
 
 // y = (CSR) w for every row, both sums of the pair at once (one product + fix-up, FP64)
+template <typename W>
 void run_store_product(const int32_t* row_ptr, const int32_t* col, const Schedule& sc, int32_t n_rows, int64_t m,
-                       const D2* w, const EpiStore2& epi, Allocator& al, cudaStream_t s) {
+                       const W* w, const EpiStore2& epi, Allocator& al, cudaStream_t s) {
   if (sc.tiles == 0) return;
   DBuf<DevState> st(al, 1);
   PSI_CUDA(cudaMemsetAsync(st.get(), 0, sizeof(DevState), s));
   int per_sm = 0;
-  PSI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmv<D2, EpiStore2>, kSpmvThreads, 0));
+  PSI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmv<W, EpiStore2>, kSpmvThreads, 0));
   int grid = (per_sm > 0 ? per_sm : 1) * (int)num_sms();
   if (grid > sc.tiles) grid = sc.tiles;
   DBuf<double> gap_part(al, (size_t)grid);
-  DBuf<D2> carry_head(al, (size_t)sc.tiles), carry_tail(al, (size_t)sc.tiles);
+  DBuf<W> carry_head(al, (size_t)sc.tiles), carry_tail(al, (size_t)sc.tiles);
   SpmvArgs a{};
   a.row_ptr = row_ptr;
   a.col = col;
@@ -380,7 +386,7 @@ void run_store_product(const int32_t* row_ptr, const int32_t* col, const Schedul
   a.gap_part = gap_part.get();
   a.carry_head = carry_head.get();
   a.carry_tail = carry_tail.get();
-  k_spmv<D2, EpiStore2><<<grid, kSpmvThreads, 0, s>>>(a, w, epi);
+  k_spmv<W, EpiStore2><<<grid, kSpmvThreads, 0, s>>>(a, w, epi);
   PSI_LAUNCHED();
   if (sc.num_fix > 0) {
     int fgrid = (int)ceil_div(sc.num_fix, kFixWarps);
@@ -396,10 +402,14 @@ void run_store_product(const int32_t* row_ptr, const int32_t* col, const Schedul
     f.gap_fix = gap_fix.get();
     f.carry_head = carry_head.get();
     f.carry_tail = carry_tail.get();
-    k_fixup<D2, EpiStore2><<<fgrid, kFixWarps * 32, 0, s>>>(f, epi);
+    k_fixup<W, EpiStore2><<<fgrid, kFixWarps * 32, 0, s>>>(f, epi);
     PSI_LAUNCHED();
   }
 }
+template void run_store_product<D2>(const int32_t*, const int32_t*, const Schedule&, int32_t, int64_t, const D2*,
+                                    const EpiStore2&, Allocator&, cudaStream_t);
+template void run_store_product<DF2>(const int32_t*, const int32_t*, const Schedule&, int32_t, int64_t, const DF2*,
+                                     const EpiStore2&, Allocator&, cudaStream_t);
 
 
 bool is_device_pointer(const void* p);
@@ -665,11 +675,21 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
     fk1.release();
     lv1.release();
     Schedule sch = make_schedule(rp_f.get(), n_f, mc, al, s, kSpmvTile);
-    DBuf<D2> w(al, (size_t)n + 1);
-    k_leader_weights<<<grid_for(n + 1), 256, 0, s>>>(lam_i.get(), mu_i.get(), n, w.get());
-    PSI_LAUNCHED();
-    run_store_product(rp_f.get(), reinterpret_cast<const int32_t*>(ls), sch, n_f, mc, w.get(),
-                      EpiStore2{sigma.get(), beta.get(), g.nX, g.nR}, al, s);
+    // sigma and beta: FP64 sums in the FP64 mode, float-pair sums otherwise (FP64 adds are
+    // slow on this part; ~48-bit sums are far inside the FP32-series mode's accuracy)
+    if (g.opt.precision == PSI_FP64) {
+      DBuf<D2> w(al, (size_t)n + 1);
+      k_leader_weights<<<grid_for(n + 1), 256, 0, s>>>(lam_i.get(), mu_i.get(), n, w.get());
+      PSI_LAUNCHED();
+      run_store_product(rp_f.get(), reinterpret_cast<const int32_t*>(ls), sch, n_f, mc, w.get(),
+                        EpiStore2{sigma.get(), beta.get(), g.nX, g.nR}, al, s);
+    } else {
+      DBuf<DF2> w(al, (size_t)n + 1);
+      k_leader_weights_df<<<grid_for(n + 1), 256, 0, s>>>(lam_i.get(), mu_i.get(), n, w.get());
+      PSI_LAUNCHED();
+      run_store_product(rp_f.get(), reinterpret_cast<const int32_t*>(ls), sch, n_f, mc, w.get(),
+                        EpiStore2{sigma.get(), beta.get(), g.nX, g.nR}, al, s);
+    }
     k_leader_counts<<<grid_for(n_f), 256, 0, s>>>(rp_f.get(), n_f, g.nX, g.nR, g.n_leaders.get());
     PSI_LAUNCHED();
     if (hook) {

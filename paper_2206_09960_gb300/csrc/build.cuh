@@ -18,9 +18,11 @@ struct Schedule {
 Schedule make_schedule(const int32_t* row_ptr, int32_t n_rows, int64_t m, Allocator& al, cudaStream_t s,
                        int32_t tile);
 
-// Per-user pair of sums over a CSR (one load-balanced FP64 product and its fix-up).
+// Per-user pair of sums over a CSR (one load-balanced product and its fix-up), summed in
+// FP64 (D2 weights) or as float pairs (DF2 weights).
+template <typename W>
 void run_store_product(const int32_t* row_ptr, const int32_t* col, const Schedule& sc, int32_t n_rows, int64_t m,
-                       const D2* w, const EpiStore2& epi, Allocator& al, cudaStream_t s);
+                       const W* w, const EpiStore2& epi, Allocator& al, cudaStream_t s);
 
 // The follower-grouped CSR of a graph under construction: rows are the users with leaders
 // (X then U, compact), columns the leaders (internal ids), padded with the id n.

@@ -44,9 +44,25 @@ __device__ __forceinline__ DF ld_gather(const DF* p, uint64_t pol) {
   return DF(x, y);
 }
 
-// two float pairs (the two scenarios of one lane in the batched product)
+// two float pairs: the two scenarios of one lane in the batched product, or the two sums
+// (sigma, beta) of the build's leader product
 struct DF2 {
   DF a, b;
+  DF2() = default;
+  __device__ __forceinline__ DF2(int z) : a(z), b(z) {}
+  __device__ __forceinline__ DF2(DF x, DF y) : a(x), b(y) {}
 };
+__device__ __forceinline__ DF2 operator+(DF2 x, DF2 y) { return DF2(x.a + y.a, x.b + y.b); }
+__device__ __forceinline__ DF2& operator+=(DF2& x, DF2 y) {
+  x = x + y;
+  return x;
+}
+__device__ __forceinline__ DF2 ld_gather(const DF2* p, uint64_t pol) {
+  float a, b, c, d;
+  asm volatile("ld.global.nc.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;"
+               : "=f"(a), "=f"(b), "=f"(c), "=f"(d)
+               : "l"(p), "l"(pol));
+  return DF2(DF(a, b), DF(c, d));
+}
 
 }  // namespace psi

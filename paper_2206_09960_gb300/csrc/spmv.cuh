@@ -60,6 +60,14 @@ template <>
 __device__ __forceinline__ DF shfl_xor_t<DF>(DF v, int o) {
   return DF(__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o));
 }
+template <>
+__device__ __forceinline__ DF2 shfl_up_t<DF2>(DF2 v, int o) {
+  return DF2(shfl_up_t(v.a, o), shfl_up_t(v.b, o));
+}
+template <>
+__device__ __forceinline__ DF2 shfl_xor_t<DF2>(DF2 v, int o) {
+  return DF2(shfl_xor_t(v.a, o), shfl_xor_t(v.b, o));
+}
 
 // ------------------------------------------------------------------ epilogues
 // row(r, y, gap): y = G(.)_r for row r (a user with followers); add |change| to gap.
@@ -156,6 +164,11 @@ struct EpiStore2 {
     const int32_t user = r < nX ? r : r + skip;
     out_a[user] = y.a;
     out_b[user] = y.b;
+  }
+  __device__ __forceinline__ void row(int32_t r, DF2 y, double&, uint64_t, uint64_t) const {
+    const int32_t user = r < nX ? r : r + skip;
+    out_a[user] = df_value(y.a);
+    out_b[user] = df_value(y.b);
   }
 };
 
