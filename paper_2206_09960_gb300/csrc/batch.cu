@@ -109,7 +109,8 @@ struct BatchState {
 
 // Per-scenario gap sums (fixed order) and stop tests; one block of 1024 threads.
 __global__ void __launch_bounds__(1024) k_b_finalize(BatchState* st, int32_t* active, int32_t* iters,
-                                                    int32_t* ok, int32_t* converged, double* gap_last,
+                                                    int32_t* phase_it, int32_t* ok, int32_t* converged,
+                                                    double* gap_last,
                                                     const double* __restrict__ scale, const double* __restrict__ gp,
                                                     int ngp, const double* __restrict__ gf, int ngf, int Sp) {
   if (st->done) return;
@@ -128,11 +129,19 @@ __global__ void __launch_bounds__(1024) k_b_finalize(BatchState* st, int32_t* ac
     double gsum = 0.0;
     for (int p = 0; p < parts; ++p) gsum += sh[p * Sp + s];
     if (active[s]) {
+      const double prev = gap_last[s];
       gap_last[s] = gsum;
       iters[s] += 1;
-      const bool met = gsum * scale[s] <= st->eps;
+      const double scaled = gsum * scale[s];
+      const bool met = scaled <= st->eps;
       if (st->mode == 0) {
-        if (met) { active[s] = 0; ok[s] = 1; }
+        // as in the single-graph path: stop the series one step early when the next gap,
+        // predicted from the last two with a 1.2x margin, meets the test (the FP64 step that
+        // follows is tested as usual)
+        phase_it[s] += 1;
+        const bool next_passes =
+            phase_it[s] >= 2 && gsum < prev && 1.2 * (gsum / prev) * scaled <= st->eps && iters[s] < st->max_iter;
+        if (met || next_passes) { active[s] = 0; ok[s] = 1; }
         else if (iters[s] >= st->max_iter) active[s] = 0;
       } else {
         if (met) converged[s] = 1;
@@ -201,7 +210,7 @@ struct Batch {
   DBuf<double> s64, psi;          // [n][kSp]
   DBuf<double> u64a, u64b;        // [nu + 1][kSp]
   DBuf<float> v0, va, vb;         // [nu + 1][kSp]
-  DBuf<int32_t> active, iters, ok, converged;
+  DBuf<int32_t> active, iters, phase_it, ok, converged;  // phase_it: steps of the current series phase
   DBuf<double> gap_last;
   DBuf<BatchState> state;
   BatchState* host = nullptr;
@@ -310,6 +319,7 @@ void batch_buffers(Batch& b) {
   b.vb.reset(al, (nu + 1) * kSp);
   b.active.reset(al, kSp);
   b.iters.reset(al, kSp);
+  b.phase_it.reset(al, kSp);
   b.ok.reset(al, kSp);
   b.converged.reset(al, kSp);
   b.gap_last.reset(al, kSp);
@@ -365,7 +375,8 @@ void batch_step(Batch& b, const V* u, const Epi& epi) {
     PSI_LAUNCHED();
     ngf = b.fgrid * 8;
   }
-  k_b_finalize<<<1, 1024, 0, s>>>(b.state.get(), b.active.get(), b.iters.get(), b.ok.get(), b.converged.get(),
+  k_b_finalize<<<1, 1024, 0, s>>>(b.state.get(), b.active.get(), b.iters.get(), b.phase_it.get(), b.ok.get(),
+                                  b.converged.get(),
                                   b.gap_last.get(), b.scale.get(), b.gap_part.get(), ngp, b.gap_fix.get(), ngf, kSp);
   PSI_LAUNCHED();
 }
@@ -439,6 +450,7 @@ psi_status batch_solve(Batch& b, double eps, int32_t max_iter, psi_solve_info* i
   while (iterate) {
     // FP32 series for the scenarios still active (Eq. 13), terms summed into s64
     PSI_CUDA(cudaMemsetAsync(b.ok.get(), 0, sizeof(int32_t) * kSp, s));
+    PSI_CUDA(cudaMemsetAsync(b.phase_it.get(), 0, sizeof(int32_t) * kSp, s));
     set_state(b, 0, max_iter, eps);
     int k = 0;
     for (;;) {

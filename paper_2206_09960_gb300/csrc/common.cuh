@@ -178,8 +178,8 @@ struct DevState {
   int32_t phase_iters;   // steps executed in the current phase
   int32_t total_iters;   // power-iteration steps so far (t)
   int32_t max_iter;      // step cap
-  int32_t converged;     // scaled gap <= eps at the last step
-  int32_t pad_;
+  int32_t converged;     // scaled gap <= eps at the last step (or predicted for the next one)
+  int32_t predict;       // FP32 series phase: stop one step early when the next gap is predicted to pass
   double eps;            // stop threshold
   double scale;          // gap scale (B_norm, divided by N for the psi tolerance)
   double gap;            // last unscaled gap ||s_t - s_{t-1}||_1

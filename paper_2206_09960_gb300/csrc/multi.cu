@@ -142,7 +142,8 @@ struct EpiFinalM {
 // the gap entries of slice b of graph g's rows (its X range, then its R range, cut into
 // kGapSlices equal slices) with several loads in flight per thread.  k_group_step: one
 // block; thread g adds graph g's slice sums in order, counts the step and moves the graph:
-//   series (mode 0): test met and steps < max_iter -> CONFIRM; steps >= max_iter -> DONE;
+//   series (mode 0): test met (or the next step predicted to meet it) and steps < max_iter
+//                    -> CONFIRM; steps >= max_iter -> DONE;
 //   FP64   (mode 1): test met -> DONE, converged; steps >= max_iter -> DONE; else SERIES;
 // then the block recounts the phases into the prefix counts and the gates.
 constexpr int kGapSlices = 8;
@@ -178,7 +179,8 @@ __global__ void __launch_bounds__(256) k_group_partial(int mode, const DevState*
 
 __global__ void __launch_bounds__(1024) k_group_step(int mode, MState* st, DevState* gate,
                                                     const double* __restrict__ part, int32_t* phase, int32_t* iters,
-                                                    int32_t* converged, int32_t* refinements, double* gap_last,
+                                                    int32_t* phase_it, int32_t* converged, int32_t* refinements,
+                                                    double* gap_last,
                                                     const double* __restrict__ scale, int32_t* cnt_series,
                                                     int32_t* cnt_confirm, int G) {
   if (gate[mode].done) return;
@@ -190,16 +192,24 @@ __global__ void __launch_bounds__(1024) k_group_step(int mode, MState* st, DevSt
     if (p == (mode == 0 ? kSeries : kConfirm)) {
       double gap = 0.0;
       for (int b = 0; b < kGapSlices; ++b) gap += part[g * kGapSlices + b];
+      const double prev = gap_last[g];
       gap_last[g] = gap;
       const int32_t it = iters[g] + 1;
       iters[g] = it;
-      const bool met = gap * scale[g] <= st->eps;
+      const double scaled = gap * scale[g];
+      const bool met = scaled <= st->eps;
       if (mode == 0) {
-        p = (met && it < st->max_iter) ? kConfirm : (it >= st->max_iter ? kDone : kSeries);
+        // as in the single-graph path: a series also stops one step early when the next gap,
+        // predicted from the last two with a 1.2x margin, meets the test
+        const int32_t pit = phase_it[g] + 1;
+        phase_it[g] = pit;
+        const bool next_passes = pit >= 2 && gap < prev && 1.2 * (gap / prev) * scaled <= st->eps;
+        p = ((met || next_passes) && it < st->max_iter) ? kConfirm : (it >= st->max_iter ? kDone : kSeries);
       } else {
         refinements[g] += 1;
         if (met) converged[g] = 1;
         p = met || it >= st->max_iter ? kDone : kSeries;
+        if (p == kSeries) phase_it[g] = 0;  // a new series starts from the residual
       }
       phase[g] = p;
     }
@@ -408,7 +418,7 @@ struct Multi {
   DBuf<int4> ranges;                   // [G] row ranges
   DBuf<int4> tile_g;                   // [tiles] graph ranges of the tiles
   // loop state
-  DBuf<int32_t> phase, iters, converged, refinements, cnt_series, cnt_confirm;
+  DBuf<int32_t> phase, iters, phase_it, converged, refinements, cnt_series, cnt_confirm;
   DBuf<double> gap_last;
   DBuf<double> gap_part;               // [G][kGapSlices] slice sums of the per-row gaps
   DBuf<MState> st;
@@ -555,6 +565,7 @@ void multi_buffers(Multi& M) {
   const size_t G = (size_t)M.G;
   M.phase.reset(al, G);
   M.iters.reset(al, G);
+  M.phase_it.reset(al, G);
   M.converged.reset(al, G);
   M.refinements.reset(al, G);
   M.cnt_series.reset(al, G + 1);
@@ -639,7 +650,8 @@ int group_step(Multi& M, cudaStream_t s, int mode) {
   // gate[mode] is read before any thread writes a gate (only the last thread does, after
   // the block's barrier), and all threads of the block see the same value
   k_group_step<<<1, 1024, 0, s>>>(mode, M.st.get(), M.gate.get(), M.gap_part.get(), M.phase.get(), M.iters.get(),
-                                  M.converged.get(), M.refinements.get(), M.gap_last.get(), M.scale.get(),
+                                  M.phase_it.get(), M.converged.get(), M.refinements.get(), M.gap_last.get(),
+                                  M.scale.get(),
                                   M.cnt_series.get(), M.cnt_confirm.get(), M.G);
   PSI_LAUNCHED();
   return 2;
@@ -752,6 +764,7 @@ psi_status multi_solve(Multi& M, double eps, int32_t max_iter, psi_solve_info* i
     PSI_CUDA(cudaMemcpyAsync(M.cnt_series.get(), cs.data(), sizeof(int32_t) * (G + 1), cudaMemcpyHostToDevice, s));
     PSI_CUDA(cudaMemcpyAsync(M.cnt_confirm.get(), cc.data(), sizeof(int32_t) * (G + 1), cudaMemcpyHostToDevice, s));
     PSI_CUDA(cudaMemsetAsync(M.iters.get(), 0, sizeof(int32_t) * G, s));
+    PSI_CUDA(cudaMemsetAsync(M.phase_it.get(), 0, sizeof(int32_t) * G, s));
     PSI_CUDA(cudaMemsetAsync(M.converged.get(), 0, sizeof(int32_t) * G, s));
     PSI_CUDA(cudaMemsetAsync(M.refinements.get(), 0, sizeof(int32_t) * G, s));
     PSI_CUDA(cudaMemsetAsync(M.gap_last.get(), 0, sizeof(double) * G, s));

@@ -28,12 +28,19 @@ __global__ void __launch_bounds__(1024) k_finalize(DevState* st, const double* _
   }
   if (threadIdx.x == 0) {
     const double gap = sh[0] + st->extra_gap;
+    const double prev = st->gap;  // the previous step's gap (same phase when phase_iters >= 1)
     st->extra_gap = 0.0;
     st->gap = gap;
     st->gap_scaled = gap * st->scale;
     st->total_iters += 1;
     st->phase_iters += 1;
-    if (st->gap_scaled <= st->eps) {
+    // In an FP32 series phase the terms shrink geometrically; when the next gap, predicted
+    // from the last two with a 1.2x margin, meets the test, the series stops one step early
+    // and the FP64 confirming step that follows is that next step (its gap is still the one
+    // tested, so the stop rule of Algorithm 2 is unchanged; a wrong guess costs a series).
+    const bool next_passes = st->predict && st->phase_iters >= 2 && gap < prev &&
+                             1.2 * (gap / prev) * st->gap_scaled <= st->eps;
+    if (st->gap_scaled <= st->eps || (next_passes && st->total_iters < st->max_iter)) {
       st->done = 1;
       st->converged = 1;
     } else if (st->total_iters >= st->max_iter) {
@@ -43,9 +50,10 @@ __global__ void __launch_bounds__(1024) k_finalize(DevState* st, const double* _
   }
 }
 
-__global__ void k_phase_begin(DevState* st) {
+__global__ void k_phase_begin(DevState* st, int predict) {
   st->phase_iters = 0;
   st->converged = 0;
+  st->predict = predict;
   st->done = st->total_iters >= st->max_iter ? 1 : 0;
 }
 
@@ -209,9 +217,9 @@ struct Stepper {
 // Runs one phase of steps; step(k) launches phase step k.  Keeps two batches in flight
 // and stops when the device reports done.  Returns the steps executed.
 template <typename F>
-static int run_phase(Graph& g, cudaStream_t s, Stepper& st, F&& step_k, int batch) {
+static int run_phase(Graph& g, cudaStream_t s, Stepper& st, F&& step_k, int batch, int predict = 0) {
   NvtxRange range("psi solve: steps");
-  k_phase_begin<<<1, 1, 0, s>>>(g.state.get());
+  k_phase_begin<<<1, 1, 0, s>>>(g.state.get(), predict);
   PSI_LAUNCHED();
   st.phase_step = 0;
   cudaEvent_t evs[2];
@@ -246,7 +254,7 @@ static int run_phase(Graph& g, cudaStream_t s, Stepper& st, F&& step_k, int batc
 template <typename F>
 static DevState run_single(Graph& g, cudaStream_t s, Stepper& st, F&& step_0) {
   NvtxRange range("psi solve: FP64 step");
-  k_phase_begin<<<1, 1, 0, s>>>(g.state.get());
+  k_phase_begin<<<1, 1, 0, s>>>(g.state.get(), 0);
   PSI_LAUNCHED();
   st.phase_step = 0;
   step_0();
@@ -475,7 +483,7 @@ psi_status solve_with(Graph& g, const SolveConsts& K, const SolveTarget& T, doub
             const float* vin = (k == 0) ? v0 : vb[(k + 1) & 1];
             EpiSeries e{K.mu32, K.isig32, s64, vb[k & 1], nX};
             st.step<float>(vin, e);
-          }, batch);
+          }, batch, /*predict=*/1);
           timed.push_back({first, steps, false});
           if (steps > 0) u_current = false;
           DevState h = read_state(g, s);
