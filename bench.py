@@ -410,6 +410,7 @@ def run_warmstart(args, n_train=200, eval_scale=23, train_steps=1500):
 def workload_config(args, stats):
     cfg = {"workload": f"rmat_scale{args.scale}_ef16_a.57_b.19_c.19_relabel_lognormal1.5",
            "n": 1 << args.scale, "edge_draws": 16 << args.scale, "eps": args.eps,
+           "allocator": getattr(args, "allocator", "torch"),
            "tolerance": "eps_t/N (psi tolerance, B_norm=1)", "precision": "fp32 terms, fp64 iterate and residual",
            "topk": 100, "l2": "inputs larger than L2 (edge list 8 B x draws)", "parallelism": "replicas"}
     if stats:
@@ -429,6 +430,8 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--eps", type=float, default=1e-8)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--allocator", default="torch", choices=["torch", "library"],
+                    help="device memory of the library: its own stream-ordered pool, or torch's caching allocator")
     ap.add_argument("--profile-solve", action="store_true",
                     help="multi workload: run one extra solve between cudaProfilerStart/Stop (ncu --profile-from-start off)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -484,8 +487,10 @@ def main():
     vals_h = torch.empty(100, dtype=torch.float64).pin_memory()
     stream = torch.cuda.current_stream()
 
+    alloc = "torch" if args.allocator == "torch" else None
+
     def step(inputs, ids, vals, profile=False):
-        with psi.Graph(n, *inputs, profile=profile, stream=stream) as g:
+        with psi.Graph(n, *inputs, profile=profile, stream=stream, allocator=alloc) as g:
             info = g.solve(args.eps, 100000)
             g.topk(100, ids, vals)
             return info, g.stats()

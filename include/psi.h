@@ -325,6 +325,12 @@ psi_status psi_solve_warm(psi_graph* g, const psi_mlp* m, double eps, int32_t ma
 psi_status psi_topk_noalloc(const double* psi_in, int64_t n, int32_t k, int32_t* ids_out, double* vals_out,
                             void* stream);
 
+/* Without a caller allocator (psi_options.allocator NULL), device memory comes from a
+ * stream-ordered pool private to the library on each device, which keeps freed memory for
+ * the next call.  psi_trim_memory waits for the current device and returns that pool's
+ * unused memory to the device. */
+psi_status psi_trim_memory(void);
+
 /* Number of CUDA kernels this library has launched in this process (instrumentation). */
 int64_t psi_kernel_launches(void);
 

@@ -3,6 +3,7 @@
 // thread-local message; nothing aborts or traps.
 #include <atomic>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -27,13 +28,41 @@ void throw_cuda(cudaError_t e, const char* what, const char* file, int line) {
   throw PsiError(PSI_ERR_CUDA, m);
 }
 
+// The library's own stream-ordered pool on each device (used when the caller gives no
+// allocator).  It keeps freed memory for reuse instead of returning it at every
+// synchronisation, as the device's default pool does with its default settings; the
+// default pool itself is left untouched.  psi_trim_memory() gives the cached memory back.
+namespace {
+std::mutex g_pool_mutex;
+cudaMemPool_t g_pools[64] = {};
+}  // namespace
+
+cudaMemPool_t library_pool() {
+  int dev = 0;
+  PSI_CUDA(cudaGetDevice(&dev));
+  PSI_REQUIRE(dev >= 0 && dev < 64, PSI_ERR_CUDA, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_pool_mutex);
+  if (!g_pools[dev]) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    PSI_CUDA(cudaMemPoolCreate(&pool, &props));
+    uint64_t keep = UINT64_MAX;
+    PSI_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+    g_pools[dev] = pool;
+  }
+  return g_pools[dev];
+}
+
 void* Allocator::alloc(size_t bytes) {
   void* p = nullptr;
   if (has_user) {
     p = user.alloc(bytes, (void*)stream, user.ctx);
     if (!p) throw PsiError(PSI_ERR_OOM, "allocator returned NULL for " + std::to_string(bytes) + " bytes");
   } else {
-    cudaError_t e = cudaMallocAsync(&p, bytes, stream);
+    cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, library_pool(), stream);
     if (e != cudaSuccess || !p) {
       cudaGetLastError();
       throw PsiError(PSI_ERR_OOM, "cudaMallocAsync of " + std::to_string(bytes) + " bytes failed: " +
@@ -356,6 +385,14 @@ const char* psi_status_string(psi_status s) {
 const char* psi_last_error(void) { return psi::g_last_error.c_str(); }
 
 int64_t psi_kernel_launches(void) { return psi::g_launches.load(); }
+
+psi_status psi_trim_memory(void) {
+  return psi::guarded([&] {
+    cudaMemPool_t pool = psi::library_pool();
+    PSI_CUDA(cudaDeviceSynchronize());
+    PSI_CUDA(cudaMemPoolTrimTo(pool, 0));
+  });
+}
 
 int32_t psi_version(void) { return 100; }
 
