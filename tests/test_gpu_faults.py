@@ -70,3 +70,18 @@ def test_allocation_failures_become_statuses_and_leak_nothing():
     # the library still works, with the same result
     again = _run(w, _CountingAllocator())
     assert again["iters"] == ref["iters"] and again["psi_sum"] == ref["psi_sum"]
+
+
+def test_library_pool_and_trim():
+    """Without a caller allocator the library uses its own pool; results match the torch
+    allocator's bit for bit, and psi_trim_memory returns the cached memory."""
+    from paper_2206_09960_gb300 import Graph, _binding as B
+
+    w = psigen.workload("rmat", seed=32, scale=11)
+    outs = []
+    for alloc in (None, "torch"):
+        with Graph(w["n"], w["follower"], w["leader"], w["lam"], w["mu"], allocator=alloc) as g:
+            g.solve(1e-8, 1000)
+            outs.append(g.scores().cpu().numpy())
+    np.testing.assert_array_equal(outs[0], outs[1])
+    assert B.load().psi_trim_memory() == B.PSI_OK
