@@ -83,14 +83,15 @@ __global__ void k_b_to_u(T* dst, const S* s, const T* isig, int32_t nX, int32_t 
   }
 }
 
-// the same into the float-pair gathered matrix of the confirming and final products
-__global__ void k_b_to_u_df(DF* dst, const double* s, const double* isig, int32_t nX, int32_t nR, int64_t lo,
-                            int64_t hi, int Sp) {
+// the same into the gathered matrix of the confirming and final products (FP64 or float pairs)
+template <typename E>
+__global__ void k_b_to_u_g(E* dst, const double* s, const double* isig, int32_t nX, int32_t nR, int64_t lo,
+                           int64_t hi, int Sp) {
   BGRID_STRIDE(idx, (hi - lo) * Sp) {
     const int64_t i = lo + idx / Sp;
     const int c = (int)(idx % Sp);
     const int64_t user = i < nX ? i : i + nR;
-    dst[i * Sp + c] = df_from(s[user * Sp + c] * isig[user * Sp + c]);
+    dst[i * Sp + c] = to_gather<E>(s[user * Sp + c] * isig[user * Sp + c]);
   }
 }
 
@@ -410,6 +411,23 @@ psi_status batch_solve(Batch& b, double eps, int32_t max_iter, psi_solve_info* i
   const int32_t nX = g.nX, nR = g.nR;
   const int64_t nu = (int64_t)g.nX + g.nU;
   const int S = b.S;
+  // float pairs in the confirming and final products when every scenario's tolerance is far
+  // above their rounding (as in the single-graph path), FP64 otherwise
+  bool pairs = true;
+  {
+    std::vector<double> sc;
+    read_vec(sc, b.scale.get(), kSp, s);
+    for (int q = 0; q < S; ++q) pairs = pairs && eps / sc[q] >= std::ldexp(1.0, -30) * (double)n;
+  }
+  auto to_u = [&](double* dst, const double* src, int64_t lo, int64_t hi) {
+    if (hi <= lo) return;
+    if (pairs)
+      k_b_to_u_g<DF><<<bgrid((hi - lo) * kSp), 256, 0, s>>>(reinterpret_cast<DF*>(dst), src, b.isig64.get(), nX, nR,
+                                                             lo, hi, kSp);
+    else
+      k_b_to_u_g<double><<<bgrid((hi - lo) * kSp), 256, 0, s>>>(dst, src, b.isig64.get(), nX, nR, lo, hi, kSp);
+    PSI_LAUNCHED();
+  };
   cudaEvent_t t0, t1;
   PSI_CUDA(cudaEventCreate(&t0));
   PSI_CUDA(cudaEventCreate(&t1));
@@ -426,12 +444,8 @@ psi_status batch_solve(Batch& b, double eps, int32_t max_iter, psi_solve_info* i
   PSI_LAUNCHED();
   k_b_to_u<float, float><<<bgrid(nu * kSp), 256, 0, s>>>(b.v0.get(), b.c32.get(), b.isig32.get(), nX, nR, 0, nu, kSp);
   PSI_LAUNCHED();
-  k_b_to_u_df<<<bgrid(nu * kSp), 256, 0, s>>>(reinterpret_cast<DF*>(b.u64a.get()), b.c64.get(), b.isig64.get(), nX,
-                                              nR, nX, nu, kSp);
-  PSI_LAUNCHED();
-  k_b_to_u_df<<<bgrid(nu * kSp), 256, 0, s>>>(reinterpret_cast<DF*>(b.u64b.get()), b.c64.get(), b.isig64.get(), nX,
-                                              nR, nX, nu, kSp);
-  PSI_LAUNCHED();
+  to_u(b.u64a.get(), b.c64.get(), nX, nu);
+  to_u(b.u64b.get(), b.c64.get(), nX, nu);
   std::vector<int32_t> act(kSp, 0);
   for (int q = 0; q < S; ++q) act[q] = 1;
   PSI_CUDA(cudaMemcpyAsync(b.active.get(), act.data(), sizeof(int32_t) * kSp, cudaMemcpyHostToDevice, s));
@@ -474,9 +488,7 @@ psi_status batch_solve(Batch& b, double eps, int32_t max_iter, psi_solve_info* i
     for (int q = 0; q < S; ++q)
       if (h_ok[q] && !h_conv[q]) { next[q] = 1; any = true; }
     if (!any) break;
-    k_b_to_u_df<<<bgrid(nX * kSp), 256, 0, s>>>(reinterpret_cast<DF*>(ub[cur_u]), b.s64.get(), b.isig64.get(), nX,
-                                                nR, 0, nX, kSp);
-    PSI_LAUNCHED();
+    to_u(ub[cur_u], b.s64.get(), 0, nX);
     if (!v0_u_cleared && g.nU > 0) {
       k_b_fill<float><<<bgrid((int64_t)g.nU * kSp), 256, 0, s>>>(b.v0.get() + (int64_t)nX * kSp, (int64_t)g.nU * kSp,
                                                                 0.f);
@@ -485,10 +497,15 @@ psi_status batch_solve(Batch& b, double eps, int32_t max_iter, psi_solve_info* i
     }
     PSI_CUDA(cudaMemcpyAsync(b.active.get(), next.data(), sizeof(int32_t) * kSp, cudaMemcpyHostToDevice, s));
     set_state(b, 1, max_iter, eps);
-    EpiResidS e{reinterpret_cast<const double2*>(b.c64.get()), reinterpret_cast<const double2*>(b.mu64.get()),
-                reinterpret_cast<const double2*>(b.isig64.get()), reinterpret_cast<double2*>(b.s64.get()),
-                reinterpret_cast<DF2*>(ub[cur_u ^ 1]), reinterpret_cast<float2*>(b.v0.get()), nX};
-    batch_step<DF2, EpiResidS>(b, reinterpret_cast<const DF2*>(ub[cur_u]), e);
+    auto resid = [&](auto tag) {
+      using V = decltype(tag);
+      EpiResidS<V> e{reinterpret_cast<const double2*>(b.c64.get()), reinterpret_cast<const double2*>(b.mu64.get()),
+                     reinterpret_cast<const double2*>(b.isig64.get()), reinterpret_cast<double2*>(b.s64.get()),
+                     reinterpret_cast<V*>(ub[cur_u ^ 1]), reinterpret_cast<float2*>(b.v0.get()), nX};
+      batch_step<V, EpiResidS<V>>(b, reinterpret_cast<const V*>(ub[cur_u]), e);
+    };
+    if (pairs) resid(DF2{});
+    else resid(double2{});
     ++refinements;
     cur_u ^= 1;
     u_current = true;
@@ -503,9 +520,7 @@ psi_status batch_solve(Batch& b, double eps, int32_t max_iter, psi_solve_info* i
     PSI_CUDA(cudaMemcpyAsync(b.active.get(), next.data(), sizeof(int32_t) * kSp, cudaMemcpyHostToDevice, s));
   }
   if (!u_current) {
-    k_b_to_u_df<<<bgrid(nX * kSp), 256, 0, s>>>(reinterpret_cast<DF*>(ub[cur_u]), b.s64.get(), b.isig64.get(), nX,
-                                                nR, 0, nX, kSp);
-    PSI_LAUNCHED();
+    to_u(ub[cur_u], b.s64.get(), 0, nX);
   }
   // final step of Algorithm 2 for every scenario: psi = (s B + d) / N
   std::vector<int32_t> all(kSp, 1);
@@ -515,9 +530,14 @@ psi_status batch_solve(Batch& b, double eps, int32_t max_iter, psi_solve_info* i
   std::vector<double> gap_save;
   read_vec(gap_save, b.gap_last.get(), kSp, s);
   set_state(b, 1, INT32_MAX, -1.0);
-  EpiFinalS ef{reinterpret_cast<const double2*>(b.lam64.get()), reinterpret_cast<const double2*>(b.d64.get()),
-               reinterpret_cast<double2*>(b.psi.get()), (double)n};
-  batch_step<DF2, EpiFinalS>(b, reinterpret_cast<const DF2*>(ub[cur_u]), ef);
+  auto final_step = [&](auto tag) {
+    using V = decltype(tag);
+    EpiFinalS<V> ef{reinterpret_cast<const double2*>(b.lam64.get()), reinterpret_cast<const double2*>(b.d64.get()),
+                    reinterpret_cast<double2*>(b.psi.get()), (double)n};
+    batch_step<V, EpiFinalS<V>>(b, reinterpret_cast<const V*>(ub[cur_u]), ef);
+  };
+  if (pairs) final_step(DF2{});
+  else final_step(double2{});
   if (g.n_rows < n) {
     k_b_psi_nonrow<<<bgrid((n - g.n_rows) * kSp), 256, 0, s>>>(b.psi.get(), b.d64.get(), g.n_rows, n, kSp);
     PSI_LAUNCHED();

@@ -96,7 +96,9 @@ struct EpiSeriesM {
 
 // Confirming step (Eq. 14) for the rows of CONFIRM graphs: s_new = c + mu * y, r = s_new - s,
 // s = s_new; v_next = r / sigma starts the graph's next series if the test fails.  The
-// product sums float pairs (as in the single-graph path); the row update is FP64.
+// product sums float pairs or FP64 (G, chosen per solve as in the single-graph path); the
+// row update is FP64.
+template <typename G>
 struct EpiResidM {
   static constexpr bool kTileSkip = true;
   const double* c;
@@ -110,12 +112,12 @@ struct EpiResidM {
   double* gap_row;
   TileGate gate;
   __device__ __forceinline__ bool tile_on(int32_t tile) const { return gate.on(tile); }
-  __device__ __forceinline__ void row(int32_t r, DF yp, double&, uint64_t pol_s, uint64_t) const {
+  __device__ __forceinline__ void row(int32_t r, G yp, double&, uint64_t pol_s, uint64_t) const {
     if (phase[gid[r]] != kConfirm) {
       gap_row[r] = 0.0;
       return;
     }
-    const double y = df_value(yp);
+    const double y = as_double(yp);
     const double s = s64[r];
     const double sn = ld_stream(c + r, pol_s) + ld_stream(mu + r, pol_s) * y;
     const double rr = sn - s;
@@ -126,14 +128,15 @@ struct EpiResidM {
 };
 
 // Final step of Algorithm 2 for every graph: psi_r = (lambda_r * G(s)_r + d_r) / N_g.
+template <typename G>
 struct EpiFinalM {
   const double* lam;
   const double* d;
   double* psi;
   const int32_t* gid;
   const double* n_of;
-  __device__ __forceinline__ void row(int32_t r, DF y, double&, uint64_t pol_s, uint64_t) const {
-    psi[r] = (ld_stream(lam + r, pol_s) * df_value(y) + ld_stream(d + r, pol_s)) / n_of[gid[r]];
+  __device__ __forceinline__ void row(int32_t r, G y, double&, uint64_t pol_s, uint64_t) const {
+    psi[r] = (ld_stream(lam + r, pol_s) * as_double(y) + ld_stream(d + r, pol_s)) / n_of[gid[r]];
   }
 };
 
@@ -254,21 +257,23 @@ __global__ void __launch_bounds__(1024) k_group_step(int mode, MState* st, DevSt
 
 // FP64 gathered vector of the CONFIRM graphs' X users: u = s / sigma (other graphs' entries
 // are read only by their own rows, which ignore them in this step)
+template <typename G>
 __global__ void k_confirm_u(const DevState* gate, const double* __restrict__ s64, const double* __restrict__ isig,
-                            const int32_t* __restrict__ gid, const int32_t* __restrict__ phase, int32_t nX, DF* u) {
+                            const int32_t* __restrict__ gid, const int32_t* __restrict__ phase, int32_t nX, G* u) {
   if (gate[1].done) return;
   MGRID_STRIDE(j, nX) {
-    if (phase[gid[j]] == kConfirm) u[j] = df_from(s64[j] * isig[j]);
+    if (phase[gid[j]] == kConfirm) u[j] = to_gather<G>(s64[j] * isig[j]);
   }
 }
 
-// float-pair gathered vector: dst[j] = s[user(j)] * isig[user(j)] for j in [lo, hi)
-__global__ void k_to_gathered_df(DF* dst, const double* __restrict__ s, const double* __restrict__ isig, int32_t nX,
-                                 int32_t nR, int64_t lo, int64_t hi) {
+// gathered vector of the confirming / final products: dst[j] = s[user(j)] * isig[user(j)]
+template <typename G>
+__global__ void k_to_gathered_g(G* dst, const double* __restrict__ s, const double* __restrict__ isig, int32_t nX,
+                                int32_t nR, int64_t lo, int64_t hi) {
   MGRID_STRIDE(i, hi - lo) {
     const int64_t j = lo + i;
     const int64_t user = j < nX ? j : j + nR;
-    dst[j] = df_from(s[user] * isig[user]);
+    dst[j] = to_gather<G>(s[user] * isig[user]);
   }
 }
 
@@ -426,14 +431,17 @@ struct Multi {
   MState* host = nullptr;              // pinned, 2 slots
   // vectors
   DBuf<double> s64, u64, gap_row, psi, psi_sum;  // u64 holds float pairs (8 bytes per entry)
-  DF* u64df() const { return reinterpret_cast<DF*>(u64.get()); }
+  template <typename G>
+  G* u64as() const {
+    return reinterpret_cast<G*>(u64.get());
+  }
   DBuf<float> v0, va, vb;
   // graph-build scratch of the hook
   DBuf<unsigned long long> bnorm_bits;
   // captured step pairs
-  cudaGraphExec_t exec = nullptr;
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};  // captured step pairs: [0] FP64, [1] float-pair products
   int pairs_per_replay = 4;
-  int launches_per_replay = 0;
+  int launches_per_replay[2] = {0, 0};
   bool solved = false;
 };
 
@@ -660,6 +668,7 @@ int group_step(Multi& M, cudaStream_t s, int mode) {
 // One step pair: a series step of the SERIES graphs reading v_in and writing v_out, their
 // stop tests, then the FP64 step of the CONFIRM graphs (whose residual, if the test fails,
 // is written to v_out for the next series step) and their tests.  Returns the launches.
+template <typename G>
 int step_pair(Multi& M, cudaStream_t s, const float* v_in, float* v_out) {
   Graph& g = M.g;
   int launches = 0;
@@ -667,13 +676,13 @@ int step_pair(Multi& M, cudaStream_t s, const float* v_in, float* v_out) {
                 TileGate{M.tile_g.get(), M.cnt_series.get()}};
   launches += multi_product<float>(M, s, v_in, es, M.gate.get() + 0);
   launches += group_step(M, s, 0);
-  k_confirm_u<<<mgrid(g.nX), 256, 0, s>>>(M.gate.get(), M.s64.get(), g.isig64.get(), M.gid.get(), M.phase.get(), g.nX,
-                                          M.u64df());
+  k_confirm_u<G><<<mgrid(g.nX), 256, 0, s>>>(M.gate.get(), M.s64.get(), g.isig64.get(), M.gid.get(), M.phase.get(),
+                                             g.nX, M.u64as<G>());
   PSI_LAUNCHED();
   ++launches;
-  EpiResidM er{g.c64.get(), g.mu64.get(), g.isig64.get(), M.s64.get(), v_out, g.nX, M.gid.get(), M.phase.get(),
+  EpiResidM<G> er{g.c64.get(), g.mu64.get(), g.isig64.get(), M.s64.get(), v_out, g.nX, M.gid.get(), M.phase.get(),
                M.gap_row.get(), TileGate{M.tile_g.get(), M.cnt_confirm.get()}};
-  launches += multi_product<DF>(M, s, M.u64df(), er, M.gate.get() + 1);
+  launches += multi_product<G>(M, s, M.u64as<G>(), er, M.gate.get() + 1);
   launches += group_step(M, s, 1);
   return launches;
 }
@@ -688,7 +697,8 @@ void read_vec_m(std::vector<T>& h, const T* d, size_t k, cudaStream_t s) {
 // Captures pairs_per_replay step pairs (an even number: buffers alternate va -> vb -> va)
 // into a CUDA graph on a private stream.  Kernel arguments are device pointers only, so the
 // graph serves every later solve of the object.
-int capture_pairs(Multi& M) {
+template <typename G>
+int capture_pairs(Multi& M, cudaGraphExec_t* exec) {
   cudaStream_t cs = nullptr;
   PSI_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   cudaGraph_t graph = nullptr;
@@ -702,7 +712,7 @@ int capture_pairs(Multi& M) {
     for (int p = 0; p < M.pairs_per_replay; ++p) {
       float* in = (p & 1) ? M.va.get() : M.vb.get();
       float* out = (p & 1) ? M.vb.get() : M.va.get();
-      launches += step_pair(M, cs, in, out);
+      launches += step_pair<G>(M, cs, in, out);
     }
   } catch (...) {
     cudaStreamEndCapture(cs, &graph);
@@ -714,7 +724,7 @@ int capture_pairs(Multi& M) {
   e = cudaStreamEndCapture(cs, &graph);
   cudaStreamDestroy(cs);
   if (e != cudaSuccess) throw_cuda(e, "cudaStreamEndCapture", __FILE__, __LINE__);
-  e = cudaGraphInstantiate(&M.exec, graph, 0);
+  e = cudaGraphInstantiate(exec, graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) throw_cuda(e, "cudaGraphInstantiate", __FILE__, __LINE__);
   return launches;
@@ -732,6 +742,22 @@ psi_status multi_solve(Multi& M, double eps, int32_t max_iter, psi_solve_info* i
   const int64_t nu = (int64_t)g.nX + g.nU;
   const int G = M.G;
   M.solved = false;
+  // float pairs in the confirming and final products when every graph's tolerance is far
+  // above their rounding (as in the single-graph path), FP64 otherwise
+  bool pairs = true;
+  {
+    std::vector<double> sc;
+    read_vec_m(sc, M.scale.get(), (size_t)G, s);
+    for (int q = 0; q < G; ++q)
+      pairs = pairs && eps / sc[q] >= std::ldexp(1.0, -30) * (double)(M.h_noff[q + 1] - M.h_noff[q]);
+  }
+  const int variant = pairs ? 1 : 0;
+  auto to_gathered = [&](const double* src, int64_t lo, int64_t hi) {
+    if (hi <= lo) return;
+    if (pairs) k_to_gathered_g<DF><<<mgrid(hi - lo), 256, 0, s>>>(M.u64as<DF>(), src, g.isig64.get(), nX, nR, lo, hi);
+    else k_to_gathered_g<double><<<mgrid(hi - lo), 256, 0, s>>>(M.u64as<double>(), src, g.isig64.get(), nX, nR, lo, hi);
+    PSI_LAUNCHED();
+  };
   cudaEvent_t t0, t1;
   PSI_CUDA(cudaEventCreate(&t0));
   PSI_CUDA(cudaEventCreate(&t1));
@@ -751,10 +777,7 @@ psi_status multi_solve(Multi& M, double eps, int32_t max_iter, psi_solve_info* i
     k_to_gathered<float><<<mgrid(nu), 256, 0, s>>>(M.v0.get(), g.c32.get(), g.isig32.get(), nX, nR, 0, nu);
     PSI_LAUNCHED();
   }
-  if (g.nU > 0) {
-    k_to_gathered_df<<<mgrid(g.nU), 256, 0, s>>>(M.u64df(), g.c64.get(), g.isig64.get(), nX, nR, nX, nu);
-    PSI_LAUNCHED();
-  }
+  if (g.nU > 0) to_gathered(g.c64.get(), nX, nu);
   const bool iterate = (1.0 > eps) && max_iter > 0;  // Algorithm 2's loop test with gap = 1
   {
     // every graph starts in SERIES; prefix counts and gates to match
@@ -784,20 +807,22 @@ psi_status multi_solve(Multi& M, double eps, int32_t max_iter, psi_solve_info* i
   }
   if (iterate) {
     // first pair from v0 (plain launches), then replays of the captured pairs
-    step_pair(M, s, M.v0.get(), M.vb.get());
-    if (!M.exec) {
-      M.launches_per_replay = capture_pairs(M);
-      count_launches(-M.launches_per_replay);  // captured, not run
+    if (pairs) step_pair<DF>(M, s, M.v0.get(), M.vb.get());
+    else step_pair<double>(M, s, M.v0.get(), M.vb.get());
+    if (!M.exec[variant]) {
+      M.launches_per_replay[variant] =
+          pairs ? capture_pairs<DF>(M, &M.exec[variant]) : capture_pairs<double>(M, &M.exec[variant]);
+      count_launches(-M.launches_per_replay[variant]);  // captured, not run
     }
     // every pair advances each graph that is not DONE by one step, so max_iter pairs end
     // the loop; the bound below only guards against a broken state
     const int64_t max_replays = (int64_t)max_iter / M.pairs_per_replay + 3;
-    const int per_replay = M.launches_per_replay;
+    const int per_replay = M.launches_per_replay[variant];
     cudaEvent_t evs[2];
     PSI_CUDA(cudaEventCreateWithFlags(&evs[0], cudaEventDisableTiming));
     PSI_CUDA(cudaEventCreateWithFlags(&evs[1], cudaEventDisableTiming));
     auto replay = [&](int slot) {
-      PSI_CUDA(cudaGraphLaunch(M.exec, s));
+      PSI_CUDA(cudaGraphLaunch(M.exec[variant], s));
       for (int q = 0; q < per_replay; ++q) count_launch();
       PSI_CUDA(cudaMemcpyAsync(M.host + slot, M.st.get(), sizeof(MState), cudaMemcpyDeviceToHost, s));
       PSI_CUDA(cudaEventRecord(evs[slot], s));
@@ -819,12 +844,14 @@ psi_status multi_solve(Multi& M, double eps, int32_t max_iter, psi_solve_info* i
     PSI_REQUIRE(finished || M.host[r & 1].all_done, PSI_ERR_CUDA, "internal: the step loop did not finish");
   }
   // final step of Algorithm 2 for every graph: psi = (s B + d) / N_g, one more product
-  if (nX > 0) {
-    k_to_gathered_df<<<mgrid(nX), 256, 0, s>>>(M.u64df(), M.s64.get(), g.isig64.get(), nX, nR, 0, nX);
-    PSI_LAUNCHED();
+  if (nX > 0) to_gathered(M.s64.get(), 0, nX);
+  if (pairs) {
+    EpiFinalM<DF> ef{g.lam64.get(), g.d64.get(), M.psi.get(), M.gid.get(), M.n_of.get()};
+    multi_product<DF>(M, s, M.u64as<DF>(), ef, M.gate.get() + 2);
+  } else {
+    EpiFinalM<double> ef{g.lam64.get(), g.d64.get(), M.psi.get(), M.gid.get(), M.n_of.get()};
+    multi_product<double>(M, s, M.u64as<double>(), ef, M.gate.get() + 2);
   }
-  EpiFinalM ef{g.lam64.get(), g.d64.get(), M.psi.get(), M.gid.get(), M.n_of.get()};
-  multi_product<DF>(M, s, M.u64df(), ef, M.gate.get() + 2);
   if (g.n_rows < n) {
     k_psi_nonrow_m<<<mgrid(n - g.n_rows), 256, 0, s>>>(M.psi.get(), g.d64.get(), M.gid.get(), M.n_of.get(), g.n_rows, n);
     PSI_LAUNCHED();
@@ -907,8 +934,10 @@ const T* on_device(const T* p, size_t count, DBuf<T>& buf, Allocator& al, cudaSt
 void release_multi(Multi* M) {
   if (!M) return;
   cudaStreamSynchronize(M->g.stream);
-  if (M->exec) cudaGraphExecDestroy(M->exec);
-  M->exec = nullptr;
+  for (auto& e : M->exec) {
+    if (e) cudaGraphExecDestroy(e);
+    e = nullptr;
+  }
   if (M->host) cudaFreeHost(M->host);
   M->host = nullptr;
   if (M->g.host_state) cudaFreeHost(M->g.host_state);

@@ -79,12 +79,13 @@ __global__ void k_to_u(T* dst, const S* s, const T* isig, int32_t nX, int32_t nR
   }
 }
 
-// the same into a float-pair gathered vector: dst[i] = s[user(i)] * isig[user(i)]
-__global__ void k_to_u_df(DF* dst, const double* s, const double* isig, int32_t nX, int32_t nR, int64_t lo,
-                          int64_t hi) {
+// the same into the gathered vector of a confirming or final product (FP64 or float pairs)
+template <typename G>
+__global__ void k_to_u_g(G* dst, const double* s, const double* isig, int32_t nX, int32_t nR, int64_t lo,
+                         int64_t hi) {
   for (int64_t i = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < hi; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t user = i < nX ? i : i + nR;
-    dst[i] = df_from(s[user] * isig[user]);
+    dst[i] = to_gather<G>(s[user] * isig[user]);
   }
 }
 
@@ -441,31 +442,33 @@ psi_status solve_with(Graph& g, const SolveConsts& K, const SolveTarget& T, doub
     g.last_s_kind = (steps & 1) ? 3 : 2;
     u_final32 = (steps == 0) ? u_first : ub[steps & 1];
   } else {  // PSI_FP32_REFINE
+    auto refine = [&](auto gather_tag) {
+      using G = decltype(gather_tag);
     double* s64 = g.s64.get();
-    // gathered vectors of the confirming and final products: float pairs (DF) in the FP64
-    // buffers (8 bytes per entry either way)
-    DF* ub[2] = {reinterpret_cast<DF*>(g.u64a.get()), reinterpret_cast<DF*>(g.u64b.get())};
+    // gathered vectors of the confirming and final products in the FP64 buffers (8 bytes
+    // per entry either way)
+    G* ub[2] = {reinterpret_cast<G*>(g.u64a.get()), reinterpret_cast<G*>(g.u64b.get())};
     float* v0 = g.u32c.get();
     float* vb[2] = {g.u32a.get(), g.u32b.get()};
     for (int b = 0; b < 2; ++b) {
       fill<double>(reinterpret_cast<double*>(ub[b]), nu + 1, 0.0, s);  // zero bits: a zero pair
-      k_to_u_df<<<eg, 256, 0, s>>>(ub[b], K.c64, K.isig64, nX, nR, nX, nu);  // U = c/sigma
+      k_to_u_g<G><<<eg, 256, 0, s>>>(ub[b], K.c64, K.isig64, nX, nR, nX, nu);  // U = c/sigma
       PSI_LAUNCHED();
       fill<float>(vb[b], nu + 1, 0.0f, s);  // series terms of U users vanish after the first
     }
     fill<float>(v0, nu + 1, 0.0f, s);
     int cur_u = 0;            // FP64 buffer that will hold u of the current s64
     bool u_current = false;   // whether it does now
-    const DF* u_resid_in = nullptr;
+    const G* u_resid_in = nullptr;
     bool resid_first = false;
     if (init_s) {
       load_init(g, s, init_s, s64);
       u0_64.reset(g.al, (size_t)nu + 1);
       fill<double>(u0_64.get(), nu + 1, 0.0, s);
-      k_to_u_df<<<eg, 256, 0, s>>>(reinterpret_cast<DF*>(u0_64.get()), s64, K.isig64, nX, nR, 0, nu);
+      k_to_u_g<G><<<eg, 256, 0, s>>>(reinterpret_cast<G*>(u0_64.get()), s64, K.isig64, nX, nR, 0, nu);
       PSI_LAUNCHED();
       if (iterate) nonrow_start(g, s, s64, K.c64);
-      u_resid_in = reinterpret_cast<const DF*>(u0_64.get());  // the first step is an FP64 step from s_0
+      u_resid_in = reinterpret_cast<const G*>(u0_64.get());  // the first step is an FP64 step from s_0
       resid_first = true;
     } else {
       PSI_CUDA(cudaMemcpyAsync(s64, K.c64, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
@@ -489,7 +492,7 @@ psi_status solve_with(Graph& g, const SolveConsts& K, const SolveTarget& T, doub
           DevState h = read_state(g, s);
           if (!h.converged) break;  // the step cap came first
           // FP64 gathered vector of the series' s64 (X users; U hold c/sigma)
-          k_to_u_df<<<eg, 256, 0, s>>>(ub[cur_u], s64, K.isig64, nX, nR, 0, nX);
+          k_to_u_g<G><<<eg, 256, 0, s>>>(ub[cur_u], s64, K.isig64, nX, nR, 0, nX);
           PSI_LAUNCHED();
           u_current = true;
           u_resid_in = ub[cur_u];
@@ -501,10 +504,10 @@ psi_status solve_with(Graph& g, const SolveConsts& K, const SolveTarget& T, doub
         }
         // one FP64 step s <- s A + c from s64; its gap is the one tested
         size_t first = ev_phase.size();
-        DF* u_out = ub[cur_u ^ 1];
+        G* u_out = ub[cur_u ^ 1];
         DevState h = run_single(g, s, st, [&]() {
-          EpiResid e{K.c64, K.mu64, K.isig64, s64, u_out, v0, nX};
-          st.step<DF>(u_resid_in, e);
+          EpiResid<G> e{K.c64, K.mu64, K.isig64, s64, u_out, v0, nX};
+          st.step<G>(u_resid_in, e);
         });
         timed.push_back({first, h.phase_iters, true});
         if (h.phase_iters == 0) break;  // the step cap came first
@@ -515,14 +518,22 @@ psi_status solve_with(Graph& g, const SolveConsts& K, const SolveTarget& T, doub
       }
     }
     if (!u_current) {  // psi from the current s64 (after a capped series, or no loop)
-      k_to_u_df<<<eg, 256, 0, s>>>(ub[cur_u], s64, K.isig64, nX, nR, 0, nX);
+      k_to_u_g<G><<<eg, 256, 0, s>>>(ub[cur_u], s64, K.isig64, nX, nR, 0, nX);
       PSI_LAUNCHED();
     }
     g.last_s_kind = 0;
     // without any step, psi comes from s_0 itself (a warm start reaches U users too)
-    u_final_df = (!iterate && init_s) ? reinterpret_cast<const DF*>(u0_64.get()) : ub[cur_u];
+    const G* u_fin = (!iterate && init_s) ? reinterpret_cast<const G*>(u0_64.get()) : ub[cur_u];
+    if constexpr (std::is_same<G, DF>::value) u_final_df = u_fin;
+    else u_final64 = u_fin;
+    };
+    // The confirming and final products sum float pairs (~48 bits) when the tolerance is
+    // far above their rounding (about 2^-46 of ||s||_1 per step); for tighter tolerances,
+    // such as an absolute s-tolerance of 1e-9 on millions of users, they sum in FP64.
+    const bool use_pairs = eps / T.scale >= std::ldexp(1.0, -30) * (double)n;
+    if (use_pairs) refine(DF{});
+    else refine(double{});
   }
-
   // final step of Algorithm 2: psi^T = (s^T B + d^T) / N, one more product
   NvtxRange final_range("psi solve: final");
   const DevState h = read_state(g, s);

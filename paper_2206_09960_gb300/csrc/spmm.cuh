@@ -65,17 +65,28 @@ struct EpiSeriesS {
 // Confirming step for S scenarios: s_new = c + mu*y, r = s_new - s, s = s_new,
 // u_new = s_new/sigma (next gather, float pairs), v32 = r/sigma (start of the next series);
 // inactive scenarios keep their state.  The product sums float pairs; the update is FP64.
+__device__ __forceinline__ double2 pair_value(double2 y) { return y; }
+__device__ __forceinline__ double2 pair_value(DF2 y) { return make_double2(df_value(y.a), df_value(y.b)); }
+template <typename V>
+__device__ __forceinline__ V pair_gather(double x, double y);
+template <>
+__device__ __forceinline__ double2 pair_gather<double2>(double x, double y) { return make_double2(x, y); }
+template <>
+__device__ __forceinline__ DF2 pair_gather<DF2>(double x, double y) { return DF2{df_from(x), df_from(y)}; }
+
+// V = DF2 (float pairs) when the tolerance is far above their rounding, double2 otherwise.
+template <typename V>
 struct EpiResidS {
   const double2* c;
   const double2* mu;
   const double2* isig;
   double2* s64;
-  DF2* u_new;
+  V* u_new;
   float2* v32;
   int32_t nX;
-  __device__ __forceinline__ void row(int32_t r, int lane, DF2 yp, const int* act, double2& gap) const {
+  __device__ __forceinline__ void row(int32_t r, int lane, V yp, const int* act, double2& gap) const {
     const int64_t o = (int64_t)r * 32 + lane;
-    const double2 y = make_double2(df_value(yp.a), df_value(yp.b));
+    const double2 y = pair_value(yp);
     const double2 cc = c[o], mm = mu[o], s = s64[o];
     double2 sn = make_double2(cc.x + mm.x * y.x, cc.y + mm.y * y.y);
     if (!act[0]) sn.x = s.x;
@@ -86,21 +97,22 @@ struct EpiResidS {
     s64[o] = sn;
     if (r < nX) {
       const double2 is = isig[o];
-      u_new[o] = DF2{df_from(sn.x * is.x), df_from(sn.y * is.y)};
+      u_new[o] = pair_gather<V>(sn.x * is.x, sn.y * is.y);
       v32[o] = make_float2((float)(rr.x * is.x), (float)(rr.y * is.y));
     }
   }
 };
 
 // psi_s = (lambda_s * G(s_s) + d_s) / N for every scenario.
+template <typename V>
 struct EpiFinalS {
   const double2* lam;
   const double2* d;
   double2* psi;
   double n;
-  __device__ __forceinline__ void row(int32_t r, int lane, DF2 yp, const int*, double2&) const {
+  __device__ __forceinline__ void row(int32_t r, int lane, V yp, const int*, double2&) const {
     const int64_t o = (int64_t)r * 32 + lane;
-    const double2 y = make_double2(df_value(yp.a), df_value(yp.b));
+    const double2 y = pair_value(yp);
     const double2 l = lam[o], dd = d[o];
     psi[o] = make_double2((l.x * y.x + dd.x) / n, (l.y * y.y + dd.y) / n);
   }

@@ -107,32 +107,7 @@ struct EpiSeries {
   }
 };
 
-// Confirming step from the FP64 iterate: s_new = c + mu*y, r = s_new - s, gap += |r|,
-// s = s_new, u_new = s_new/sigma (next gather, as a float pair), v32 = r/sigma (start of an
-// FP32 correction series).  The product sums float pairs; the row's update is FP64.
-struct EpiResid {
-  const double* c;
-  const double* mu;
-  const double* isig;
-  double* s64;
-  DF* u_new;
-  float* v32;
-  int32_t nX;
-  __device__ __forceinline__ void row(int32_t r, DF yp, double& gap, uint64_t pol_s, uint64_t pol_k) const {
-    const double y = df_value(yp);
-    double sn = ld_stream(c + r, pol_s) + ld_stream(mu + r, pol_s) * y;
-    double rr = sn - s64[r];
-    gap += fabs(rr);
-    s64[r] = sn;
-    if (r < nX) {
-      double is = ld_stream(isig + r, pol_s);
-      st_keep(u_new + r, df_from(sn * is), pol_k);
-      v32[r] = (float)(rr * is);
-    }
-  }
-};
-
-// Final step of Algorithm 2: psi_r = (lambda_r * G(s)_r + d_r) / N.
+// y of a product, as FP64, and an FP64 value in a product's gather format
 template <typename T>
 __device__ __forceinline__ double as_double(T y) {
   return (double)y;
@@ -141,6 +116,43 @@ template <>
 __device__ __forceinline__ double as_double<DF>(DF y) {
   return df_value(y);
 }
+template <typename G>
+__device__ __forceinline__ G to_gather(double x) {
+  return (G)x;
+}
+template <>
+__device__ __forceinline__ DF to_gather<DF>(double x) {
+  return df_from(x);
+}
+
+// Confirming step from the FP64 iterate: s_new = c + mu*y, r = s_new - s, gap += |r|,
+// s = s_new, u_new = s_new/sigma (next gather), v32 = r/sigma (start of an FP32 correction
+// series).  G is the product's gather and sum type: DF (float pairs) when the tolerance is
+// far above their rounding, double otherwise; the row's update is FP64 either way.
+template <typename G>
+struct EpiResid {
+  const double* c;
+  const double* mu;
+  const double* isig;
+  double* s64;
+  G* u_new;
+  float* v32;
+  int32_t nX;
+  __device__ __forceinline__ void row(int32_t r, G yp, double& gap, uint64_t pol_s, uint64_t pol_k) const {
+    const double y = as_double(yp);
+    double sn = ld_stream(c + r, pol_s) + ld_stream(mu + r, pol_s) * y;
+    double rr = sn - s64[r];
+    gap += fabs(rr);
+    s64[r] = sn;
+    if (r < nX) {
+      double is = ld_stream(isig + r, pol_s);
+      st_keep(u_new + r, to_gather<G>(sn * is), pol_k);
+      v32[r] = (float)(rr * is);
+    }
+  }
+};
+
+// Final step of Algorithm 2: psi_r = (lambda_r * G(s)_r + d_r) / N.
 template <typename T>
 struct EpiFinal {
   const double* lam;

@@ -120,3 +120,16 @@ def test_batch_errors():
     with pytest.raises(PsiError) as e:
         batch_solve(n, f, l, big_l, big_m, 1e-8)
     assert e.value.status == B.PSI_ERR_INVALID_ARG
+
+
+def test_batch_tight_absolute_tolerance():
+    w = psigen.workload("rmat", seed=42, scale=12)
+    n = w["n"]
+    lam, mu = _rates(n, 4, 11)
+    out = batch_solve(n, w["follower"], w["leader"], lam, mu, 1e-10, tol_mode="s_abs")
+    assert out["status"] == "PSI_OK"
+    for q in range(4):
+        ref = oracle.solve(n, w["follower"], w["leader"], lam[q], mu[q], eps=1e-10, tol_mode=oracle.TOL_S_ABS)
+        # refinement rounds of the FP32 series: more steps than plain FP64, but boundedly
+        assert out["infos"][q]["iters"] <= 2 * ref["iters"] + 10
+        assert rel_l1(out["psi"][q], ref["psi"]) <= 1e-9

@@ -211,3 +211,14 @@ def test_multi_errors():
         assert e.value.status == B.PSI_ERR_INVALID_ARG
         ids, _ = mg.topk(3)
         assert ids.shape == (2, 3)
+
+
+def test_multi_tight_absolute_tolerance():
+    w = psigen.multi_workload(4, seed=43, n_lo=500, n_hi=4000)
+    out = multi_solve(w, eps=1e-11, tol_mode="s_abs")
+    assert out["status"] == "PSI_OK"
+    for q, (n, f, l, lam, mu) in enumerate(_split(w)):
+        ref = oracle.solve(n, f, l, lam, mu, eps=1e-11, tol_mode=oracle.TOL_S_ABS)
+        # refinement rounds of the FP32 series: more steps than plain FP64, but boundedly
+        assert out["infos"][q]["iters"] <= 2 * ref["iters"] + 10
+        assert rel_l1(out["psi"][sum(int(x) for x in w["n_g"][:q]):][:n], ref["psi"]) <= 1e-9

@@ -328,3 +328,18 @@ def test_profile_reports_kernel_time():
     assert info["spmv_timed"] + info["refine_timed"] == info["iters"]
     assert info["refine_timed"] == info["refinements"] >= 1
     assert 0 < info["spmv_ms"] + info["refine_ms"] <= info["ms"]
+
+
+def test_tight_absolute_tolerance_takes_the_fp64_products():
+    """An absolute s-tolerance near the FP64 floor: the default mode must switch its
+    confirming and final products from float pairs to FP64 (float-pair rounding alone would
+    keep the gap above eps and the solve would stall).  Its FP32 series still needs a few
+    refinement rounds for such a target, so it takes more steps than the FP64 mode, but
+    boundedly more, and ends at the same psi."""
+    w = psigen.workload("rmat", seed=41, scale=14)
+    args = (w["n"], w["follower"], w["leader"], w["lam"], w["mu"], 1e-10)
+    ref = gpu_solve(*args, precision="fp64", tol_mode="s_abs")
+    out = gpu_solve(*args, precision="fp32_refine", tol_mode="s_abs")
+    assert ref["info"]["converged"] and out["info"]["converged"]
+    assert out["info"]["iters"] <= 2 * ref["info"]["iters"] + 10, (out["info"]["iters"], ref["info"]["iters"])
+    assert rel_l1(out["psi"], ref["psi"]) <= 1e-12
