@@ -374,8 +374,7 @@ void run_store_product(const int32_t* row_ptr, const int32_t* col, const Schedul
   PSI_CUDA(cudaMemsetAsync(st.get(), 0, sizeof(DevState), s));
   int per_sm = 0;
   PSI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmv<W, EpiStore2>, kSpmvThreads, 0));
-  int grid = (per_sm > 0 ? per_sm : 1) * (int)num_sms();
-  if (grid > sc.tiles) grid = sc.tiles;
+  const int grid = spmv_blocks(per_sm, sc.tiles);
   DBuf<double> gap_part(al, (size_t)grid);
   DBuf<W> carry_head(al, (size_t)sc.tiles), carry_tail(al, (size_t)sc.tiles);
   SpmvArgs a{};

@@ -160,17 +160,16 @@ __device__ __forceinline__ void ld_stream_v8(const int* p, uint64_t pol, int (&c
 }
 
 // ---------------------------------------------------------------- sizes
-#ifndef PSI_SPMV_ITEMS
-#define PSI_SPMV_ITEMS 8
-#endif
-#ifndef PSI_SPMV_PREFETCH
-#define PSI_SPMV_PREFETCH 0
-#endif
+// One warp sums one tile of kSpmvTile consecutive nonzeros, in kSpmvSteps steps of
+// kSpmvStep nonzeros (kSpmvItems per lane: one 32-byte index load).
 constexpr int kSpmvThreads = 256;
-constexpr int kSpmvItems = PSI_SPMV_ITEMS;             // nnz per thread per tile (multiple of 8)
-constexpr int kSpmvTile = kSpmvThreads * kSpmvItems;   // nnz per tile
-constexpr bool kSpmvPrefetch = PSI_SPMV_PREFETCH != 0; // gather the next tile while finishing this one
-static_assert(kSpmvItems % 8 == 0, "column loads are 32-byte vectors");
+constexpr int kSpmvWarps = kSpmvThreads / 32;
+constexpr int kSpmvItems = 8;
+constexpr int kSpmvStep = 32 * kSpmvItems;
+constexpr int kSpmvTile = 2048;
+constexpr int kSpmvSteps = kSpmvTile / kSpmvStep;
+static_assert(kSpmvItems == 8, "a lane's row ends are one byte of the tile's bitmap");
+static_assert(kSpmvTile % kSpmvStep == 0, "whole steps per tile");
 
 // ---------------------------------------------------------------- device-side loop state
 struct DevState {

@@ -606,8 +606,7 @@ int multi_spmv_grid(int tiles) {
     PSI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_spmv<T, Epi>, kSpmvThreads, 0));
     per_sm = b > 0 ? b : 1;
   }
-  const int grid = per_sm * (int)num_sms();
-  return grid < tiles ? grid : tiles;
+  return spmv_blocks(per_sm, tiles);
 }
 
 // product + fix-up of one step, skipped on the device when gate->done

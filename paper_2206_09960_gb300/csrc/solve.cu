@@ -138,14 +138,14 @@ void fill(T* x, int64_t n, T v, cudaStream_t s) {
 }
 
 template <typename T, typename Epi>
-int spmv_grid() {
+int spmv_grid(int32_t tiles) {
   static int per_sm = -1;
   if (per_sm < 0) {
     int b = 0;
     PSI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_spmv<T, Epi>, kSpmvThreads, 0));
     per_sm = b > 0 ? b : 1;
   }
-  return per_sm * (int)num_sms();
+  return spmv_blocks(per_sm, tiles);
 }
 
 }  // namespace
@@ -181,8 +181,7 @@ struct Stepper {
       PSI_CUDA(cudaEventRecord(e0, s));
     }
     if (g.num_tiles > 0) {
-      grid = spmv_grid<T, Epi>();
-      if (grid > g.num_tiles) grid = g.num_tiles;
+      grid = spmv_grid<T, Epi>(g.num_tiles);
       k_spmv<T, Epi><<<grid, kSpmvThreads, 0, s>>>(a, u, epi);
       PSI_LAUNCHED();
     }

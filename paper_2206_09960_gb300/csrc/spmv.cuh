@@ -7,12 +7,12 @@
 // (the transposed CSR: rows = leaders, columns = followers) followed by a per-row
 // epilogue; no per-edge value is stored.
 //
-// Load balance is merge-based: the nonzeros are cut into fixed tiles of kSpmvTile (each
-// thread owns kSpmvItems consecutive nonzeros, loaded as two 16-byte vectors), rows are
-// found by a binary search over the tile's slice of row_ptr, and partial row sums are
-// joined by a block-wide segmented scan.  A row that starts in an earlier tile is closed
-// by the fix-up kernel, which adds the tile carries in tile order.  Every sum therefore
-// runs in an order fixed by the graph alone: results are bit-reproducible.
+// Load balance is merge-based: the nonzeros are cut into fixed tiles of kSpmvTile, one
+// warp per tile; row boundaries inside a tile come from a bitmap of row ends built from
+// the tile's slice of row_ptr, and partial row sums are joined by warp segmented scans and
+// a register carried from step to step.  A row that starts in an earlier tile is closed by
+// the fix-up kernel, which adds the tile carries in tile order.  Every sum therefore runs
+// in an order fixed by the graph alone: results are bit-reproducible.
 #pragma once
 
 #include "common.cuh"
@@ -67,6 +67,20 @@ __device__ __forceinline__ DF2 shfl_up_t<DF2>(DF2 v, int o) {
 template <>
 __device__ __forceinline__ DF2 shfl_xor_t<DF2>(DF2 v, int o) {
   return DF2(shfl_xor_t(v.a, o), shfl_xor_t(v.b, o));
+}
+template <typename T>
+__device__ __forceinline__ T shfl_idx_t(T v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+template <>
+__device__ __forceinline__ D2 shfl_idx_t<D2>(D2 v, int src) {
+  return D2(__shfl_sync(0xffffffffu, v.a, src), __shfl_sync(0xffffffffu, v.b, src));
+}
+template <>
+__device__ __forceinline__ DF shfl_idx_t<DF>(DF v, int src) {
+  return DF(__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src));
+}
+template <>
+__device__ __forceinline__ DF2 shfl_idx_t<DF2>(DF2 v, int src) {
+  return DF2(shfl_idx_t(v.a, src), shfl_idx_t(v.b, src));
 }
 
 // ------------------------------------------------------------------ epilogues
@@ -230,125 +244,157 @@ struct tile_skip_of<E, decltype((void)E::kTileSkip)> {
   static constexpr bool value = E::kTileSkip;
 };
 
+// Blocks for a product over `tiles` tiles: `per_sm` resident blocks on every SM, and no
+// more blocks than the tiles fill (one tile per warp).
+inline int spmv_blocks(int per_sm, int32_t tiles) {
+  const int64_t cap = (int64_t)(per_sm > 0 ? per_sm : 1) * num_sms();
+  const int64_t need = ceil_div(tiles > 0 ? tiles : 1, kSpmvWarps);
+  return (int)(need < cap ? need : cap);
+}
+
+// One warp per tile; the warps of all blocks walk the tiles with a grid-wide stride.  A
+// tile's row ends are first marked in a bitmap in shared memory (bit q: nonzero nnz0 + q is
+// the last one of its row) from the tile's slice of row_ptr.  Every row has at least one
+// nonzero, so the k-th row end of the tile belongs to row tile_row[tile] + k.  Each step
+// covers kSpmvStep nonzeros, kSpmvItems per lane: a lane sums its items, closing a row at
+// every marked item; the pieces that cross lanes are joined by a warp segmented scan, and
+// the sum of the row still open after the step is carried to the next step in a register.
+// Closed rows are staged in shared memory and their epilogues run 32 rows at a time, one
+// row per lane (coalesced).  The gathers of the next step are issued before the current
+// step is reduced.  No block barrier is taken inside the tile loop.
 template <typename T, typename Epi>
 __global__ void __launch_bounds__(kSpmvThreads) k_spmv(SpmvArgs a, const T* __restrict__ u, Epi epi) {
   constexpr bool kSkip = tile_skip_of<Epi>::value;
+  constexpr int kWords = kSpmvTile / 32;  // bitmap words of a tile
+  constexpr int kSlots = 32 + kSpmvStep;  // < 32 rows left staged + the row ends of one step
   if (a.state->done) return;
-  __shared__ int32_t rp[kSpmvTile + 2];  // row_ptr slice of the tile's rows
-  __shared__ T ys[kSpmvTile + 1];        // G(.) of every row that ends in the tile
-  __shared__ int wf[kSpmvThreads / 32];
-  __shared__ T wv[kSpmvThreads / 32];
-  __shared__ double gsh[kSpmvThreads / 32];
+  __shared__ uint32_t ends_sh[kSpmvWarps][kWords];
+  __shared__ T stage_sh[kSpmvWarps][kSlots];
+  __shared__ double gsh[kSpmvWarps];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t* ends = ends_sh[warp];
+  T* stage = stage_sh[warp];
   const uint64_t pol_s = policy_evict_first();
   const uint64_t pol_k = policy_evict_last();
   T* carry_head = static_cast<T*>(a.carry_head);
   T* carry_tail = static_cast<T*>(a.carry_tail);
+  const int32_t stride = (int32_t)gridDim.x * kSpmvWarps;
   double gap = 0.0;
 
-  // column indices and gathered values of one tile: this thread's kSpmvItems nonzeros
-  // (col is padded to whole tiles, pad entries point at u[n] = 0)
-  auto gather_tile = [&](int32_t t, T (&x)[kSpmvItems]) {
-    const int* cp = a.col + (int64_t)t * kSpmvTile + (int64_t)threadIdx.x * kSpmvItems;
+  // column indices and gathered values of step k of a tile: this lane's kSpmvItems
+  // nonzeros (col is padded to whole tiles, pad entries point at u[n] = 0)
+  auto gather_step = [&](int32_t t, int k, T (&x)[kSpmvItems]) {
+    int c[kSpmvItems];
+    ld_stream_v8(a.col + (int64_t)t * kSpmvTile + k * kSpmvStep + lane * kSpmvItems, pol_s, c);
 #pragma unroll
-    for (int q = 0; q < kSpmvItems / 8; ++q) {
-      int c[8];
-      ld_stream_v8(cp + 8 * q, pol_s, c);
-#pragma unroll
-      for (int j = 0; j < 8; ++j) x[8 * q + j] = ld_gather(u + c[j], pol_k);
-    }
+    for (int j = 0; j < kSpmvItems; ++j) x[j] = ld_gather(u + c[j], pol_k);
   };
-  T xn[kSpmvItems];
-  if (!kSkip && (int32_t)blockIdx.x < a.num_tiles) gather_tile(blockIdx.x, xn);
-
-  for (int32_t tile = blockIdx.x; tile < a.num_tiles; tile += gridDim.x) {
+  auto next_on = [&](int32_t t) {  // this warp's first tile from t on that is not turned off
     if constexpr (kSkip) {
-      if (!epi.tile_on(tile)) continue;  // uniform over the block
+      while (t < a.num_tiles && !epi.tile_on(t)) t += stride;
     }
-    const int64_t nnz0 = (int64_t)tile * kSpmvTile;
-    const int64_t nnz1 = nnz0 + kSpmvTile < a.m ? nnz0 + kSpmvTile : a.m;
+    return t;
+  };
+
+  int32_t tile = next_on((int32_t)blockIdx.x * kSpmvWarps + warp);
+  T xn[kSpmvItems];
+  if (tile < a.num_tiles) gather_step(tile, 0, xn);
+  while (tile < a.num_tiles) {
+    const int32_t nnz0 = tile * kSpmvTile;  // < m < 2^31
     const int32_t r0 = a.tile_row[tile];
-    const int32_t r_hi = a.tile_row[tile + 1];
-    const int32_t nr = r_hi - r0 + 1;  // rows touching [nnz0, nnz0 + tile)
-    __syncthreads();                    // shared buffers are reused across tiles
-    if constexpr (kSkip) gather_tile(tile, xn);
-    for (int i = threadIdx.x; i <= nr; i += kSpmvThreads) rp[i] = ld_stream(a.row_ptr + r0 + i, pol_s);
-    const int64_t p0 = nnz0 + (int64_t)threadIdx.x * kSpmvItems;
-    T x[kSpmvItems];
-#pragma unroll
-    for (int i = 0; i < kSpmvItems; ++i) x[i] = xn[i];
-    const int32_t next = tile + gridDim.x;
-    if (kSpmvPrefetch && !kSkip) {
-      if (next < a.num_tiles) gather_tile(next, xn);
-    } else {
-      (void)next;
+    const int32_t nr = a.tile_row[tile + 1] - r0 + 1;  // rows touching the tile
+    const int32_t next = next_on(tile + stride);
+    for (int w = lane; w < kWords; w += 32) ends[w] = 0u;
+    __syncwarp();
+    const bool head_open = ld_stream(a.row_ptr + r0, pol_s) < nnz0;  // row r0 began earlier
+    for (int i = lane; i < nr; i += 32) {
+      const int32_t q = ld_stream(a.row_ptr + r0 + i + 1, pol_s) - 1 - nnz0;
+      if ((uint32_t)q < (uint32_t)kSpmvTile) atomicOr(ends + (q >> 5), 1u << (q & 31));
     }
-    __syncthreads();
-    // first row whose end lies beyond p0
-    int lo = 0, hi = nr;
-    while (lo < hi) {
-      int mid = (lo + hi) >> 1;
-      if ((int64_t)rp[mid + 1] > p0) hi = mid; else lo = mid + 1;
-    }
-    int cur = lo;
-    int64_t next_end = cur < nr ? (int64_t)rp[cur + 1] : INT64_MAX;
-    T acc = T(0), first_val = T(0);
-    int has_end = 0, first_row = 0;
+    __syncwarp();
+
+    T open = T(0);        // sum of the row left open by the last step
+    int staged = 0;       // row sums waiting in stage[0, staged), in row order
+    int32_t closed = 0;   // row ends of the tile whose sums have left the stage
+    // epilogues of `count` staged rows from slot `pos`; the first row end of a tile whose
+    // first row began in an earlier tile leaves its partial for the fix-up kernel
+    auto flush = [&](int pos, int count) {
+      if (lane < count) {
+        const int32_t j = closed + lane;
+        const T y = stage[pos + lane];
+        if (j == 0 && head_open) carry_head[tile] = y;
+        else epi.row(r0 + j, y, gap, pol_s, pol_k);
+      }
+      closed += count;
+    };
+#pragma unroll 1
+    for (int k = 0; k < kSpmvSteps; ++k) {
+      T x[kSpmvItems];
 #pragma unroll
-    for (int i = 0; i < kSpmvItems; ++i) {
-      acc += x[i];
-      if (p0 + i + 1 == next_end) {  // row `cur` ends at nonzero p0 + i
-        if (!has_end) {
-          has_end = 1;
-          first_row = cur;
-          first_val = acc;
-        } else {
-          ys[cur] = acc;               // the row began inside this thread's span
+      for (int j = 0; j < kSpmvItems; ++j) x[j] = xn[j];
+      if (k + 1 < kSpmvSteps) gather_step(tile, k + 1, xn);
+      else if (next < a.num_tiles) gather_step(next, 0, xn);
+
+      const int bit = k * kSpmvStep + lane * kSpmvItems;
+      const uint32_t e = (ends[bit >> 5] >> (bit & 31)) & 0xffu;  // this lane's row ends
+      const int cnt = __popc(e);
+      int incl = cnt;  // row ends up to this lane
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const int total = __shfl_sync(0xffffffffu, incl, 31);
+      const int s0 = staged + incl - cnt;  // stage slot of this lane's first row end
+      // rows that begin and end inside this lane go to the stage now; the head (up to the
+      // first row end) waits for the sum carried in from the lanes before
+      T acc = lane == 0 ? open : T(0);
+      T head = T(0);
+      int sl = s0;
+#pragma unroll
+      for (int j = 0; j < kSpmvItems; ++j) {
+        acc += x[j];
+        if ((e >> j) & 1u) {
+          if (sl == s0) head = acc;
+          else stage[sl] = acc;
+          ++sl;
+          acc = T(0);
         }
-        acc = T(0);
-        ++cur;
-        next_end = cur < nr ? (int64_t)rp[cur + 1] : INT64_MAX;
+      }
+      // segmented scan of (has a row end, sum after the last row end) in lane order
+      int f = cnt > 0;
+      T v = acc;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int fu = __shfl_up_sync(0xffffffffu, f, o);
+        const T vu = shfl_up_t(v, o);
+        if (lane >= o) seg_join(fu, vu, f, v);
+      }
+      T ve = shfl_up_t(v, 1);  // carried into this lane
+      if (lane == 0) ve = T(0);
+      if (cnt > 0) stage[s0] = ve + head;
+      open = shfl_idx_t(v, 31);
+      staged += total;
+      __syncwarp();
+      if (staged >= 32) {
+        int pos = 0;
+        do {
+          flush(pos, 32);
+          pos += 32;
+        } while (staged - pos >= 32);
+        const int rem = staged - pos;
+        T keep = T(0);
+        if (lane < rem) keep = stage[pos + lane];
+        __syncwarp();
+        if (lane < rem) stage[lane] = keep;
+        __syncwarp();
+        staged = rem;
       }
     }
-    // block-wide segmented scan of (has_end, acc) in thread order
-    int f = has_end;
-    T v = acc;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      int fu = __shfl_up_sync(0xffffffffu, f, o);
-      T vu = shfl_up_t(v, o);
-      if (lane >= o) seg_join(fu, vu, f, v);
-    }
-    if (lane == 31) { wf[warp] = f; wv[warp] = v; }
-    int fe = __shfl_up_sync(0xffffffffu, f, 1);  // exclusive within the warp
-    T ve = shfl_up_t(v, 1);
-    if (lane == 0) { fe = 0; ve = T(0); }
-    __syncthreads();
-    int fw = 0;  // inclusive prefix of the warps before this one
-    T vw = T(0);
-    for (int w = 0; w < warp; ++w) {
-      int g = wf[w];
-      T gv = wv[w];
-      seg_join(fw, vw, g, gv);
-      fw = g;
-      vw = gv;
-    }
-    seg_join(fw, vw, fe, ve);  // exclusive prefix of this thread
-    if (has_end) ys[first_row] = ve + first_val;
-    if (threadIdx.x == kSpmvThreads - 1) {
-      seg_join(fw, vw, f, v);  // inclusive prefix of the whole tile
-      carry_tail[tile] = v;
-    }
-    __syncthreads();
-    // epilogues of the rows that end in this tile, one row per thread, coalesced; a first
-    // row that began in an earlier tile leaves its partial for the fix-up kernel
-    const bool head_open = (int64_t)rp[0] < nnz0;
-    for (int i = threadIdx.x; i < nr; i += kSpmvThreads) {
-      if ((int64_t)rp[i + 1] > nnz1) break;  // this row and the next ones end later
-      if (i == 0 && head_open) carry_head[tile] = ys[0];
-      else epi.row(r0 + i, ys[i], gap, pol_s, pol_k);
-    }
-    if (!kSpmvPrefetch && !kSkip && next < a.num_tiles) gather_tile(next, xn);
+    flush(0, staged);
+    if (lane == 0) carry_tail[tile] = open;  // the sum after the tile's last row end
+    __syncwarp();  // the bitmap and the stage are rewritten for the next tile
+    tile = next;
   }
   // per-CTA gap partial, fixed order
 #pragma unroll
@@ -357,7 +403,7 @@ __global__ void __launch_bounds__(kSpmvThreads) k_spmv(SpmvArgs a, const T* __re
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
-    for (int w = 0; w < kSpmvThreads / 32; ++w) t += gsh[w];
+    for (int w = 0; w < kSpmvWarps; ++w) t += gsh[w];
     a.gap_part[blockIdx.x] = t;
   }
 }

@@ -326,8 +326,7 @@ void compute_features(Graph& g, float* x) {
   PSI_CUDA(cudaMemsetAsync(st.get(), 0, sizeof(DevState), s));
   int per_sm = 0;
   PSI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmv<D2, EpiMean2>, kSpmvThreads, 0));
-  int grid = (per_sm > 0 ? per_sm : 1) * (int)num_sms();
-  if (grid > g.num_tiles) grid = g.num_tiles;
+  const int grid = spmv_blocks(per_sm, g.num_tiles);
   DBuf<double> gap_part(al, (size_t)grid);
   DBuf<D2> ch(al, (size_t)g.num_tiles), ct(al, (size_t)g.num_tiles);
   for (int c0 = 4; c0 <= 6; c0 += 2) {
