@@ -256,24 +256,33 @@ inline int spmv_blocks(int per_sm, int32_t tiles) {
 // tile's row ends are first marked in a bitmap in shared memory (bit q: nonzero nnz0 + q is
 // the last one of its row) from the tile's slice of row_ptr.  Every row has at least one
 // nonzero, so the k-th row end of the tile belongs to row tile_row[tile] + k.  Each step
-// covers kSpmvStep nonzeros, kSpmvItems per lane: a lane sums its items, closing a row at
-// every marked item; the pieces that cross lanes are joined by a warp segmented scan, and
-// the sum of the row still open after the step is carried to the next step in a register.
-// Closed rows are staged in shared memory and their epilogues run 32 rows at a time, one
-// row per lane (coalesced).  The gathers of the next step are issued before the current
-// step is reduced.  No block barrier is taken inside the tile loop.
+// covers kSpmvStep nonzeros, kSpmvItems per lane: a lane sums its items and runs the
+// epilogue of every row that begins and ends among them at once; the row of its first row
+// end, which may have begun in earlier lanes, is completed by a warp segmented scan and
+// closed by the same lane, and the sum of the row still open after the step is carried to
+// the next step in a register.  The gathers of the next step are issued before the current
+// step is reduced.  No block barrier is taken inside the tile loop, and shared memory holds
+// only the bitmaps, which leaves the rest of the SM's on-chip memory to the L1 that serves
+// the gathers.
+// Resident blocks per SM the register allocation must allow (measured at R-MAT scale 25):
+// the products are bound by gather latency and gain from more warps, down to 48 registers
+// for FP32 sums (5 blocks; 6 spill) and 64 for 8-byte sums (4 blocks); the 16-byte pair
+// sums of the graph build keep their registers.
+template <typename T>
+constexpr int spmv_min_blocks() {
+  return sizeof(T) == 4 ? 5 : (sizeof(T) == 8 ? 4 : 1);
+}
+
 template <typename T, typename Epi>
-__global__ void __launch_bounds__(kSpmvThreads) k_spmv(SpmvArgs a, const T* __restrict__ u, Epi epi) {
+__global__ void __launch_bounds__(kSpmvThreads, spmv_min_blocks<T>())
+    k_spmv(SpmvArgs a, const T* __restrict__ u, Epi epi) {
   constexpr bool kSkip = tile_skip_of<Epi>::value;
   constexpr int kWords = kSpmvTile / 32;  // bitmap words of a tile
-  constexpr int kSlots = 32 + kSpmvStep;  // < 32 rows left staged + the row ends of one step
   if (a.state->done) return;
   __shared__ uint32_t ends_sh[kSpmvWarps][kWords];
-  __shared__ T stage_sh[kSpmvWarps][kSlots];
   __shared__ double gsh[kSpmvWarps];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t* ends = ends_sh[warp];
-  T* stage = stage_sh[warp];
   const uint64_t pol_s = policy_evict_first();
   const uint64_t pol_k = policy_evict_last();
   T* carry_head = static_cast<T*>(a.carry_head);
@@ -313,20 +322,8 @@ __global__ void __launch_bounds__(kSpmvThreads) k_spmv(SpmvArgs a, const T* __re
     }
     __syncwarp();
 
-    T open = T(0);        // sum of the row left open by the last step
-    int staged = 0;       // row sums waiting in stage[0, staged), in row order
-    int32_t closed = 0;   // row ends of the tile whose sums have left the stage
-    // epilogues of `count` staged rows from slot `pos`; the first row end of a tile whose
-    // first row began in an earlier tile leaves its partial for the fix-up kernel
-    auto flush = [&](int pos, int count) {
-      if (lane < count) {
-        const int32_t j = closed + lane;
-        const T y = stage[pos + lane];
-        if (j == 0 && head_open) carry_head[tile] = y;
-        else epi.row(r0 + j, y, gap, pol_s, pol_k);
-      }
-      closed += count;
-    };
+    T open = T(0);      // sum of the row left open by the last step
+    int32_t done = 0;   // row ends of the tile in the steps before this one
 #pragma unroll 1
     for (int k = 0; k < kSpmvSteps; ++k) {
       T x[kSpmvItems];
@@ -344,20 +341,20 @@ __global__ void __launch_bounds__(kSpmvThreads) k_spmv(SpmvArgs a, const T* __re
         const int y = __shfl_up_sync(0xffffffffu, incl, o);
         if (lane >= o) incl += y;
       }
-      const int total = __shfl_sync(0xffffffffu, incl, 31);
-      const int s0 = staged + incl - cnt;  // stage slot of this lane's first row end
-      // rows that begin and end inside this lane go to the stage now; the head (up to the
-      // first row end) waits for the sum carried in from the lanes before
+      const int32_t j0 = done + incl - cnt;  // index in the tile of this lane's first row end
+      done += __shfl_sync(0xffffffffu, incl, 31);
+      // rows that begin and end inside this lane are closed now; the head (up to the first
+      // row end) waits for the sum carried in from the lanes before
       T acc = lane == 0 ? open : T(0);
       T head = T(0);
-      int sl = s0;
+      int32_t jr = j0;
 #pragma unroll
       for (int j = 0; j < kSpmvItems; ++j) {
         acc += x[j];
         if ((e >> j) & 1u) {
-          if (sl == s0) head = acc;
-          else stage[sl] = acc;
-          ++sl;
+          if (jr == j0) head = acc;
+          else epi.row(r0 + jr, acc, gap, pol_s, pol_k);
+          ++jr;
           acc = T(0);
         }
       }
@@ -372,28 +369,17 @@ __global__ void __launch_bounds__(kSpmvThreads) k_spmv(SpmvArgs a, const T* __re
       }
       T ve = shfl_up_t(v, 1);  // carried into this lane
       if (lane == 0) ve = T(0);
-      if (cnt > 0) stage[s0] = ve + head;
       open = shfl_idx_t(v, 31);
-      staged += total;
-      __syncwarp();
-      if (staged >= 32) {
-        int pos = 0;
-        do {
-          flush(pos, 32);
-          pos += 32;
-        } while (staged - pos >= 32);
-        const int rem = staged - pos;
-        T keep = T(0);
-        if (lane < rem) keep = stage[pos + lane];
-        __syncwarp();
-        if (lane < rem) stage[lane] = keep;
-        __syncwarp();
-        staged = rem;
+      // the first row end of a tile whose first row began in an earlier tile leaves its
+      // partial for the fix-up kernel
+      if (cnt > 0) {
+        const T y = ve + head;
+        if (j0 == 0 && head_open) carry_head[tile] = y;
+        else epi.row(r0 + j0, y, gap, pol_s, pol_k);
       }
     }
-    flush(0, staged);
     if (lane == 0) carry_tail[tile] = open;  // the sum after the tile's last row end
-    __syncwarp();  // the bitmap and the stage are rewritten for the next tile
+    __syncwarp();  // the bitmap is rewritten for the next tile
     tile = next;
   }
   // per-CTA gap partial, fixed order
