@@ -290,11 +290,12 @@ __global__ void __launch_bounds__(kSpmvThreads, spmv_min_blocks<T>())
   const int32_t stride = (int32_t)gridDim.x * kSpmvWarps;
   double gap = 0.0;
 
-  // column indices and gathered values of step k of a tile: this lane's kSpmvItems
-  // nonzeros (col is padded to whole tiles, pad entries point at u[n] = 0)
-  auto gather_step = [&](int32_t t, int k, T (&x)[kSpmvItems]) {
-    int c[kSpmvItems];
+  // column indices of step k of a tile (this lane's kSpmvItems nonzeros; col is padded to
+  // whole tiles, pad entries point at u[n] = 0) and their gathered values
+  auto load_cols = [&](int32_t t, int k, int (&c)[kSpmvItems]) {
     ld_stream_v8(a.col + (int64_t)t * kSpmvTile + k * kSpmvStep + lane * kSpmvItems, pol_s, c);
+  };
+  auto gather = [&](const int (&c)[kSpmvItems], T (&x)[kSpmvItems]) {
 #pragma unroll
     for (int j = 0; j < kSpmvItems; ++j) x[j] = ld_gather(u + c[j], pol_k);
   };
@@ -306,8 +307,17 @@ __global__ void __launch_bounds__(kSpmvThreads, spmv_min_blocks<T>())
   };
 
   int32_t tile = next_on((int32_t)blockIdx.x * kSpmvWarps + warp);
+  // software pipeline: the values of the next step are in flight while a step is reduced,
+  // and the column indices of the step after it, so its gathers issue without waiting
   T xn[kSpmvItems];
-  if (tile < a.num_tiles) gather_step(tile, 0, xn);
+  int cn[kSpmvItems];
+  static_assert(kSpmvSteps >= 2, "the index loads run two steps ahead within a tile");
+  if (tile < a.num_tiles) {
+    int c0[kSpmvItems];
+    load_cols(tile, 0, c0);
+    gather(c0, xn);
+    load_cols(tile, 1, cn);
+  }
   while (tile < a.num_tiles) {
     const int32_t nnz0 = tile * kSpmvTile;  // < m < 2^31
     const int32_t r0 = a.tile_row[tile];
@@ -329,8 +339,9 @@ __global__ void __launch_bounds__(kSpmvThreads, spmv_min_blocks<T>())
       T x[kSpmvItems];
 #pragma unroll
       for (int j = 0; j < kSpmvItems; ++j) x[j] = xn[j];
-      if (k + 1 < kSpmvSteps) gather_step(tile, k + 1, xn);
-      else if (next < a.num_tiles) gather_step(next, 0, xn);
+      if (k + 1 < kSpmvSteps || next < a.num_tiles) gather(cn, xn);
+      if (k + 2 < kSpmvSteps) load_cols(tile, k + 2, cn);
+      else if (next < a.num_tiles) load_cols(next, k + 2 - kSpmvSteps, cn);
 
       const int bit = k * kSpmvStep + lane * kSpmvItems;
       const uint32_t e = (ends[bit >> 5] >> (bit & 31)) & 0xffu;  // this lane's row ends
