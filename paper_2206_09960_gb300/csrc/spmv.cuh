@@ -222,15 +222,6 @@ struct FixArgs {
   const void* carry_tail;
 };
 
-// Segmented scan element: f = a row ended inside the span, v = sum after the last row
-// end.  Combining a left span L with the right span R that follows it:
-//   (L.f | R.f, R.f ? R.v : L.v + R.v).
-template <typename T>
-__device__ __forceinline__ void seg_join(int lf, T lv, int& rf, T& rv) {  // R <- L . R
-  if (!rf) rv = lv + rv;
-  rf |= lf;
-}
-
 // An epilogue may declare `static constexpr bool kTileSkip = true` and a member
 // `bool tile_on(int32_t tile) const`: tiles it turns off are neither gathered nor reduced
 // (their rows get no epilogue call).  Used when several independent graphs share one
@@ -266,11 +257,11 @@ inline int spmv_blocks(int per_sm, int32_t tiles) {
 // the gathers.
 // Resident blocks per SM the register allocation must allow (measured at R-MAT scale 25):
 // the products are bound by gather latency and gain from more warps, down to 48 registers
-// for FP32 sums (5 blocks; 6 spill) and 64 for 8-byte sums (4 blocks); the 16-byte pair
-// sums of the graph build keep their registers.
+// for FP32 sums (5 blocks; 6 spill), 64 for 8-byte sums (4 blocks) and 128 for the
+// 16-byte pair sums of the graph build (2 blocks).
 template <typename T>
 constexpr int spmv_min_blocks() {
-  return sizeof(T) == 4 ? 5 : (sizeof(T) == 8 ? 4 : 1);
+  return sizeof(T) == 4 ? 5 : (sizeof(T) == 8 ? 4 : 2);
 }
 
 template <typename T, typename Epi>
@@ -346,14 +337,17 @@ __global__ void __launch_bounds__(kSpmvThreads, spmv_min_blocks<T>())
       const int bit = k * kSpmvStep + lane * kSpmvItems;
       const uint32_t e = (ends[bit >> 5] >> (bit & 31)) & 0xffu;  // this lane's row ends
       const int cnt = __popc(e);
-      int incl = cnt;  // row ends up to this lane
+      // row ends in the lanes before this one and in the whole step, one ballot per item
+      const uint32_t below = (1u << lane) - 1u;
+      int before = 0, total = 0;
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
+      for (int j = 0; j < kSpmvItems; ++j) {
+        const uint32_t b = __ballot_sync(0xffffffffu, (e >> j) & 1u);
+        before += __popc(b & below);
+        total += __popc(b);
       }
-      const int32_t j0 = done + incl - cnt;  // index in the tile of this lane's first row end
-      done += __shfl_sync(0xffffffffu, incl, 31);
+      const int32_t j0 = done + before;  // index in the tile of this lane's first row end
+      done += total;
       // rows that begin and end inside this lane are closed now; the head (up to the first
       // row end) waits for the sum carried in from the lanes before
       T acc = lane == 0 ? open : T(0);
@@ -369,14 +363,15 @@ __global__ void __launch_bounds__(kSpmvThreads, spmv_min_blocks<T>())
           acc = T(0);
         }
       }
-      // segmented scan of (has a row end, sum after the last row end) in lane order
-      int f = cnt > 0;
+      // segmented inclusive scan of the sums after each lane's last row end: after offset o
+      // a lane holds the sum over lanes max(lane - 2o + 1, last_end) .. lane, so it adds its
+      // partner's value only while no row end lies in its own window
+      const int last_end = 31 - __clz(__ballot_sync(0xffffffffu, cnt > 0) & (below | (1u << lane)));
       T v = acc;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
-        const int fu = __shfl_up_sync(0xffffffffu, f, o);
         const T vu = shfl_up_t(v, o);
-        if (lane >= o) seg_join(fu, vu, f, v);
+        if (lane >= o && last_end <= lane - o) v = vu + v;
       }
       T ve = shfl_up_t(v, 1);  // carried into this lane
       if (lane == 0) ve = T(0);
