@@ -92,6 +92,11 @@ typedef struct psi_options {
                           the gathered iterate is compact in L2; 0: keep the input order
                           within each class.  Results do not depend on it beyond rounding. */
   int32_t profile;     /* 1: time every sparse product with CUDA events (psi_solve_info) */
+  int32_t spmv_tile;   /* nonzeros per tile of the sparse product (one warp per tile): 0
+                          (default) picks 2048, 1024 or 512 from the edge count so that small
+                          graphs still spread over every SM (psi_multi_create: 512); else
+                          one of 512, 1024, 2048.  Results do not depend on it beyond
+                          rounding. */
   void* stream;        /* cudaStream_t to queue all work on */
   const psi_allocator* allocator; /* NULL: cudaMallocAsync on stream */
 } psi_options;
@@ -127,6 +132,7 @@ typedef struct psi_graph_stats {
   double rho_inf;         /* max_j sum_{l in L(j)} mu_l / sigma_j (< 1: contraction rate bound) */
   double build_ms;        /* wall time of psi_graph_create on the stream */
   int64_t device_bytes;   /* device memory held by the handle */
+  int64_t spmv_tile;      /* nonzeros per tile of the sparse product (psi_options.spmv_tile) */
 } psi_graph_stats;
 
 /*

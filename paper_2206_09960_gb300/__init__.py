@@ -73,7 +73,7 @@ class Graph:
 
     def __init__(self, n, follower, leader, lam, mu, precision="fp32_refine", tol_mode="psi",
                  bnorm_mode="none", self_loops="reject", reorder=True, profile=False, stream=None,
-                 allocator="torch"):
+                 allocator="torch", spmv_tile=0):
         import torch
 
         B.load()
@@ -86,6 +86,7 @@ class Graph:
         opt.self_loops = B.SELF_LOOPS[self_loops]
         opt.reorder = 1 if reorder else 0
         opt.profile = 1 if profile else 0
+        opt.spmv_tile = int(spmv_tile)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -174,7 +175,7 @@ class Batch:
     ``lam``/``mu`` are [S, n] FP64 (scenario-major), host or device; 1 <= S <= 64."""
 
     def __init__(self, n, follower, leader, lam, mu, tol_mode="psi", bnorm_mode="none", self_loops="reject",
-                 reorder=True, stream=None, allocator="torch"):
+                 reorder=True, stream=None, allocator="torch", spmv_tile=0):
         import torch
 
         B.load()
@@ -186,6 +187,7 @@ class Batch:
         opt.bnorm_mode = B.BNORM_MODE[bnorm_mode]
         opt.self_loops = B.SELF_LOOPS[self_loops]
         opt.reorder = 1 if reorder else 0
+        opt.spmv_tile = int(spmv_tile)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -248,7 +250,7 @@ class Multi:
     one after another (sum of n_g values).  Host (numpy) or device (torch) arrays."""
 
     def __init__(self, n_g, m_g, follower, leader, lam, mu, tol_mode="psi", bnorm_mode="none",
-                 self_loops="reject", reorder=True, stream=None, allocator="torch"):
+                 self_loops="reject", reorder=True, stream=None, allocator="torch", spmv_tile=0):
         import torch
 
         B.load()
@@ -262,6 +264,7 @@ class Multi:
         opt.bnorm_mode = B.BNORM_MODE[bnorm_mode]
         opt.self_loops = B.SELF_LOOPS[self_loops]
         opt.reorder = 1 if reorder else 0
+        opt.spmv_tile = int(spmv_tile)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream

@@ -185,6 +185,7 @@ void psi_options_default(psi_options* opt) {
   opt->self_loops = PSI_REJECT;
   opt->reorder = 1;
   opt->profile = 0;
+  opt->spmv_tile = 0;
   opt->stream = nullptr;
   opt->allocator = nullptr;
 }
@@ -208,6 +209,8 @@ psi_status psi_graph_create(int64_t n, int64_t m, const int32_t* follower, const
     PSI_REQUIRE(o.bnorm_mode == PSI_BNORM_NONE || o.bnorm_mode == PSI_BNORM_INF, PSI_ERR_INVALID_ARG,
                 "unknown bnorm_mode");
     PSI_REQUIRE(o.self_loops == PSI_REJECT || o.self_loops == PSI_DROP, PSI_ERR_INVALID_ARG, "unknown self_loops");
+    PSI_REQUIRE(o.spmv_tile == 0 || o.spmv_tile == 512 || o.spmv_tile == 1024 || o.spmv_tile == 2048,
+                PSI_ERR_INVALID_ARG, "spmv_tile must be 0, 512, 1024 or 2048");
     h = new psi_graph();
     h->g.opt = o;
     h->g.stream = static_cast<cudaStream_t>(o.stream);
@@ -350,6 +353,7 @@ psi_status psi_graph_get_stats(const psi_graph* g, psi_graph_stats* st) {
   st->rho_inf = gg.rho_inf;
   st->build_ms = gg.build_ms;
   st->device_bytes = gg.al.live_bytes;
+  st->spmv_tile = gg.tile;
   return PSI_OK;
 }
 

@@ -344,7 +344,7 @@ SpmmArgs spmm_args(Batch& b) {
   Graph& g = b.g;
   SpmmArgs a{};
   a.row_ptr = g.row_ptr.get();
-  a.col = g.col.get();  // padded to whole 2048-nonzero tiles, a multiple of the chunk
+  a.col = g.col.get();  // padded to a multiple of kSpmvTileMax nonzeros, a multiple of the chunk
   a.chunk_row = b.sched.tile_row.get();
   a.num_chunks = b.sched.tiles;
   a.n_rows = g.n_rows;
@@ -643,6 +643,8 @@ psi_status psi_batch_create(int64_t n, int64_t m, const int32_t* follower, const
     PSI_REQUIRE(o.bnorm_mode == PSI_BNORM_NONE || o.bnorm_mode == PSI_BNORM_INF, PSI_ERR_INVALID_ARG,
                 "unknown bnorm_mode");
     PSI_REQUIRE(o.self_loops == PSI_REJECT || o.self_loops == PSI_DROP, PSI_ERR_INVALID_ARG, "unknown self_loops");
+    PSI_REQUIRE(o.spmv_tile == 0 || o.spmv_tile == 512 || o.spmv_tile == 1024 || o.spmv_tile == 2048,
+                PSI_ERR_INVALID_ARG, "spmv_tile must be 0, 512, 1024 or 2048");
     o.precision = PSI_FP32_REFINE;
     h = new psi_batch();
     Graph& g = h->b.g;

@@ -340,6 +340,7 @@ T read1(const T* d, cudaStream_t s) {
 Schedule make_schedule(const int32_t* row_ptr, int32_t n_rows, int64_t m, Allocator& al, cudaStream_t s,
                        int32_t tile) {
   Schedule sc;
+  sc.tile = tile;
   sc.tiles = (int32_t)ceil_div(m, tile);
   sc.tile_row.reset(al, (size_t)sc.tiles + 1);
   if (sc.tiles == 0) {
@@ -381,6 +382,7 @@ void run_store_product(const int32_t* row_ptr, const int32_t* col, const Schedul
   a.row_ptr = row_ptr;
   a.col = col;
   a.tile_row = sc.tile_row.get();
+  a.tile = sc.tile;
   a.num_tiles = sc.tiles;
   a.n_rows = n_rows;
   a.m = m;
@@ -391,20 +393,19 @@ void run_store_product(const int32_t* row_ptr, const int32_t* col, const Schedul
   k_spmv<W, EpiStore2><<<grid, kSpmvThreads, 0, s>>>(a, w, epi);
   PSI_LAUNCHED();
   if (sc.num_fix > 0) {
-    int fgrid = (int)ceil_div(sc.num_fix, kFixWarps);
-    const int cap = (int)num_sms() * 8;
-    if (fgrid > cap) fgrid = cap;
+    int fgrid = fix_blocks(sc.num_fix);
     DBuf<double> gap_fix(al, (size_t)fgrid);
     FixArgs f{};
     f.row_ptr = row_ptr;
     f.tile_row = sc.tile_row.get();
+    f.tile = sc.tile;
     f.fix_tile = sc.fix_tile.get();
     f.num_fix = sc.num_fix;
     f.state = st.get();
     f.gap_fix = gap_fix.get();
     f.carry_head = carry_head.get();
     f.carry_tail = carry_tail.get();
-    k_fixup<W, EpiStore2><<<fgrid, kFixWarps * 32, 0, s>>>(f, epi);
+    k_fixup<W, EpiStore2><<<fgrid, kFixThreads, 0, s>>>(f, epi);
     PSI_LAUNCHED();
   }
 }
@@ -592,8 +593,9 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
       mu_count = 0;
     }
     g.m_unique = mu_count;
-    g.num_tiles = (int32_t)ceil_div(mu_count, kSpmvTile);
-    const int64_t padded = (int64_t)g.num_tiles * kSpmvTile;
+    g.tile = g.opt.spmv_tile > 0 ? g.opt.spmv_tile : spmv_tile_for(mu_count);
+    g.num_tiles = (int32_t)ceil_div(mu_count, g.tile);
+    const int64_t padded = ceil_div(mu_count, kSpmvTileMax) * kSpmvTileMax;
     g.col.reset(al, (size_t)(padded > 0 ? padded : 4));
     li.reset(al, (size_t)(mu_count > 0 ? mu_count : 1));
     if (mu_count > 0) {
@@ -641,9 +643,9 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
   if (mu_count > 0) {
     const int64_t mc = mu_count;
     const int32_t n_f = g.nX + g.nU;  // followers: users with leaders
-    const int32_t tiles_f = (int32_t)ceil_div(mc, kSpmvTile);
+    const int32_t tiles_f = (int32_t)ceil_div(mc, kSpmvTileMax);
     DBuf<uint32_t> fk0(al, (size_t)mc), fk1(al, (size_t)mc);
-    DBuf<uint32_t> lv0(al, (size_t)tiles_f * kSpmvTile), lv1(al, (size_t)mc);
+    DBuf<uint32_t> lv0(al, (size_t)tiles_f * kSpmvTileMax), lv1(al, (size_t)mc);
     // keys: the followers' gathered indices (the transposed CSR's columns, left untouched);
     // values: the leader rows (non-negative int32, read as uint32)
     bool alt = radix_sort<uint32_t>(fk0.get(), fk1.get(), lv0.get(), lv1.get(), mc, b, al, s,
@@ -660,9 +662,9 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
     } else {
       lpad = std::move(lv0);
     }
-    if ((int64_t)tiles_f * kSpmvTile > mc) {
-      k_fill_i32<<<grid_for((int64_t)tiles_f * kSpmvTile - mc), 256, 0, s>>>(reinterpret_cast<int32_t*>(ls), mc,
-                                                                            (int64_t)tiles_f * kSpmvTile, (int32_t)n);
+    if ((int64_t)tiles_f * kSpmvTileMax > mc) {
+      k_fill_i32<<<grid_for((int64_t)tiles_f * kSpmvTileMax - mc), 256, 0, s>>>(reinterpret_cast<int32_t*>(ls), mc,
+                                                                            (int64_t)tiles_f * kSpmvTileMax, (int32_t)n);
       PSI_LAUNCHED();
     }
     DBuf<int32_t> rp_f(al, (size_t)n_f + 1);
@@ -676,7 +678,7 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
     fk0.release();
     fk1.release();
     lv1.release();
-    Schedule sch = make_schedule(rp_f.get(), n_f, mc, al, s, kSpmvTile);
+    Schedule sch = make_schedule(rp_f.get(), n_f, mc, al, s, kSpmvTileMax);
     // sigma and beta: FP64 sums in the FP64 mode, float-pair sums otherwise (FP64 adds are
     // slow on this part; ~48-bit sums are far inside the FP32-series mode's accuracy)
     if (g.opt.precision == PSI_FP64) {
@@ -731,7 +733,7 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
   phases.next("psi build 6: schedule");
   // ---- 6. tile schedule of the Power-psi product
   {
-    Schedule sch = make_schedule(g.row_ptr.get(), g.n_rows, mu_count, al, s, kSpmvTile);
+    Schedule sch = make_schedule(g.row_ptr.get(), g.n_rows, mu_count, al, s, g.tile);
     g.tile_row = std::move(sch.tile_row);
     g.fix_tile = std::move(sch.fix_tile);
     g.num_fix = sch.num_fix;

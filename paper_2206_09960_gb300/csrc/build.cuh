@@ -11,6 +11,7 @@ namespace psi {
 struct Schedule {
   DBuf<int32_t> tile_row;  // [tiles + 1]: row holding the tile's first nonzero
   DBuf<int32_t> fix_tile;  // tiles whose first row began in an earlier tile
+  int32_t tile = kSpmvTileMax;  // nonzeros per tile
   int32_t tiles = 0;
   int32_t num_fix = 0;
 };

@@ -160,16 +160,17 @@ __device__ __forceinline__ void ld_stream_v8(const int* p, uint64_t pol, int (&c
 }
 
 // ---------------------------------------------------------------- sizes
-// One warp sums one tile of kSpmvTile consecutive nonzeros, in kSpmvSteps steps of
-// kSpmvStep nonzeros (kSpmvItems per lane: one 32-byte index load).
+// One warp sums one tile of `tile` consecutive nonzeros (kSpmvTileMin .. kSpmvTileMax, a
+// power of two chosen per graph), in steps of kSpmvStep nonzeros (kSpmvItems per lane: one
+// 32-byte index load).  Column arrays are padded to a multiple of kSpmvTileMax.
 constexpr int kSpmvThreads = 256;
 constexpr int kSpmvWarps = kSpmvThreads / 32;
 constexpr int kSpmvItems = 8;
 constexpr int kSpmvStep = 32 * kSpmvItems;
-constexpr int kSpmvTile = 2048;
-constexpr int kSpmvSteps = kSpmvTile / kSpmvStep;
+constexpr int kSpmvTileMin = 512;
+constexpr int kSpmvTileMax = 2048;
 static_assert(kSpmvItems == 8, "a lane's row ends are one byte of the tile's bitmap");
-static_assert(kSpmvTile % kSpmvStep == 0, "whole steps per tile");
+static_assert(kSpmvTileMin >= 2 * kSpmvStep && kSpmvTileMax % kSpmvTileMin == 0, "whole steps per tile, two at least");
 
 // ---------------------------------------------------------------- device-side loop state
 struct DevState {
@@ -205,9 +206,10 @@ struct Graph {
   DBuf<int32_t> perm;       // internal -> input id [n]
   DBuf<int32_t> n_leaders;  // leaders of each user (internal order), for model features
   DBuf<int32_t> row_ptr;    // [n_rows + 1]
-  DBuf<int32_t> col;        // [m padded to a tile multiple]: internal follower id, pad = n
+  DBuf<int32_t> col;        // [m padded to a multiple of kSpmvTileMax]: internal follower id, pad = n
   DBuf<int32_t> tile_row;   // [num_tiles + 1]: row holding the tile's first nnz
   DBuf<int32_t> fix_tile;   // tiles whose first row started in an earlier tile
+  int32_t tile = kSpmvTileMax;  // nonzeros per tile of the product
   int32_t num_tiles = 0, num_fix = 0;
 
   // per-user constants, internal order

@@ -619,6 +619,7 @@ int multi_product(Multi& M, cudaStream_t s, const T* u, const Epi& epi, const De
     a.row_ptr = g.row_ptr.get();
     a.col = g.col.get();
     a.tile_row = g.tile_row.get();
+    a.tile = g.tile;
     a.num_tiles = g.num_tiles;
     a.n_rows = g.n_rows;
     a.m = g.m_unique;
@@ -634,16 +635,15 @@ int multi_product(Multi& M, cudaStream_t s, const T* u, const Epi& epi, const De
     FixArgs f{};
     f.row_ptr = g.row_ptr.get();
     f.tile_row = g.tile_row.get();
+    f.tile = g.tile;
     f.fix_tile = g.fix_tile.get();
     f.num_fix = g.num_fix;
     f.state = gate;
     f.gap_fix = g.gap_fix.get();
     f.carry_head = g.carry_head.get();
     f.carry_tail = g.carry_tail.get();
-    int fgrid = (int)ceil_div(g.num_fix, kFixWarps);
-    const int cap = (int)num_sms() * 8;
-    if (fgrid > cap) fgrid = cap;
-    k_fixup<T, Epi><<<fgrid, kFixWarps * 32, 0, s>>>(f, epi);
+    int fgrid = fix_blocks(g.num_fix);
+    k_fixup<T, Epi><<<fgrid, kFixThreads, 0, s>>>(f, epi);
     PSI_LAUNCHED();
     ++launches;
   }
@@ -981,7 +981,12 @@ psi_status psi_multi_create(int32_t G, const int64_t* n_g, const int64_t* m_g, c
     PSI_REQUIRE(o.bnorm_mode == PSI_BNORM_NONE || o.bnorm_mode == PSI_BNORM_INF, PSI_ERR_INVALID_ARG,
                 "unknown bnorm_mode");
     PSI_REQUIRE(o.self_loops == PSI_REJECT || o.self_loops == PSI_DROP, PSI_ERR_INVALID_ARG, "unknown self_loops");
+    PSI_REQUIRE(o.spmv_tile == 0 || o.spmv_tile == 512 || o.spmv_tile == 1024 || o.spmv_tile == 2048,
+                PSI_ERR_INVALID_ARG, "spmv_tile must be 0, 512, 1024 or 2048");
     o.precision = PSI_FP32_REFINE;
+    // small tiles: once most graphs have stopped, the few still stepping own few nonzeros,
+    // and every tile is walked by one warp
+    if (o.spmv_tile == 0) o.spmv_tile = 512;
     h = new psi_multi();
     Multi& M = h->m;
     Graph& g = M.g;

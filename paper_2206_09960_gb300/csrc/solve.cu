@@ -166,6 +166,7 @@ struct Stepper {
     a.row_ptr = g.row_ptr.get();
     a.col = g.col.get();
     a.tile_row = g.tile_row.get();
+    a.tile = g.tile;
     a.num_tiles = g.num_tiles;
     a.n_rows = g.n_rows;
     a.m = g.m_unique;
@@ -189,16 +190,15 @@ struct Stepper {
       FixArgs f{};
       f.row_ptr = g.row_ptr.get();
       f.tile_row = g.tile_row.get();
+      f.tile = g.tile;
       f.fix_tile = g.fix_tile.get();
       f.num_fix = g.num_fix;
       f.state = g.state.get();
       f.gap_fix = g.gap_fix.get();
       f.carry_head = g.carry_head.get();
       f.carry_tail = g.carry_tail.get();
-      fgrid = (int)ceil_div(g.num_fix, kFixWarps);
-      int cap = (int)num_sms() * 8;
-      if (fgrid > cap) fgrid = cap;
-      k_fixup<T, Epi><<<fgrid, kFixWarps * 32, 0, s>>>(f, epi);
+      fgrid = fix_blocks(g.num_fix);
+      k_fixup<T, Epi><<<fgrid, kFixThreads, 0, s>>>(f, epi);
       PSI_LAUNCHED();
     }
     if (profile) {

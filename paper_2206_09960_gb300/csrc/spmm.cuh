@@ -18,7 +18,7 @@
 
 namespace psi {
 
-constexpr int kSpmmChunk = 512;  // nonzeros per warp task (a divisor of the 2048-nonzero tiles)
+constexpr int kSpmmChunk = 512;  // nonzeros per warp task (a divisor of kSpmvTileMax)
 constexpr int kSpmmMaxS = 64;    // scenarios per launch (lane l: 2l, 2l+1)
 
 struct SpmmArgs {

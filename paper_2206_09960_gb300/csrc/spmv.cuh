@@ -7,8 +7,8 @@
 // (the transposed CSR: rows = leaders, columns = followers) followed by a per-row
 // epilogue; no per-edge value is stored.
 //
-// Load balance is merge-based: the nonzeros are cut into fixed tiles of kSpmvTile, one
-// warp per tile; row boundaries inside a tile come from a bitmap of row ends built from
+// Load balance is merge-based: the nonzeros are cut into fixed tiles (512 to 2048 per
+// graph), one warp per tile; row boundaries inside a tile come from a bitmap of row ends built from
 // the tile's slice of row_ptr, and partial row sums are joined by warp segmented scans and
 // a register carried from step to step.  A row that starts in an earlier tile is closed by
 // the fix-up kernel, which adds the tile carries in tile order.  Every sum therefore runs
@@ -202,6 +202,7 @@ struct SpmvArgs {
   const int32_t* row_ptr;
   const int32_t* col;
   const int32_t* tile_row;
+  int32_t tile;           // nonzeros per tile: kSpmvTileMin .. kSpmvTileMax, a power of two
   int32_t num_tiles;
   int32_t n_rows;
   int64_t m;
@@ -214,6 +215,7 @@ struct SpmvArgs {
 struct FixArgs {
   const int32_t* row_ptr;
   const int32_t* tile_row;
+  int32_t tile;
   const int32_t* fix_tile;
   int32_t num_fix;
   const DevState* state;
@@ -235,12 +237,31 @@ struct tile_skip_of<E, decltype((void)E::kTileSkip)> {
   static constexpr bool value = E::kTileSkip;
 };
 
+// Nonzeros per tile for a product over m nonzeros: the largest power of two up to
+// kSpmvTileMax that still gives every resident warp of the series product (5 CTAs of 8 warps
+// per SM) four tiles, at least kSpmvTileMin.
+inline int32_t spmv_tile_for(int64_t m) {
+  const int64_t tiles_wanted = num_sms() * 5 * kSpmvWarps * 4;
+  int32_t t = kSpmvTileMax;
+  while (t > kSpmvTileMin && m < (int64_t)t * tiles_wanted) t >>= 1;
+  return t;
+}
+
 // Blocks for a product over `tiles` tiles: `per_sm` resident blocks on every SM, and no
 // more blocks than the tiles fill (one tile per warp).
 inline int spmv_blocks(int per_sm, int32_t tiles) {
   const int64_t cap = (int64_t)(per_sm > 0 ? per_sm : 1) * num_sms();
   const int64_t need = ceil_div(tiles > 0 ? tiles : 1, kSpmvWarps);
   return (int)(need < cap ? need : cap);
+}
+
+// Resident blocks per SM the register allocation must allow (measured at R-MAT scale 25):
+// the products are bound by gather latency and gain from more warps, down to 48 registers
+// for FP32 sums (5 blocks; 6 spill), 64 for 8-byte sums (4 blocks) and 128 for the
+// 16-byte pair sums of the graph build (2 blocks).
+template <typename T>
+constexpr int spmv_min_blocks() {
+  return sizeof(T) == 4 ? 5 : (sizeof(T) == 8 ? 4 : 2);
 }
 
 // One warp per tile; the warps of all blocks walk the tiles with a grid-wide stride.  A
@@ -251,24 +272,15 @@ inline int spmv_blocks(int per_sm, int32_t tiles) {
 // epilogue of every row that begins and ends among them at once; the row of its first row
 // end, which may have begun in earlier lanes, is completed by a warp segmented scan and
 // closed by the same lane, and the sum of the row still open after the step is carried to
-// the next step in a register.  The gathers of the next step are issued before the current
-// step is reduced.  No block barrier is taken inside the tile loop, and shared memory holds
+// the next step in a register.  The gathers of the next step, and the column indices of
+// the step after it, are issued before the current step is reduced.  No block barrier is taken inside the tile loop, and shared memory holds
 // only the bitmaps, which leaves the rest of the SM's on-chip memory to the L1 that serves
 // the gathers.
-// Resident blocks per SM the register allocation must allow (measured at R-MAT scale 25):
-// the products are bound by gather latency and gain from more warps, down to 48 registers
-// for FP32 sums (5 blocks; 6 spill), 64 for 8-byte sums (4 blocks) and 128 for the
-// 16-byte pair sums of the graph build (2 blocks).
-template <typename T>
-constexpr int spmv_min_blocks() {
-  return sizeof(T) == 4 ? 5 : (sizeof(T) == 8 ? 4 : 2);
-}
-
 template <typename T, typename Epi>
 __global__ void __launch_bounds__(kSpmvThreads, spmv_min_blocks<T>())
     k_spmv(SpmvArgs a, const T* __restrict__ u, Epi epi) {
   constexpr bool kSkip = tile_skip_of<Epi>::value;
-  constexpr int kWords = kSpmvTile / 32;  // bitmap words of a tile
+  constexpr int kWords = kSpmvTileMax / 32;  // bitmap words of the largest tile
   if (a.state->done) return;
   __shared__ uint32_t ends_sh[kSpmvWarps][kWords];
   __shared__ double gsh[kSpmvWarps];
@@ -284,7 +296,7 @@ __global__ void __launch_bounds__(kSpmvThreads, spmv_min_blocks<T>())
   // column indices of step k of a tile (this lane's kSpmvItems nonzeros; col is padded to
   // whole tiles, pad entries point at u[n] = 0) and their gathered values
   auto load_cols = [&](int32_t t, int k, int (&c)[kSpmvItems]) {
-    ld_stream_v8(a.col + (int64_t)t * kSpmvTile + k * kSpmvStep + lane * kSpmvItems, pol_s, c);
+    ld_stream_v8(a.col + (int64_t)t * a.tile + k * kSpmvStep + lane * kSpmvItems, pol_s, c);
   };
   auto gather = [&](const int (&c)[kSpmvItems], T (&x)[kSpmvItems]) {
 #pragma unroll
@@ -302,7 +314,8 @@ __global__ void __launch_bounds__(kSpmvThreads, spmv_min_blocks<T>())
   // and the column indices of the step after it, so its gathers issue without waiting
   T xn[kSpmvItems];
   int cn[kSpmvItems];
-  static_assert(kSpmvSteps >= 2, "the index loads run two steps ahead within a tile");
+  const int steps = a.tile / kSpmvStep;  // >= 2: the index loads run two steps ahead
+  const int words = a.tile / 32;
   if (tile < a.num_tiles) {
     int c0[kSpmvItems];
     load_cols(tile, 0, c0);
@@ -310,29 +323,29 @@ __global__ void __launch_bounds__(kSpmvThreads, spmv_min_blocks<T>())
     load_cols(tile, 1, cn);
   }
   while (tile < a.num_tiles) {
-    const int32_t nnz0 = tile * kSpmvTile;  // < m < 2^31
+    const int32_t nnz0 = tile * a.tile;  // < m < 2^31
     const int32_t r0 = a.tile_row[tile];
     const int32_t nr = a.tile_row[tile + 1] - r0 + 1;  // rows touching the tile
     const int32_t next = next_on(tile + stride);
-    for (int w = lane; w < kWords; w += 32) ends[w] = 0u;
+    for (int w = lane; w < words; w += 32) ends[w] = 0u;
     __syncwarp();
     const bool head_open = ld_stream(a.row_ptr + r0, pol_s) < nnz0;  // row r0 began earlier
     for (int i = lane; i < nr; i += 32) {
       const int32_t q = ld_stream(a.row_ptr + r0 + i + 1, pol_s) - 1 - nnz0;
-      if ((uint32_t)q < (uint32_t)kSpmvTile) atomicOr(ends + (q >> 5), 1u << (q & 31));
+      if ((uint32_t)q < (uint32_t)a.tile) atomicOr(ends + (q >> 5), 1u << (q & 31));
     }
     __syncwarp();
 
     T open = T(0);      // sum of the row left open by the last step
     int32_t done = 0;   // row ends of the tile in the steps before this one
 #pragma unroll 1
-    for (int k = 0; k < kSpmvSteps; ++k) {
+    for (int k = 0; k < steps; ++k) {
       T x[kSpmvItems];
 #pragma unroll
       for (int j = 0; j < kSpmvItems; ++j) x[j] = xn[j];
-      if (k + 1 < kSpmvSteps || next < a.num_tiles) gather(cn, xn);
-      if (k + 2 < kSpmvSteps) load_cols(tile, k + 2, cn);
-      else if (next < a.num_tiles) load_cols(next, k + 2 - kSpmvSteps, cn);
+      if (k + 1 < steps || next < a.num_tiles) gather(cn, xn);
+      if (k + 2 < steps) load_cols(tile, k + 2, cn);
+      else if (next < a.num_tiles) load_cols(next, k + 2 - steps, cn);
 
       const int bit = k * kSpmvStep + lane * kSpmvItems;
       const uint32_t e = (ends[bit >> 5] >> (bit & 31)) & 0xffu;  // this lane's row ends
@@ -400,35 +413,49 @@ __global__ void __launch_bounds__(kSpmvThreads, spmv_min_blocks<T>())
   }
 }
 
-constexpr int kFixWarps = 8;  // warps per fix-up block
+constexpr int kFixThreads = 256;  // threads per fix-up block, one fix-up each
 
-// Closes rows that began in an earlier tile: y = sum of the tile carries in tile order
-// plus the partial of the tile where the row ends.
+// Blocks for the fix-up of num_fix rows (at most 8 per SM: the gap_fix buffers' size).
+inline int fix_blocks(int32_t num_fix) {
+  const int64_t need = ceil_div(num_fix > 0 ? num_fix : 1, kFixThreads);
+  const int64_t cap = num_sms() * 8;
+  return (int)(need < cap ? need : cap);
+}
+
+// Closes rows that began in an earlier tile, one row per thread: y = the sum of the tile
+// carries in tile order (four interleaved partial sums, joined pairwise) plus the partial
+// of the tile where the row ends.
 template <typename T, typename Epi>
-__global__ void __launch_bounds__(kFixWarps * 32) k_fixup(FixArgs a, Epi epi) {
+__global__ void __launch_bounds__(kFixThreads) k_fixup(FixArgs a, Epi epi) {
   if (a.state->done) return;
-  __shared__ double gsh[kFixWarps];
+  __shared__ double gsh[kFixThreads / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint64_t pol_s = policy_evict_first();
   const uint64_t pol_k = policy_evict_last();
   const T* ch = static_cast<const T*>(a.carry_head);
   const T* ct = static_cast<const T*>(a.carry_tail);
   double gap = 0.0;
-  for (int32_t q = blockIdx.x * kFixWarps + warp; q < a.num_fix; q += gridDim.x * kFixWarps) {
+  for (int32_t q = blockIdx.x * kFixThreads + threadIdx.x; q < a.num_fix; q += gridDim.x * kFixThreads) {
     const int32_t k = a.fix_tile[q];
     const int32_t r0 = a.tile_row[k];
-    const int32_t ks = a.row_ptr[r0] / kSpmvTile;  // tile where row r0 begins
-    T acc = T(0);
-    for (int32_t kk = ks + lane; kk < k; kk += 32) acc += ct[kk];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += shfl_xor_t(acc, o);
-    if (lane == 0) epi.row(r0, acc + ch[k], gap, pol_s, pol_k);
+    int32_t kk = a.row_ptr[r0] / a.tile;  // tile where row r0 begins
+    T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+    for (; kk + 4 <= k; kk += 4) {
+      s0 += ct[kk];
+      s1 += ct[kk + 1];
+      s2 += ct[kk + 2];
+      s3 += ct[kk + 3];
+    }
+    for (; kk < k; ++kk) s0 += ct[kk];
+    epi.row(r0, ((s0 + s1) + (s2 + s3)) + ch[k], gap, pol_s, pol_k);
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) gap += __shfl_xor_sync(0xffffffffu, gap, o);
   if (lane == 0) gsh[warp] = gap;
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
-    for (int w = 0; w < kFixWarps; ++w) t += gsh[w];
+    for (int w = 0; w < kFixThreads / 32; ++w) t += gsh[w];
     a.gap_fix[blockIdx.x] = t;
   }
 }

@@ -336,6 +336,7 @@ void compute_features(Graph& g, float* x) {
     a.row_ptr = g.row_ptr.get();
     a.col = g.col.get();
     a.tile_row = g.tile_row.get();
+    a.tile = g.tile;
     a.num_tiles = g.num_tiles;
     a.n_rows = g.n_rows;
     a.m = g.m_unique;
@@ -346,20 +347,19 @@ void compute_features(Graph& g, float* x) {
     k_spmv<D2, EpiMean2><<<grid, kSpmvThreads, 0, s>>>(a, u, epi);
     PSI_LAUNCHED();
     if (g.num_fix > 0) {
-      int fgrid = (int)ceil_div(g.num_fix, kFixWarps);
-      const int cap = (int)num_sms() * 8;
-      if (fgrid > cap) fgrid = cap;
+      int fgrid = fix_blocks(g.num_fix);
       DBuf<double> gap_fix(al, (size_t)fgrid);
       FixArgs f{};
       f.row_ptr = g.row_ptr.get();
       f.tile_row = g.tile_row.get();
+      f.tile = g.tile;
       f.fix_tile = g.fix_tile.get();
       f.num_fix = g.num_fix;
       f.state = st.get();
       f.gap_fix = gap_fix.get();
       f.carry_head = ch.get();
       f.carry_tail = ct.get();
-      k_fixup<D2, EpiMean2><<<fgrid, kFixWarps * 32, 0, s>>>(f, epi);
+      k_fixup<D2, EpiMean2><<<fgrid, kFixThreads, 0, s>>>(f, epi);
       PSI_LAUNCHED();
     }
   }

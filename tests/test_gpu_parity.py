@@ -166,19 +166,23 @@ def test_fp32_plain_mode_is_close():
     assert rel_l1(out["psi"], ref["psi"]) <= 2e-5
 
 
-def _run_pair(n, f, l, lam, mu, precision="fp32_refine"):
+def _run_pair(n, f, l, lam, mu, precision="fp32_refine", **kw):
     ref = oracle.solve(n, f, l, lam, mu, to_floor=True, max_iter=20000)
     out = gpu_solve(n, f, l, lam, mu, 1e-14 if precision == "fp64" else 1e-9, precision=precision,
-                    max_iter=20000, k=min(100, n))
+                    max_iter=20000, k=min(100, n), **kw)
     return ref, out
 
 
-@pytest.mark.parametrize("lengths", [[1] * 50, [31, 32, 33], [4096, 1, 2048, 2049, 5], [20000], [2047, 2048, 2049]],
-                         ids=["ones", "warpish", "tiles", "one_long_row", "tile_edges"])
+@pytest.mark.parametrize("lengths", [[1] * 50, [31, 32, 33], [4096, 1, 2048, 2049, 5], [20000], [2047, 2048, 2049],
+                                     [511, 512, 513, 1023, 1024, 1025], [255, 256, 257, 1, 1, 767]],
+                         ids=["ones", "warpish", "tiles", "one_long_row", "tile_edges", "small_tile_edges",
+                              "step_edges"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
-def test_row_length_bins(lengths, precision):
+@pytest.mark.parametrize("spmv_tile", [512, 2048])
+def test_row_length_bins(lengths, precision, spmv_tile):
     """Rows (followers per leader) of chosen lengths, including one row spanning many tiles,
-    rows ending exactly on tile boundaries and ragged tails."""
+    rows ending exactly on tile and step boundaries and ragged tails, for the smallest and
+    the largest tile of the product."""
     rng = np.random.default_rng(sum(lengths))
     n = max(lengths) + len(lengths) + 10
     f, l = [], []
@@ -191,7 +195,8 @@ def test_row_length_bins(lengths, precision):
         f.append(i)
         l.append((i + 1) % len(lengths) if len(lengths) > 1 else n - 1)
     lam, mu = rng.uniform(0.1, 1, n), rng.uniform(0.1, 1, n)
-    ref, out = _run_pair(n, np.array(f), np.array(l), lam, mu, precision)
+    ref, out = _run_pair(n, np.array(f), np.array(l), lam, mu, precision, spmv_tile=spmv_tile)
+    assert out["stats"]["spmv_tile"] == spmv_tile
     tol = 1e-12 if precision == "fp64" else 1e-6
     assert rel_l1(out["psi"], ref["psi"]) <= tol
     assert_same_ranking(out["ids"], ref["psi"], tol)
@@ -343,3 +348,24 @@ def test_tight_absolute_tolerance_takes_the_fp64_products():
     assert ref["info"]["converged"] and out["info"]["converged"]
     assert out["info"]["iters"] <= 2 * ref["info"]["iters"] + 10, (out["info"]["iters"], ref["info"]["iters"])
     assert rel_l1(out["psi"], ref["psi"]) <= 1e-12
+
+
+def test_tile_sizes_agree_and_the_automatic_choice():
+    """The product's tile (nonzeros per warp) changes only the summation order: FP64 results
+    of every tile size agree to rounding, a small graph gets the smallest tile, and tile
+    sizes outside {0, 512, 1024, 2048} are rejected."""
+    from paper_2206_09960_gb300 import PsiError, _binding as B
+
+    w = psigen.workload("rmat", seed=31, scale=14)
+    args = (w["n"], w["follower"], w["leader"], w["lam"], w["mu"], 1e-13)
+    outs = {t: gpu_solve(*args, precision="fp64", spmv_tile=t) for t in (0, 512, 1024, 2048)}
+    assert outs[0]["stats"]["spmv_tile"] == 512  # ~262K edges: far fewer than 4 tiles per warp at 2048
+    ref = oracle.solve(w["n"], w["follower"], w["leader"], w["lam"], w["mu"], eps=1e-13)
+    for t in (512, 1024, 2048):
+        assert outs[t]["stats"]["spmv_tile"] == t
+        assert rel_l1(outs[t]["psi"], outs[2048]["psi"]) <= 1e-13
+        assert rel_l1(outs[t]["psi"], ref["psi"]) <= 1e-12
+    for bad in (256, 1000, 4096, -1):
+        with pytest.raises(PsiError) as e:
+            gpu_solve(*args, spmv_tile=bad)
+        assert e.value.status == B.PSI_ERR_INVALID_ARG
