@@ -255,15 +255,20 @@ __global__ void __launch_bounds__(1024) k_group_step(int mode, MState* st, DevSt
   }
 }
 
-// FP64 gathered vector of the CONFIRM graphs' X users: u = s / sigma (other graphs' entries
-// are read only by their own rows, which ignore them in this step)
+// Gathered vector of the CONFIRM graphs' X users: u = s / sigma (other graphs' entries are
+// read only by their own rows, which ignore them in this step).  kGapSlices blocks per
+// graph over its X range; blocks of graphs in another phase return at once.
 template <typename G>
-__global__ void k_confirm_u(const DevState* gate, const double* __restrict__ s64, const double* __restrict__ isig,
-                            const int32_t* __restrict__ gid, const int32_t* __restrict__ phase, int32_t nX, G* u) {
+__global__ void __launch_bounds__(256) k_confirm_u(const DevState* gate, const double* __restrict__ s64,
+                                                  const double* __restrict__ isig, const int4* __restrict__ ranges,
+                                                  const int32_t* __restrict__ phase, G* u) {
   if (gate[1].done) return;
-  MGRID_STRIDE(j, nX) {
-    if (phase[gid[j]] == kConfirm) u[j] = to_gather<G>(s64[j] * isig[j]);
-  }
+  const int g = blockIdx.x / kGapSlices, b = blockIdx.x % kGapSlices;
+  if (phase[g] != kConfirm) return;
+  const int4 rg = ranges[g];
+  const int64_t nx = rg.y - rg.x;
+  const int64_t lo = rg.x + nx * b / kGapSlices, hi = rg.x + nx * (b + 1) / kGapSlices;
+  for (int64_t j = lo + threadIdx.x; j < hi; j += blockDim.x) u[j] = to_gather<G>(s64[j] * isig[j]);
 }
 
 // gathered vector of the confirming / final products: dst[j] = s[user(j)] * isig[user(j)]
@@ -675,8 +680,8 @@ int step_pair(Multi& M, cudaStream_t s, const float* v_in, float* v_out) {
                 TileGate{M.tile_g.get(), M.cnt_series.get()}};
   launches += multi_product<float>(M, s, v_in, es, M.gate.get() + 0);
   launches += group_step(M, s, 0);
-  k_confirm_u<G><<<mgrid(g.nX), 256, 0, s>>>(M.gate.get(), M.s64.get(), g.isig64.get(), M.gid.get(), M.phase.get(),
-                                             g.nX, M.u64as<G>());
+  k_confirm_u<G><<<M.G * kGapSlices, 256, 0, s>>>(M.gate.get(), M.s64.get(), g.isig64.get(), M.ranges.get(),
+                                                  M.phase.get(), M.u64as<G>());
   PSI_LAUNCHED();
   ++launches;
   EpiResidM<G> er{g.c64.get(), g.mu64.get(), g.isig64.get(), M.s64.get(), v_out, g.nX, M.gid.get(), M.phase.get(),

@@ -302,14 +302,31 @@ __global__ void __launch_bounds__(kSpmvThreads, spmv_min_blocks<T>())
 #pragma unroll
     for (int j = 0; j < kSpmvItems; ++j) x[j] = ld_gather(u + c[j], pol_k);
   };
-  auto next_on = [&](int32_t t) {  // this warp's first tile from t on that is not turned off
+  // this warp's tiles, in order: first, first + stride, ... (all below 2^31: num_tiles +
+  // 32 strides); with tile skipping, the gates of 32 candidates are tested at once (one per
+  // lane) and a ballot gives the tiles to run
+  const int32_t first = (int32_t)blockIdx.x * kSpmvWarps + warp;
+  int32_t cand = first;  // next candidate tile (the first of the next batch when skipping)
+  uint32_t on_bits = 0;  // tiles of the last batch still to run
+  auto next_tile = [&]() -> int32_t {
     if constexpr (kSkip) {
-      while (t < a.num_tiles && !epi.tile_on(t)) t += stride;
+      while (on_bits == 0) {
+        if (cand >= a.num_tiles) return a.num_tiles;
+        const int32_t tl = cand + lane * stride;
+        on_bits = __ballot_sync(0xffffffffu, tl < a.num_tiles && epi.tile_on(tl));
+        cand += 32 * stride;
+      }
+      const int b = __ffs(on_bits) - 1;
+      on_bits &= on_bits - 1;
+      return cand - (32 - b) * stride;
+    } else {
+      const int32_t t = cand;
+      cand += stride;
+      return t < a.num_tiles ? t : a.num_tiles;
     }
-    return t;
   };
 
-  int32_t tile = next_on((int32_t)blockIdx.x * kSpmvWarps + warp);
+  int32_t tile = next_tile();
   // software pipeline: the values of the next step are in flight while a step is reduced,
   // and the column indices of the step after it, so its gathers issue without waiting
   T xn[kSpmvItems];
@@ -326,7 +343,7 @@ __global__ void __launch_bounds__(kSpmvThreads, spmv_min_blocks<T>())
     const int32_t nnz0 = tile * a.tile;  // < m < 2^31
     const int32_t r0 = a.tile_row[tile];
     const int32_t nr = a.tile_row[tile + 1] - r0 + 1;  // rows touching the tile
-    const int32_t next = next_on(tile + stride);
+    const int32_t next = next_tile();
     for (int w = lane; w < words; w += 32) ends[w] = 0u;
     __syncwarp();
     const bool head_open = ld_stream(a.row_ptr + r0, pol_s) < nnz0;  // row r0 began earlier
