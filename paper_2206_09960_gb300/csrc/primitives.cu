@@ -75,13 +75,17 @@ constexpr int kRsItems = 12;                    // measured: 12 beats 8 and 16 o
 constexpr int kRsTile = kRsThreads * kRsItems;  // 3072 keys per tile
 constexpr int kRsPerWarp = 32 * kRsItems;       // 384 consecutive keys per warp
 
-// Lanes of the warp holding the same 9-bit digit (256 marks "no item"), from one ballot
-// per digit bit: the lanes that agree with this lane on every bit.  Ballots run on the ALU
-// pipe; the hardware match instruction would serialise on a narrow pipe here.
-__device__ __forceinline__ uint32_t digit_peers(int d) {
+// Lanes of the warp holding the same 8-bit digit.  Ballots (one per digit bit: the lanes
+// that agree with this lane on every bit) run on the ALU pipe, the match instruction on the
+// narrower ADU pipe; a pass that used only one of them kept that pipe ~90% busy, so the
+// rounds of a tile share the work: every kRsMatchEvery-th round matches (measured on the
+// scale-25 build: every 2nd / 3rd / 4th / 6th round 60.1 / 59.7 / 60.3 / 60.8 ms, ballots
+// only 61.2 ms).
+constexpr int kRsMatchEvery = 3;
+__device__ __forceinline__ uint32_t digit_peers_ballot(int d) {
   uint32_t peers = 0xffffffffu;
 #pragma unroll
-  for (int b = 0; b < 9; ++b) {
+  for (int b = 0; b < 8; ++b) {
     const bool bit = (d >> b) & 1;
     const uint32_t bal = __ballot_sync(0xffffffffu, bit);
     peers &= bit ? bal : ~bal;
@@ -120,7 +124,7 @@ __global__ void __launch_bounds__(kRsThreads) k_radix_scatter(const K* __restric
   extern __shared__ __align__(16) unsigned char rs_dyn[];
   K* sk = reinterpret_cast<K*>(rs_dyn);
   uint32_t* sv = reinterpret_cast<uint32_t*>(rs_dyn + (size_t)kRsTile * sizeof(K));
-  __shared__ uint32_t wh[kRsWarps][257];
+  __shared__ uint32_t wh[kRsWarps][257];  // per-warp digit counts (padded row: fewer bank conflicts)
   __shared__ uint32_t tile_base[256];
   __shared__ uint32_t dstart[256];
   __shared__ uint32_t wsum[kRsWarps];
@@ -133,15 +137,18 @@ __global__ void __launch_bounds__(kRsThreads) k_radix_scatter(const K* __restric
   const uint32_t lt_mask = (1u << lane) - 1u;
   K k[kRsItems];
   uint32_t v[kRsItems];
-  uint32_t dp[kRsItems];  // digit (9 bits, 256 = no item) << 16 | rank inside the warp's digit run
+  uint32_t dp[kRsItems];  // digit << 16 | rank inside the warp's digit run
 #pragma unroll
   for (int r = 0; r < kRsItems; ++r) {
     int64_t idx = wbase + (int64_t)r * 32 + lane;
     bool ok = idx < n;
     k[r] = ok ? keys[idx] : K(0);
     if (VALS) v[r] = ok ? vals[idx] : 0u;
-    int d = ok ? (int)((uint32_t)(k[r] >> shift) & 0xFFu) : 256;
-    uint32_t peers = digit_peers(d);
+    // a key past the end takes digit 255: such keys are a suffix of the tile in ranking
+    // order, so they sort to the end of the tile's buffer and are never written out
+    const int d = ok ? (int)((uint32_t)(k[r] >> shift) & 0xFFu) : 255;
+    const uint32_t peers = (kRsMatchEvery > 0 && r % kRsMatchEvery == 0) ? __match_any_sync(0xffffffffu, d)
+                                                                          : digit_peers_ballot(d);
     uint32_t before = wh[warp][d];
     __syncwarp();
     if ((peers & lt_mask) == 0) wh[warp][d] = before + __popc(peers);
@@ -175,11 +182,9 @@ __global__ void __launch_bounds__(kRsThreads) k_radix_scatter(const K* __restric
 #pragma unroll
   for (int r = 0; r < kRsItems; ++r) {
     const int d = (int)(dp[r] >> 16);
-    if (d < 256) {
-      const uint32_t lp = dstart[d] + wh[warp][d] + (dp[r] & 0xFFFFu);
-      sk[lp] = k[r];
-      if (VALS) sv[lp] = v[r];
-    }
+    const uint32_t lp = dstart[d] + wh[warp][d] + (dp[r] & 0xFFFFu);
+    sk[lp] = k[r];
+    if (VALS) sv[lp] = v[r];
   }
   __syncthreads();
   const int64_t rem = n - tile0;
