@@ -88,16 +88,18 @@ __global__ void k_check_rates(const double* __restrict__ lam, const double* __re
   if (bad) atomicOr(err, bad);
 }
 
-// Validates every edge and marks, exactly, who has followers (has_fol) and who has leaders
-// (has_lead) with plain byte stores.  Degrees are only an ordering key for locality: they
+// Validates every edge and marks, exactly, who has followers (fol_bits) and who has leaders
+// (lead_bits), one bit per user: a bit is set with an atomic OR only after a plain load
+// found it clear (hub users are hit by many edges, and the 4 MB bitmaps mostly stay in L1
+// and L2, so most edges cost two cached loads and no store).  Degrees are only an ordering key for locality: they
 // are counted on the edges whose global index is a multiple of sample_mask + 1 (a power of
 // two; all edges when sample_mask == 0).
 // Runs on edges [e_base, e_base + m) (f and l point at edge e_base), so that the edges can
 // be validated chunk by chunk as they arrive.  Four edges per thread per round, their eight
-// flag loads issued before any store, so that the random flag reads overlap (the stores
-// only ever set a flag, so reading the flags of later edges first changes nothing).
+// bitmap loads issued before any update, so that the random reads overlap (updates only
+// ever set bits, so reading the bits of later edges first changes nothing).
 __global__ void k_edges(const int32_t* __restrict__ f, const int32_t* __restrict__ l, int64_t m, int64_t e_base,
-                        int64_t n, int drop_self, int64_t sample_mask, uint8_t* has_fol, uint8_t* has_lead,
+                        int64_t n, int drop_self, int64_t sample_mask, uint32_t* fol_bits, uint32_t* lead_bits,
                         uint32_t* in_deg, uint32_t* out_deg, uint32_t* err) {
   constexpr int kQ = 4;
   uint32_t bits = 0;
@@ -112,7 +114,7 @@ __global__ void k_edges(const int32_t* __restrict__ f, const int32_t* __restrict
       a[q] = ok[q] ? f[e] : 0;
       b[q] = ok[q] ? l[e] : 0;
     }
-    uint8_t hl[kQ], hf[kQ];
+    uint32_t hl[kQ], hf[kQ];
 #pragma unroll
     for (int q = 0; q < kQ; ++q) {
       if (ok[q]) {
@@ -124,15 +126,13 @@ __global__ void k_edges(const int32_t* __restrict__ f, const int32_t* __restrict
           ok[q] = false;
         }
       }
-      // store only when not yet set: hub users are hit by many edges, and their flag lines
-      // stay in L1, so most of the two stores per edge are skipped
-      hl[q] = ok[q] ? has_lead[a[q]] : (uint8_t)1;
-      hf[q] = ok[q] ? has_fol[b[q]] : (uint8_t)1;
+      hl[q] = ok[q] ? ~lead_bits[a[q] >> 5] & (1u << (a[q] & 31)) : 0u;  // bit still to set
+      hf[q] = ok[q] ? ~fol_bits[b[q] >> 5] & (1u << (b[q] & 31)) : 0u;
     }
 #pragma unroll
     for (int q = 0; q < kQ; ++q) {
-      if (!hl[q]) has_lead[a[q]] = 1;
-      if (!hf[q]) has_fol[b[q]] = 1;
+      if (hl[q]) atomicOr(&lead_bits[a[q] >> 5], hl[q]);
+      if (hf[q]) atomicOr(&fol_bits[b[q] >> 5], hf[q]);
       if (ok[q] && ((e_base + e0 + q * gs) & sample_mask) == 0) {
         atomicAdd(&out_deg[a[q]], 1u);
         atomicAdd(&in_deg[b[q]], 1u);
@@ -145,7 +145,7 @@ __global__ void k_edges(const int32_t* __restrict__ f, const int32_t* __restrict
 // key = class (2 bits) | rank (23 bits); value = user id.  A stable sort gives ties by id.
 // With groups (independent graphs solved together), the key is class | group (10 bits) |
 // rank (13 bits), so each group's users stay contiguous inside every class.
-__global__ void k_node_keys(const uint8_t* __restrict__ has_fol, const uint8_t* __restrict__ has_lead,
+__global__ void k_node_keys(const uint32_t* __restrict__ fol_bits, const uint32_t* __restrict__ lead_bits,
                             const uint32_t* __restrict__ in_deg, const uint32_t* __restrict__ out_deg, int64_t n,
                             int reorder, const int32_t* __restrict__ group, uint32_t* key, uint32_t* val,
                             uint32_t* class_count) {
@@ -154,7 +154,8 @@ __global__ void k_node_keys(const uint8_t* __restrict__ has_fol, const uint8_t* 
   __syncthreads();
   GRID_STRIDE(i, n) {
     uint32_t di = in_deg[i], dout = out_deg[i];
-    uint32_t cls = has_fol[i] ? (has_lead[i] ? 0u : 1u) : (has_lead[i] ? 2u : 3u);
+    const bool has_fol = (fol_bits[i >> 5] >> (i & 31)) & 1u, has_lead = (lead_bits[i >> 5] >> (i & 31)) & 1u;
+    uint32_t cls = has_fol ? (has_lead ? 0u : 1u) : (has_lead ? 2u : 3u);
     // rows (X, R) by row length (in-degree, which in these graphs also tracks how often a
     // user is gathered); U by how often it is gathered (out-degree)
     uint32_t deg = cls <= 1 ? di : (cls == 2 ? dout : 0u);
@@ -534,11 +535,12 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
   DBuf<uint32_t> err(al, 8);  // [0] error bits, [1..4] class counts, [5] rows seen, [6..7] spare
   PSI_CUDA(cudaMemsetAsync(err.get(), 0, 8 * sizeof(uint32_t), s));
   DBuf<uint32_t> in_deg(al, (size_t)n), out_deg(al, (size_t)n);
-  DBuf<uint8_t> has_fol(al, (size_t)n), has_lead(al, (size_t)n);
+  const size_t n_words = (size_t)ceil_div(n, 32);
+  DBuf<uint32_t> fol_bits(al, n_words), lead_bits(al, n_words);
   PSI_CUDA(cudaMemsetAsync(in_deg.get(), 0, sizeof(uint32_t) * n, s));
   PSI_CUDA(cudaMemsetAsync(out_deg.get(), 0, sizeof(uint32_t) * n, s));
-  PSI_CUDA(cudaMemsetAsync(has_fol.get(), 0, n, s));
-  PSI_CUDA(cudaMemsetAsync(has_lead.get(), 0, n, s));
+  PSI_CUDA(cudaMemsetAsync(fol_bits.get(), 0, sizeof(uint32_t) * n_words, s));
+  PSI_CUDA(cudaMemsetAsync(lead_bits.get(), 0, sizeof(uint32_t) * n_words, s));
   if (any_host) PSI_CUDA(cudaStreamWaitEvent(s, arrived[1], 0));
   k_check_rates<<<grid_for(n), 256, 0, s>>>(dlam, dmu, n, err.get());
   PSI_LAUNCHED();
@@ -550,7 +552,7 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
       const int64_t e0 = c * chunk, len = std::min(chunk, m - e0);
       if (any_host) PSI_CUDA(cudaStreamWaitEvent(s, arrived[2 + c], 0));
       k_edges<<<grid_for(len), 256, 0, s>>>(df + e0, dl + e0, len, e0, n, g.opt.self_loops == PSI_DROP ? 1 : 0,
-                                            sample_mask, has_fol.get(), has_lead.get(), in_deg.get(), out_deg.get(),
+                                            sample_mask, fol_bits.get(), lead_bits.get(), in_deg.get(), out_deg.get(),
                                             err.get());
       PSI_LAUNCHED();
     }
@@ -565,7 +567,7 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
   DBuf<uint32_t> perm32;
   {
     DBuf<uint32_t> k0(al, (size_t)n), k1(al, (size_t)n), v0(al, (size_t)n), v1(al, (size_t)n);
-    k_node_keys<<<grid_for(n), 256, 0, s>>>(has_fol.get(), has_lead.get(), in_deg.get(), out_deg.get(), n,
+    k_node_keys<<<grid_for(n), 256, 0, s>>>(fol_bits.get(), lead_bits.get(), in_deg.get(), out_deg.get(), n,
                                             g.opt.reorder ? 1 : 0, hook ? hook->user_group() : nullptr, k0.get(),
                                             v0.get(), err.get() + 1);
     PSI_LAUNCHED();
@@ -574,8 +576,8 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
   }
   in_deg.release();
   out_deg.release();
-  has_fol.release();
-  has_lead.release();
+  fol_bits.release();
+  lead_bits.release();
   uint32_t cls[4];
   PSI_CUDA(cudaMemcpyAsync(cls, err.get() + 1, sizeof(cls), cudaMemcpyDeviceToHost, s));
   PSI_CUDA(cudaStreamSynchronize(s));
