@@ -199,23 +199,76 @@ __device__ __forceinline__ bool first_of_run(const uint64_t* key, int64_t e, uin
   return k != sentinel && (e == 0 || key[e - 1] != k);
 }
 
-__global__ void k_unique_flags(const uint64_t* __restrict__ key, int64_t m, uint64_t sentinel,
-                               uint32_t* __restrict__ flag) {
-  GRID_STRIDE(e, m) flag[e] = first_of_run(key, e, sentinel) ? 1u : 0u;
+// Duplicate merge and CSR of the sorted edge keys as one stream compaction over tiles of
+// kUqTile keys: k_unique_count counts the unique keys of every tile, an exclusive scan of
+// those counts gives each tile its output offset, and k_unique_write writes the unique keys
+// in order (li: leader row, col: follower gathered index) with row_ptr[r] at the first
+// unique key of row r, counting the rows seen.
+constexpr int kUqThreads = 256;
+constexpr int kUqItems = 16;
+constexpr int kUqTile = kUqThreads * kUqItems;
+
+__global__ void __launch_bounds__(kUqThreads) k_unique_count(const uint64_t* __restrict__ key, int64_t m,
+                                                             uint64_t sentinel, uint32_t* __restrict__ count) {
+  const int64_t base = (int64_t)blockIdx.x * kUqTile;
+  uint32_t c = 0;
+#pragma unroll 4
+  for (int j = 0; j < kUqItems; ++j) {
+    const int64_t e = base + (int64_t)j * kUqThreads + threadIdx.x;
+    if (e < m && first_of_run(key, e, sentinel)) ++c;
+  }
+  c = block_sum(c);
+  if (threadIdx.x == 0) count[blockIdx.x] = c;
 }
 
-__global__ void k_unique_compact(const uint64_t* __restrict__ key, int64_t m, uint64_t sentinel,
-                                 const uint32_t* __restrict__ pos, int b, int32_t* __restrict__ li,
-                                 int32_t* __restrict__ fi) {
-  const uint64_t mask = ((uint64_t)1 << b) - 1;
-  grid_stride4(m, [&](int64_t e) {
-    if (first_of_run(key, e, sentinel)) {
-      const uint32_t p = pos[e];
-      const uint64_t k = key[e];
-      li[p] = (int32_t)(k >> b);
-      fi[p] = (int32_t)(k & mask);
+__global__ void __launch_bounds__(kUqThreads) k_unique_write(const uint64_t* __restrict__ key, int64_t m,
+                                                             uint64_t sentinel, const uint32_t* __restrict__ off,
+                                                             int b, int32_t* __restrict__ li,
+                                                             int32_t* __restrict__ col, int32_t* __restrict__ row_ptr,
+                                                             uint32_t* rows_seen) {
+  __shared__ uint32_t wcount[2][kUqThreads / 32];  // double-buffered: one barrier per round
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  const uint64_t low = ((uint64_t)1 << b) - 1;
+  const int64_t base = (int64_t)blockIdx.x * kUqTile;
+  uint32_t run = off[blockIdx.x];  // output position of the tile's next unique key
+  uint32_t rows = 0;
+  for (int j = 0; j < kUqItems; ++j) {
+    const int64_t e = base + (int64_t)j * kUqThreads + threadIdx.x;
+    uint64_t k = sentinel;
+    bool uniq = false, first_in_row = false;
+    if (e < m) {
+      k = key[e];
+      if (k != sentinel) {
+        const uint64_t prev = e > 0 ? key[e - 1] : 0;
+        uniq = e == 0 || prev != k;
+        first_in_row = e == 0 || (prev >> b) != (k >> b);
+      }
     }
-  });
+    const uint32_t bal = __ballot_sync(0xffffffffu, uniq);
+    if (lane == 0) wcount[j & 1][warp] = __popc(bal);
+    __syncthreads();
+    uint32_t before = 0, total = 0;
+#pragma unroll
+    for (int w = 0; w < kUqThreads / 32; ++w) {
+      const uint32_t t = wcount[j & 1][w];
+      before += w < warp ? t : 0u;
+      total += t;
+    }
+    if (uniq) {
+      const uint32_t o = run + before + __popc(bal & lt_mask);
+      const int32_t r = (int32_t)(k >> b);
+      li[o] = r;
+      col[o] = (int32_t)(k & low);
+      if (first_in_row) {
+        row_ptr[r] = (int32_t)o;
+        ++rows;
+      }
+    }
+    run += total;
+  }
+  rows = block_sum(rows);  // one atomic per block
+  if (threadIdx.x == 0 && rows) atomicAdd(rows_seen, rows);
 }
 
 // row_ptr[r] = first unique edge of leader r; counts the rows seen
@@ -614,12 +667,13 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
     lbuf.release();
     bool alt = radix_sort<uint64_t>(k0.get(), k1.get(), nullptr, nullptr, m, bl + bf, al, s);
     const uint64_t* keys = alt ? k1.get() : k0.get();
-    DBuf<uint32_t> pos(al, (size_t)m);
+    const int64_t uq_tiles = ceil_div(m, kUqTile);
+    DBuf<uint32_t> uq_off(al, (size_t)(uq_tiles > 0 ? uq_tiles : 1));
     DBuf<uint32_t> total(al, 1);
     if (m > 0) {
-      k_unique_flags<<<grid_for(m), 256, 0, s>>>(keys, m, sentinel, pos.get());
+      k_unique_count<<<(unsigned)uq_tiles, kUqThreads, 0, s>>>(keys, m, sentinel, uq_off.get());
       PSI_LAUNCHED();
-      exclusive_scan_u32(pos.get(), pos.get(), m, al, s, total.get());
+      exclusive_scan_u32(uq_off.get(), uq_off.get(), uq_tiles, al, s, total.get());
       mu_count = read1(total.get(), s);
     } else {
       mu_count = 0;
@@ -630,8 +684,10 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
     const int64_t padded = ceil_div(mu_count, kSpmvTileMax) * kSpmvTileMax;
     g.col.reset(al, (size_t)(padded > 0 ? padded : 4));
     li.reset(al, (size_t)(mu_count > 0 ? mu_count : 1));
+    g.row_ptr.reset(al, (size_t)g.n_rows + 1);
     if (mu_count > 0) {
-      k_unique_compact<<<grid_for(m), 256, 0, s>>>(keys, m, sentinel, pos.get(), bf, li.get(), g.col.get());
+      k_unique_write<<<(unsigned)uq_tiles, kUqThreads, 0, s>>>(keys, m, sentinel, uq_off.get(), bf, li.get(),
+                                                              g.col.get(), g.row_ptr.get(), err.get() + 5);
       PSI_LAUNCHED();
     }
     if (padded > mu_count) {
@@ -639,12 +695,7 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
       PSI_LAUNCHED();
     }
   }
-  g.row_ptr.reset(al, (size_t)g.n_rows + 1);
   {
-    if (mu_count > 0) {
-      k_row_bounds<<<grid_for(mu_count), 256, 0, s>>>(li.get(), mu_count, g.row_ptr.get(), err.get() + 5);
-      PSI_LAUNCHED();
-    }
     k_set_i32<<<1, 1, 0, s>>>(g.row_ptr.get() + g.n_rows, (int32_t)mu_count);
     PSI_LAUNCHED();
     const uint32_t rows_seen = read1(err.get() + 5, s);
