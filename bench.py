@@ -32,8 +32,8 @@ METRIC = "Power-ψ time-to-L1<1e-8 and GTEPS/iter at N=2^25; % of HBM peak"
 FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes per launch of the FP32 series step (k_spmv + fix-up) from one ncu capture,
 # valid only while the kernel sources hash to `sha`.
-NCU_TRAFFIC = {"sha": "7d9b998dc1c546a0", "bytes_per_launch": 2898464768,
-               "note": "k_spmv<float,EpiSeries> 2.731 GB read + 0.120 GB write (mean of 2 launches), k_fixup 0.047 GB; "
+NCU_TRAFFIC = {"sha": "3b9099a38f018b52", "bytes_per_launch": 2895861632,
+               "note": "k_spmv<float,EpiSeries> 2.731 GB read + 0.118 GB write (mean of 2 launches), k_fixup 0.047 GB; "
                        "R-MAT scale 25 bench step, one ncu capture of 3 launches (1-pass metrics)"}
 KERNEL_SOURCES = ["paper_2206_09960_gb300/csrc/spmv.cuh", "paper_2206_09960_gb300/csrc/common.cuh"]
 CPU_SAMPLE_SCALE = 20
