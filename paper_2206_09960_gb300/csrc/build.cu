@@ -1,18 +1,20 @@
 // build.cu -- the operator of Sec. II built on the device from an edge list.
 //
-//  1. validate ids, self-loops and rates; mark users with followers / with leaders (exact)
-//     and count degrees (on a fixed 1-in-k subset of the edges for large graphs);
+//  1. validate ids, self-loops and rates; mark users with followers / with leaders (exact,
+//     two bitmaps) and count degrees (on a fixed 1-in-2^k subset of the edges for large
+//     graphs);
 //  2. renumber users by class (X: followers and leaders, R: followers only, U: leaders
 //     only, Z: isolated) and, within a class, by decreasing degree, so rows form one range
 //     [0, nX+nR) and the gathered users one compact L2-friendly range;
 //  3. sort the renumbered (leader, follower) pairs (stable LSD radix), merge duplicates
-//     (L(j) is a set), and cut the transposed CSR: row i = followers of leader i;
+//     (L(j) is a set) and cut the transposed CSR (row i = followers of leader i) in one
+//     stream compaction;
 //  4. regroup the unique edges by follower (stable radix on the follower id) and form,
 //     for every follower j, sigma_j = sum_{l in L(j)} (lambda_l + mu_l) and
-//     beta_j = sum_{l in L(j)} lambda_l in FP64 (the denominators of a_ji, b_ji) in one
-//     load-balanced product over that follower-grouped CSR;
+//     beta_j = sum_{l in L(j)} lambda_l (the denominators of a_ji, b_ji; float-pair sums,
+//     FP64 in the FP64 mode) in one load-balanced product over that follower-grouped CSR;
 //  5. per-user constants c, d, 1/sigma in FP64 and FP32; ||B||_inf = max_j beta_j/sigma_j;
-//  6. the merge-path tile schedule of the sparse product.
+//  6. the tile schedule of the sparse product (tiles of nonzeros, one warp each).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
