@@ -515,9 +515,9 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
   NvtxPhases phases;
   phases.next("psi build 0: staging");
   // ---- stage inputs (host pointers are copied; device pointers are read in place).  Host
-  //      copies run on a private stream, the rates first, then the edges in chunks; the
-  //      validation pass (step 1) takes each chunk as soon as it has arrived, so it overlaps
-  //      the transfer.
+  //      copies run on two private streams (followers and lambda on one, leaders and mu on
+  //      the other), the rates first, then the edges in chunks; the validation pass (step 1)
+  //      takes each chunk as soon as both halves have arrived, so it overlaps the transfer.
   DBuf<int32_t> fbuf, lbuf;
   DBuf<double> lam_buf, mu_buf;
   const int32_t* df = follower;
@@ -545,43 +545,55 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
     dmu = mu_buf.get();
   }
   const bool any_host = f_host || l_host || lam_host || mu_host;
-  cudaStream_t cs = nullptr;
-  std::vector<cudaEvent_t> arrived;  // [0]: buffers ready, [1]: rates arrived, [2 + c]: edge chunk c
+  // two copy streams, so that two copy engines move the follower and the leader arrays at once
+  cudaStream_t cs[2] = {nullptr, nullptr};
+  // [0]: buffers ready, [1], [2]: lambda, mu arrived, [3 + 2c], [4 + 2c]: follower / leader
+  // chunk c arrived
+  std::vector<cudaEvent_t> arrived;
   const int64_t chunk = (int64_t)1 << 25;
   const int64_t n_chunks = m > 0 ? ceil_div(m, chunk) : 0;
   auto release_copies = [&]() {
-    if (cs) cudaStreamSynchronize(cs);
+    for (cudaStream_t& c : cs) {
+      if (c) cudaStreamSynchronize(c);
+    }
     for (cudaEvent_t e : arrived) cudaEventDestroy(e);
     arrived.clear();
-    if (cs) cudaStreamDestroy(cs);
-    cs = nullptr;
+    for (cudaStream_t& c : cs) {
+      if (c) cudaStreamDestroy(c);
+      c = nullptr;
+    }
   };
   struct CopyGuard {
     decltype(release_copies)& f;
     ~CopyGuard() { f(); }
   } copy_guard{release_copies};  // waits for the copies before the staging buffers go
   if (any_host) {
-    PSI_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    for (cudaStream_t& c : cs) PSI_CUDA(cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking));
     cudaEvent_t ready;
     PSI_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
     arrived.push_back(ready);  // the staging buffers exist (stream-ordered allocation on s)
     PSI_CUDA(cudaEventRecord(ready, s));
-    PSI_CUDA(cudaStreamWaitEvent(cs, ready, 0));
-    if (lam_host) PSI_CUDA(cudaMemcpyAsync(lam_buf.get(), lambda, sizeof(double) * n, cudaMemcpyHostToDevice, cs));
-    if (mu_host) PSI_CUDA(cudaMemcpyAsync(mu_buf.get(), mu, sizeof(double) * n, cudaMemcpyHostToDevice, cs));
-    cudaEvent_t ev;
-    PSI_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-    arrived.push_back(ev);
-    PSI_CUDA(cudaEventRecord(ev, cs));
+    for (cudaStream_t c : cs) PSI_CUDA(cudaStreamWaitEvent(c, ready, 0));
+    if (lam_host) PSI_CUDA(cudaMemcpyAsync(lam_buf.get(), lambda, sizeof(double) * n, cudaMemcpyHostToDevice, cs[0]));
+    if (mu_host) PSI_CUDA(cudaMemcpyAsync(mu_buf.get(), mu, sizeof(double) * n, cudaMemcpyHostToDevice, cs[1]));
+    auto mark = [&](cudaStream_t c) {
+      cudaEvent_t ev;
+      PSI_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+      arrived.push_back(ev);
+      PSI_CUDA(cudaEventRecord(ev, c));
+    };
+    mark(cs[0]);  // [1]: lambda
+    mark(cs[1]);  // [2]: mu
     for (int64_t c = 0; c < n_chunks; ++c) {
       const int64_t e0 = c * chunk, len = std::min(chunk, m - e0);
       if (f_host)
-        PSI_CUDA(cudaMemcpyAsync(fbuf.get() + e0, follower + e0, sizeof(int32_t) * len, cudaMemcpyHostToDevice, cs));
+        PSI_CUDA(cudaMemcpyAsync(fbuf.get() + e0, follower + e0, sizeof(int32_t) * len, cudaMemcpyHostToDevice,
+                                 cs[0]));
       if (l_host)
-        PSI_CUDA(cudaMemcpyAsync(lbuf.get() + e0, leader + e0, sizeof(int32_t) * len, cudaMemcpyHostToDevice, cs));
-      PSI_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-      arrived.push_back(ev);
-      PSI_CUDA(cudaEventRecord(ev, cs));
+        PSI_CUDA(cudaMemcpyAsync(lbuf.get() + e0, leader + e0, sizeof(int32_t) * len, cudaMemcpyHostToDevice,
+                                 cs[1]));
+      mark(cs[0]);
+      mark(cs[1]);
     }
   }
 
@@ -596,7 +608,10 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
   PSI_CUDA(cudaMemsetAsync(out_deg.get(), 0, sizeof(uint32_t) * n, s));
   PSI_CUDA(cudaMemsetAsync(fol_bits.get(), 0, sizeof(uint32_t) * n_words, s));
   PSI_CUDA(cudaMemsetAsync(lead_bits.get(), 0, sizeof(uint32_t) * n_words, s));
-  if (any_host) PSI_CUDA(cudaStreamWaitEvent(s, arrived[1], 0));
+  if (any_host) {
+    PSI_CUDA(cudaStreamWaitEvent(s, arrived[1], 0));
+    PSI_CUDA(cudaStreamWaitEvent(s, arrived[2], 0));
+  }
   k_check_rates<<<grid_for(n), 256, 0, s>>>(dlam, dmu, n, err.get());
   PSI_LAUNCHED();
   if (m > 0) {
@@ -605,7 +620,10 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
     while (m > ((sample_mask + 1) << 26)) sample_mask = 2 * sample_mask + 1;
     for (int64_t c = 0; c < n_chunks; ++c) {
       const int64_t e0 = c * chunk, len = std::min(chunk, m - e0);
-      if (any_host) PSI_CUDA(cudaStreamWaitEvent(s, arrived[2 + c], 0));
+      if (any_host) {
+        PSI_CUDA(cudaStreamWaitEvent(s, arrived[3 + 2 * c], 0));
+        PSI_CUDA(cudaStreamWaitEvent(s, arrived[4 + 2 * c], 0));
+      }
       k_edges<<<grid_for(len), 256, 0, s>>>(df + e0, dl + e0, len, e0, n, g.opt.self_loops == PSI_DROP ? 1 : 0,
                                             sample_mask, fol_bits.get(), lead_bits.get(), in_deg.get(), out_deg.get(),
                                             err.get());
