@@ -272,10 +272,12 @@ constexpr int spmv_min_blocks() {
 // epilogue of every row that begins and ends among them at once; the row of its first row
 // end, which may have begun in earlier lanes, is completed by a warp segmented scan and
 // closed by the same lane, and the sum of the row still open after the step is carried to
-// the next step in a register.  The gathers of the next step, and the column indices of
-// the step after it, are issued before the current step is reduced.  No block barrier is taken inside the tile loop, and shared memory holds
-// only the bitmaps, which leaves the rest of the SM's on-chip memory to the L1 that serves
-// the gathers.
+// the next step in a register.  Row indices come from the lanes' prefix counts of row ends
+// (one ballot per item position) and the scan's segment flags from one ballot.  The
+// gathers of the next step, and the column indices of the step after it, are issued before
+// the current step is reduced.  No block barrier is taken inside the tile loop, and shared
+// memory holds only the bitmaps, which leaves the rest of the SM's on-chip memory to the
+// L1 that serves the gathers.
 template <typename T, typename Epi>
 __global__ void __launch_bounds__(kSpmvThreads, spmv_min_blocks<T>())
     k_spmv(SpmvArgs a, const T* __restrict__ u, Epi epi) {
