@@ -66,7 +66,9 @@ class Graph:
 
     ``follower[k]`` follows ``leader[k]`` (int32, host or device); ``lam``/``mu`` are FP64
     per-user rates.  Options mirror ``psi_options`` (precision ``fp32 | fp32_refine | fp64``,
-    tol_mode ``psi | s_abs``, bnorm_mode ``none | inf``, self_loops ``reject | drop``).
+    tol_mode ``psi | s_abs``, bnorm_mode ``none | inf``, self_loops ``reject | drop``,
+    spmv_tile ``0`` (chosen from the edge count) ``| 512 | 1024 | 2048`` nonzeros per tile of
+    the sparse product).
     ``allocator``: "torch" (the caching allocator), None (the library's stream-ordered
     cudaMallocAsync) or an object whose ``struct`` is a ``psi_allocator``.
     """
