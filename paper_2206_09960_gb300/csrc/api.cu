@@ -169,6 +169,20 @@ psi_status guarded(F&& f) {
 
 }  // namespace
 
+void fill_graph_stats(const Graph& g, psi_graph_stats* st) {
+  st->n = g.n;
+  st->m_input = g.m_input;
+  st->m_unique = g.m_unique;
+  st->n_rows = g.n_rows;
+  st->n_gathered = (int64_t)g.nX + g.nU;
+  st->max_followers = g.max_followers;
+  st->bnorm_inf = g.bnorm_inf;
+  st->rho_inf = g.rho_inf;
+  st->build_ms = g.build_ms;
+  st->device_bytes = g.al.live_bytes;
+  st->spmv_tile = g.tile;
+}
+
 }  // namespace psi
 
 using psi::Graph;
@@ -342,18 +356,7 @@ psi_status psi_graph_get_stats(const psi_graph* g, psi_graph_stats* st) {
     psi::set_last_error("graph or stats is NULL");
     return PSI_ERR_INVALID_ARG;
   }
-  const Graph& gg = g->g;
-  st->n = gg.n;
-  st->m_input = gg.m_input;
-  st->m_unique = gg.m_unique;
-  st->n_rows = gg.n_rows;
-  st->n_gathered = (int64_t)gg.nX + gg.nU;
-  st->max_followers = gg.max_followers;
-  st->bnorm_inf = gg.bnorm_inf;
-  st->rho_inf = gg.rho_inf;
-  st->build_ms = gg.build_ms;
-  st->device_bytes = gg.al.live_bytes;
-  st->spmv_tile = gg.tile;
+  psi::fill_graph_stats(g->g, st);
   return PSI_OK;
 }
 

@@ -1151,17 +1151,7 @@ psi_status psi_multi_get_stats(const psi_multi* h, psi_graph_stats* st) {
     psi::set_last_error("multi or stats is NULL");
     return PSI_ERR_INVALID_ARG;
   }
-  const psi::Graph& g = h->m.g;
-  st->n = g.n;
-  st->m_input = g.m_input;
-  st->m_unique = g.m_unique;
-  st->n_rows = g.n_rows;
-  st->n_gathered = (int64_t)g.nX + g.nU;
-  st->max_followers = g.max_followers;
-  st->bnorm_inf = g.bnorm_inf;
-  st->rho_inf = g.rho_inf;
-  st->build_ms = g.build_ms;
-  st->device_bytes = g.al.live_bytes;
+  psi::fill_graph_stats(h->m.g, st);
   return PSI_OK;
 }
 

@@ -32,6 +32,8 @@ void topk(const Graph& g, int32_t k, int32_t* d_ids, double* d_vals);
 void topk_raw(const double* psi, const int32_t* perm, int64_t n, int32_t k, int32_t* d_ids, double* d_vals,
               Allocator& al, cudaStream_t s);
 bool is_device_pointer(const void* p);
+// the psi_graph_stats of a built graph (the single-graph, batch and multi-graph handles)
+void fill_graph_stats(const Graph& g, psi_graph_stats* st);
 // graph build (build.cu); hook (nullable) sees the follower-grouped CSR before it is freed
 struct BuildHook;
 void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const int32_t* leader,

@@ -222,3 +222,14 @@ def test_multi_tight_absolute_tolerance():
         # refinement rounds of the FP32 series: more steps than plain FP64, but boundedly
         assert out["infos"][q]["iters"] <= 2 * ref["iters"] + 10
         assert rel_l1(out["psi"][sum(int(x) for x in w["n_g"][:q]):][:n], ref["psi"]) <= 1e-9
+
+
+def test_multi_tile_sizes_agree():
+    """The union's product runs on 512-nonzero tiles unless told otherwise; another tile size
+    changes only the summation order (and so, at most, a refinement round)."""
+    w = psigen.multi_workload(8, seed=5, n_lo=500, n_hi=8000)
+    small = multi_solve(w, eps=1e-9)
+    large = multi_solve(w, eps=1e-9, spmv_tile=2048)
+    assert small["stats"]["spmv_tile"] == 512 and large["stats"]["spmv_tile"] == 2048
+    _check_against_oracle(w, large, eps=1e-9)
+    assert rel_l1(small["psi"], large["psi"]) <= 1e-8
