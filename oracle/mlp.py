@@ -5,6 +5,16 @@ Algorithm 2 (whose fixed point does not depend on s_0). This module is the plain
 its GPU forward and backward kernels are checked against: 8 -> 64 -> 64 -> 1 with exact
 GELU, x -> (x - mean) / std rounded to BF16, weights rounded to BF16, every sum in FP64.
 Loss: mean over rows of (yhat - (t - t_mean) / t_std)^2.
+
+Both routines take ``bf16_round``: True (default) rounds the weights and normalised inputs to
+BF16 as the GPU kernels do; False keeps them in FP64, which makes the loss a smooth function
+of the parameters so the gradient can be checked against finite differences.
+
+Parity pins (``tests/test_oracle_mlp.py``, CPU): ``gelu`` against tabulated values of the
+standard normal distribution function; ``gelu_grad`` against central differences of
+``gelu``; ``forward`` against a network whose output is worked out by hand from those
+tabulated values; ``loss_and_grad`` against central differences of the loss, parameter by
+parameter, with the rounding off.
 """
 from __future__ import annotations
 
@@ -41,20 +51,30 @@ def gelu_grad(z):
     return 0.5 * (1.0 + erf(z / np.sqrt(2.0))) + z * np.exp(-0.5 * z * z) / np.sqrt(2.0 * np.pi)
 
 
-def forward(params, norm, x):
+def _inputs(params, norm, x, bf16_round):
+    if bf16_round:
+        p = {k: bf16(v) for k, v in unpack(params).items()}
+        xn = bf16((np.asarray(x, np.float32) - np.float32(norm[:K_IN])) / np.float32(norm[K_IN:2 * K_IN]))
+    else:
+        p = unpack(params)
+        xn = (np.asarray(x, np.float64) - np.asarray(norm[:K_IN], np.float64)) / np.asarray(norm[K_IN:2 * K_IN],
+                                                                                             np.float64)
+    return p, xn
+
+
+def forward(params, norm, x, bf16_round=True):
     """Predicted log s (de-normalised)."""
-    p = {k: bf16(v) for k, v in unpack(params).items()}
-    xn = bf16((np.asarray(x, np.float32) - np.float32(norm[:K_IN])) / np.float32(norm[K_IN:2 * K_IN]))
+    p, xn = _inputs(params, norm, x, bf16_round)
     h1 = gelu(xn @ p["W1"] + p["b1"])
     h2 = gelu(h1 @ p["W2"] + p["b2"])
     y = h2 @ p["W3"] + p["b3"][0]
     return y * norm[2 * K_IN + 1] + norm[2 * K_IN]
 
 
-def loss_and_grad(params, norm, x, t):
-    """(loss, gradient[4801]) with respect to the BF16-rounded parameters."""
-    p = {k: bf16(v) for k, v in unpack(params).items()}
-    xn = bf16((np.asarray(x, np.float32) - np.float32(norm[:K_IN])) / np.float32(norm[K_IN:2 * K_IN]))
+def loss_and_grad(params, norm, x, t, bf16_round=True):
+    """(loss, gradient[4801]) with respect to the (BF16-rounded, unless bf16_round is False)
+    parameters."""
+    p, xn = _inputs(params, norm, x, bf16_round)
     tn = (np.asarray(t, np.float64) - norm[2 * K_IN]) / norm[2 * K_IN + 1]
     z1 = xn @ p["W1"] + p["b1"]
     h1 = gelu(z1)
