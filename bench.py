@@ -8,10 +8,14 @@ psi_topk (k = 100).  Default workload: R-MAT scale 25 (N = 2^25), edge factor 16
 (a, b, c) = (.57, .19, .19), random relabel, lambda, mu ~ LogNormal(0, 1.5) clipped to
 [1e-3, 1e3] -- a synthetic stand-in for the paper's social graphs.
 
-``value`` is the seconds per step with inputs resident in HBM; ``e2e`` is the same step
-through the C ABI from pinned host buffers (H2D of edges and rates, D2H of the top-k inside
-the timed region).  ``--impl reference`` times the FP64 CPU oracle on the host cores
-instead.  Multi-GPU runs are replicas (one independent graph per rank, weak scaling).
+``value`` is the whole-path throughput in input edges per second (edge draws of the
+workload x ranks / seconds per step) with inputs resident in HBM; ``ms_per_step`` is the
+step time behind it.  ``e2e`` is the same step through the C ABI from pinned host buffers
+(H2D of edges and rates, D2H of the top-k inside the timed region).  After the timed
+steps the oracle solves the same graph on the host cores: its time is ``cpu_baseline``
+and the comparison of its psi with the GPU's is ``parity``.  ``--impl reference`` times the
+FP64 CPU oracle alone, one bounded sample of the workload per step.  Multi-GPU runs are
+replicas (one independent graph per rank, weak scaling).
 """
 from __future__ import annotations
 
@@ -22,6 +26,7 @@ import os
 import statistics
 import subprocess
 import sys
+import platform
 import tempfile
 import time
 
@@ -37,6 +42,8 @@ NCU_TRAFFIC = {"sha": "7bef0330ec15c30e", "bytes_per_launch": 2895861632,
                        "R-MAT scale 25 bench step, one ncu capture of 3 launches (1-pass metrics)"}
 KERNEL_SOURCES = ["paper_2206_09960_gb300/csrc/spmv.cuh", "paper_2206_09960_gb300/csrc/common.cuh"]
 CPU_SAMPLE_SCALE = 20
+ONE_THREAD_SCALE = 18
+UNIT = "edges/s"
 
 
 def kernel_sha() -> str:
@@ -121,40 +128,170 @@ def dist_env():
     return ws, rank, local
 
 
-def cpu_sample_seconds(seed: int, eps: float):
-    """Full oracle solve (canonicalise + build A, B + Algorithm 2 + ranking) of a smaller
-    graph with the same recipe; returns (seconds, draws of the sample, threads)."""
-    import oracle
-    import psigen
+def host_info():
+    """Host cores and CPU model of the machine the oracle runs on."""
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model or platform.processor() or platform.machine()}
 
-    w = psigen.workload("rmat", seed=seed, scale=CPU_SAMPLE_SCALE)
+
+def oracle_seconds(w, eps, threads=None):
+    """The oracle as it stands on workload `w`: canonicalise + build A, B explicitly +
+    Algorithm 2 to eps on the psi-tolerance + the top-100 ranking.  Returns (seconds,
+    oracle output, threads used)."""
+    import oracle
+
+    if threads:
+        oracle.set_threads(threads)
+    used = oracle.num_threads()
     t = time.perf_counter()
     out = oracle.solve(w["n"], w["follower"], w["leader"], w["lam"], w["mu"], eps=eps, tol_mode=oracle.TOL_PSI)
-    oracle.topk(out["psi"], 100)
-    return time.perf_counter() - t, int(w["follower"].size), oracle.num_threads()
+    out["top_ids"], out["top_vals"] = oracle.topk(out["psi"], 100)
+    sec = time.perf_counter() - t
+    if threads:
+        oracle.set_threads(os.cpu_count() or 1)
+    return sec, out, used
+
+
+def oracle_bytes(n, draws):
+    """Host memory the oracle needs for a graph: the sort keys (8 B per draw), both explicit
+    CSR copies of A and B (two ids and four FP64 values per edge) and its per-user vectors."""
+    return 8 * draws + 40 * draws + 64 * n
+
+
+def host_available_bytes():
+    """MemAvailable, capped by the cgroup's memory limit (None if neither is readable)."""
+    avail = None
+    try:
+        with open("/proc/meminfo") as fh:
+            for line in fh:
+                if line.startswith("MemAvailable:"):
+                    avail = int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    for path in ("/sys/fs/cgroup/memory.max", "/sys/fs/cgroup/memory/memory.limit_in_bytes"):
+        try:
+            with open(path) as fh:
+                v = fh.read().strip()
+            if v.isdigit():
+                used = 0
+                for upath in ("/sys/fs/cgroup/memory.current", "/sys/fs/cgroup/memory/memory.usage_in_bytes"):
+                    if os.path.exists(upath):
+                        with open(upath) as fh:
+                            used = int(fh.read().strip() or 0)
+                        break
+                room = int(v) - used
+                avail = room if avail is None else min(avail, room)
+        except (OSError, ValueError):
+            pass
+    return avail
+
+
+def parity_block(gpu_psi, gpu_top, out, m_unique_gpu, tol=1e-6):
+    """psi of the GPU against the oracle's on the same graph: relative L1 (Eq. 12's psi, the
+    spec measure), relative L2 (the paper's Eq. 23), the top-100 ids (a swap of two
+    users whose oracle values differ by less than tol relative to them counts as a near
+    tie, not a mismatch) and the unique edge count (bit-exact)."""
+    import numpy as np
+
+    ref = out["psi"]
+    rel_l1 = float(np.abs(gpu_psi - ref).sum() / np.abs(ref).sum())
+    rel_l2 = float(np.linalg.norm(gpu_psi - ref) / np.linalg.norm(ref))
+    ids_g = np.asarray(gpu_top[0])
+    ids_o = np.asarray(out["top_ids"])
+    exact = bool(np.array_equal(ids_g, ids_o))
+    swaps = [(int(a), int(b)) for a, b in zip(ids_g, ids_o) if a != b]
+    near = len(swaps)
+    ok = all(abs(ref[a] - ref[b]) <= tol * max(abs(ref[a]), abs(ref[b])) for a, b in swaps)
+    return {"rel_l1": rel_l1, "rel_l2": rel_l2, "tol_rel_l1": tol, "rel_l1_ok": rel_l1 <= tol,
+            "top100_equal": exact, "top100_equal_up_to_near_ties": bool(ok), "near_tie_swaps": near,
+            "m_unique_equal": int(out["m_unique"]) == int(m_unique_gpu),
+            "psi_sum_gpu": float(gpu_psi.sum()), "psi_sum_oracle": float(ref.sum()),
+            "oracle": f"FP64, same graph and stop rule, {int(out['iters'])} steps"}
+
+
+def host_placement(buf):
+    """Where a pinned host buffer lives relative to the GPU: the NUMA nodes of its pages (from
+    /proc/self/numa_maps), the GPU's NUMA node and the host's node count (Linux only)."""
+    import glob
+
+    out = {"host_numa_nodes": len(glob.glob("/sys/devices/system/node/node[0-9]*"))}
+    try:
+        bus = subprocess.run(["nvidia-smi", "--query-gpu=pci.bus_id", "--format=csv,noheader", "-i",
+                              os.environ.get("LOCAL_RANK", "0")], capture_output=True, text=True,
+                             timeout=10).stdout.strip().lower()
+        tail = bus[-12:] if bus else ""
+        for d in glob.glob("/sys/bus/pci/devices/*"):
+            if tail and d.lower().endswith(tail[-7:]):
+                with open(os.path.join(d, "numa_node")) as fh:
+                    out["gpu_numa_node"] = int(fh.read().strip())
+    except (OSError, ValueError, subprocess.SubprocessError):
+        pass
+    try:
+        addr = buf.data_ptr()
+        with open("/proc/self/numa_maps") as fh:
+            for line in fh:
+                start = int(line.split()[0], 16)
+                if start <= addr < start + buf.numel() * buf.element_size():
+                    out["buffer_pages"] = " ".join(t for t in line.split() if t.startswith("N") and "=" in t)
+                    break
+    except (OSError, ValueError):
+        pass
+    return out
+
+
+def pinned_h2d_gbs(h, d, stream, reps=3):
+    """Host-to-device bandwidth of one pinned input buffer (GB/s), timed with CUDA events."""
+    import torch
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    d.copy_(h, non_blocking=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        d.copy_(h, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return h.numel() * h.element_size() * reps / (e0.elapsed_time(e1) / 1e3) / 1e9
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle alone on the host cores.  Each step is one bounded
+    sample of the workload -- the whole path (canonicalise, build, Algorithm 2, ranking) on
+    an R-MAT graph of the same recipe at scale CPU_SAMPLE_SCALE -- and the value is that
+    sample's edge draws per second, the unit of the GPU arm."""
+    import psigen
+
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    draws_full = 16 << args.scale
+    w = psigen.workload("rmat", seed=args.seed, scale=min(CPU_SAMPLE_SCALE, args.scale))
+    draws = int(w["follower"].size)
     times = []
     threads = 1
     for i in range(args.warmup + args.steps):
-        sec, draws, threads = cpu_sample_seconds(args.seed, args.eps)
+        sec, _, threads = oracle_seconds(w, args.eps)
         if i >= args.warmup:
-            times.append(sec * draws_full / draws)
-    v = statistics.mean(times)
-    sample = (f"full FP64 oracle solve (canonicalise, explicit A/B, Algorithm 2 to eps={args.eps:g} on eps_t/N, "
-              f"top-100) of R-MAT scale {CPU_SAMPLE_SCALE} (same recipe), time x {draws_full // draws} "
-              f"(edge-draw ratio to scale {args.scale})")
-    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(workload_config(args, None), precision="fp64 throughout (the oracle)"),
-            "cpu_baseline": {"value": v, "unit": "s", "cores": threads, "kind": "oracle", "sample": sample},
-            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            times.append(sec)
+    sec = statistics.mean(times)
+    v = draws / sec
+    sample = (f"whole path of the oracle (canonicalise, explicit A/B, Algorithm 2 to eps={args.eps:g} on eps_t/N, "
+              f"top-100) on R-MAT scale {min(CPU_SAMPLE_SCALE, args.scale)} of the same recipe ({draws} edge draws) "
+              f"per step, {threads} threads")
+    cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample}
+    cpu.update(host_info())
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(args),
+            "cpu_baseline": cpu,
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
@@ -412,17 +549,12 @@ def run_warmstart(args, n_train=200, eval_scale=23, train_steps=1500):
     print(json.dumps(line), flush=True)
 
 
-def workload_config(args, stats):
-    cfg = {"workload": f"rmat_scale{args.scale}_ef16_a.57_b.19_c.19_relabel_lognormal1.5",
-           "n": 1 << args.scale, "edge_draws": 16 << args.scale, "eps": args.eps,
-           "allocator": getattr(args, "allocator", "torch"),
-           "tolerance": "eps_t/N (psi tolerance, B_norm=1)", "precision": "fp32 terms, fp64 iterate and residual",
-           "topk": 100, "l2": "inputs larger than L2 (edge list 8 B x draws)", "parallelism": "replicas"}
-    if stats:
-        cfg["m_unique"] = stats["m_unique"]
-        cfg["n_rows"] = stats["n_rows"]
-        cfg["n_gathered"] = stats["n_gathered"]
-    return cfg
+def workload_config(args):
+    """The workload's configuration, identical in both arms."""
+    return {"workload": f"rmat_scale{args.scale}_ef16_a.57_b.19_c.19_relabel_lognormal1.5",
+            "n": 1 << args.scale, "edge_draws": 16 << args.scale, "eps": args.eps,
+            "tolerance": "eps_t/N (psi tolerance, B_norm=1)", "topk": 100,
+            "l2": "inputs larger than L2 (edge list 8 B x draws)", "parallelism": "replicas"}
 
 
 def main():
@@ -440,6 +572,7 @@ def main():
     ap.add_argument("--profile-solve", action="store_true",
                     help="multi workload: run one extra solve between cudaProfilerStart/Stop (ncu --profile-from-start off)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-check", action="store_true", help="skip the oracle parity check after the timed steps")
     ap.add_argument("--workload", default="rmat", choices=["rmat", "batch", "warmstart", "multi", "pagerank"],
                     help="rmat: the single-graph step (default); batch: 64 activity scenarios on one graph; "
                          "warmstart: train the start-vector network and compare steps and time to eps")
@@ -544,14 +677,25 @@ def main():
         t0 = time.perf_counter()
         h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         h0.record(stream)
+        e2e_marks, e2e_walls = [h0], []
         for _ in range(args.steps):
+            tw = time.perf_counter()
             step(host_in, ids_h, vals_h)
+            e2e_walls.append(time.perf_counter() - tw)
+            m = torch.cuda.Event(enable_timing=True)
+            m.record(stream)
+            e2e_marks.append(m)
         h1.record(stream)
         barrier()
         wall = (time.perf_counter() - t0) / args.steps
         e2e_s = max_over_ranks(max(h0.elapsed_time(h1) / 1e3 / args.steps, wall))
-        e2e = {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(2 * 4 * m0 + 2 * 8 * n),
-               "d2h_bytes_per_step": int(100 * (4 + 8))}
+        e2e_steps_ms = [round(e2e_marks[i].elapsed_time(e2e_marks[i + 1]), 3) for i in range(args.steps)]
+        h2d_gbs = pinned_h2d_gbs(f_h, f_d, stream)
+        placement = host_placement(f_h)
+        e2e = {"value": ws * m0 / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(2 * 4 * m0 + 2 * 8 * n),
+               "d2h_bytes_per_step": int(100 * (4 + 8)), "s_per_step": e2e_s, "h2d_gbs": h2d_gbs,
+               "host_buffers": placement, "steps_ms": e2e_steps_ms,
+               "steps_wall_ms": [round(x * 1e3, 3) for x in e2e_walls]}
 
     # ---- roofline of the dominant kernel: the FP32 series step (sparse product + fix-up)
     iters = statistics.mean(i["iters"] for i in infos)
@@ -559,38 +703,76 @@ def main():
     spmv_ms = sum(i["spmv_ms"] for i in infos)
     avg_launch_s = spmv_ms / 1e3 / max(spmv_launches, 1)
     m_u, n_rows, n_g = stats["m_unique"], stats["n_rows"], stats["n_gathered"]
-    alg_bytes = 4 * m_u + 32 * n_rows + 4 * n_g
+    alg_bytes = 4 * m_u + 32 * n  # 4M + 32N: every user's vectors once, every column index once
+    kernel_bytes = 4 * m_u + 32 * n_rows + 4 * n_g  # what this kernel has to touch (rows, gathered users)
     peak, peak_kind = measured_peaks()
     achieved = alg_bytes / avg_launch_s / 1e9
     traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["sha"] == kernel_sha() else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_kind": peak_kind,
                 "kernel": "k_spmv<float,EpiSeries> + k_fixup (FP32 series step of Eq. 13)",
-                "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_launch_s * 1e3,
-                "launches_timed": spmv_launches}
+                "alg_bytes_per_launch": alg_bytes, "alg_bytes_formula": "4*M_unique + 32*N",
+                "avg_launch_ms": avg_launch_s * 1e3, "launches_timed": spmv_launches,
+                "kernel_bytes_per_launch": kernel_bytes,
+                "frac_kernel_bytes": kernel_bytes / avg_launch_s / 1e9 / peak}
     solve_s = statistics.mean(i["ms"] for i in infos) / 1e3
     build_s = statistics.mean(builds_ms) / 1e3
 
-    cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        sec, draws, threads = cpu_sample_seconds(args.seed, args.eps)
-        cpu = {"value": sec * m0 / draws, "unit": "s", "cores": threads, "kind": "oracle",
-               "sample": f"full FP64 oracle solve of R-MAT scale {CPU_SAMPLE_SCALE} (same recipe, eps={args.eps:g} "
-                         f"on eps_t/N, top-100) took {sec:.2f} s; scaled by the edge-draw ratio {m0 // draws}"}
+    # ---- the GPU's psi and ranking of the same graph, for the parity check below
+    gpu_psi = gpu_top = None
+    if rank == 0 and ws == 1 and not args.no_check:
+        with psi.Graph(n, *dev_in, stream=stream, allocator=alloc) as g:
+            g.solve(args.eps, 100000)
+            gpu_psi = g.scores().cpu().numpy()
+            ids, vals = g.topk(100)
+            gpu_top = (ids.cpu().numpy(), vals.cpu().numpy())
 
-    line = {"metric": METRIC, "value": step_s, "unit": "s", "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(args, stats),
-            "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "roofline": roofline, "cpu_baseline": cpu,
+    line = {"metric": METRIC, "value": ws * m0 / step_s, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(args),
+            "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "roofline": roofline,
+            "precision": "fp32 series terms, fp64 iterate; confirming step and final product in float pairs "
+                         "(~48-bit sums) with fp64 row updates; fp64 gap, psi and sum of psi",
+            "allocator": args.allocator,
+            "graph": {"m_unique": m_u, "n_rows": n_rows, "n_gathered": n_g, "spmv_tile": stats.get("spmv_tile")},
             "time_to_eps_s": solve_s, "build_s": build_s, "iters": iters,
             "steps_ms": [round(x, 3) for x in steps_ms],
             "steps_build_ms": [round(x, 3) for x in builds_ms],
             "steps_solve_ms": [round(i["ms"], 3) for i in infos],
             "refinements": statistics.mean(i["refinements"] for i in infos),
             "gteps_per_iter": m_u / avg_launch_s / 1e9,
-            "hbm_frac_per_iter_4M_32N": (4 * m_u + 32 * n) / avg_launch_s / 1e9 / peak,
             "gap_psi_bound": infos[-1]["gap_psi_bound"], "gap_scaled": infos[-1]["gap_scaled"],
             "psi_sum": infos[-1]["psi_sum"], "problems_per_s": ws / step_s}
+
+    # ---- after every GPU measurement: the oracle on the same graph (all host cores), which
+    # is both the measured CPU baseline and the parity check, plus a one-thread sample
+    if rank == 0 and ws == 1 and not (args.no_check and args.no_cpu_baseline):
+        del dev_in, f_d, l_d, lam_d, mu_d
+        w = {"n": n, "follower": f_h.numpy(), "leader": l_h.numpy(), "lam": lam_h.numpy(), "mu": mu_h.numpy()}
+        need = oracle_bytes(n, m0)
+        avail = host_available_bytes()
+        if avail is not None and avail < 1.5 * need:
+            why = f"host memory: {avail / 2**30:.0f} GiB available, the oracle needs ~{need / 2**30:.0f} GiB"
+            line["cpu_baseline"] = {"unavailable": why}
+            line["parity"] = {"unavailable": why}
+        else:
+            sec, out, threads = oracle_seconds(w, args.eps)
+            cpu = {"value": m0 / sec, "unit": UNIT, "cores": threads, "kind": "oracle",
+                   "sample": f"the whole workload (R-MAT scale {args.scale}, {m0} edge draws), one full oracle run: "
+                             f"canonicalise, explicit A/B, Algorithm 2 to eps={args.eps:g} on eps_t/N, top-100; "
+                             f"{sec:.1f} s on {threads} threads",
+                   "seconds": sec, "iters": int(out["iters"])}
+            cpu.update(host_info())
+            w1 = psigen.workload("rmat", seed=args.seed, scale=min(ONE_THREAD_SCALE, args.scale))
+            sec1, _, _ = oracle_seconds(w1, args.eps, threads=1)
+            d1 = int(w1["follower"].size)
+            cpu["one_thread"] = {"value": d1 / sec1, "unit": UNIT, "cores": 1, "seconds": sec1,
+                                 "sample": f"whole oracle path on R-MAT scale {min(ONE_THREAD_SCALE, args.scale)} "
+                                           f"of the same recipe ({d1} edge draws), 1 thread"}
+            if not args.no_cpu_baseline:
+                line["cpu_baseline"] = cpu
+            if gpu_psi is not None:
+                line["parity"] = parity_block(gpu_psi, gpu_top, out, stats["m_unique"])
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:

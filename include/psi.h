@@ -313,14 +313,19 @@ psi_status psi_solve_warm(psi_graph* g, const psi_mlp* m, double eps, int32_t ma
  * device memory up front in its own arena, or a host framework whose allocator owns every
  * device byte (a late cudaMalloc could fail, fragment that budget, or synchronise the
  * device mid-request).
- *   psi_in    device pointer: n FP64 values >= 0 (for example written by psi_scores);
- *             user id = index
+ *   psi_in    device pointer: n FP64 values (for example written by psi_scores); user
+ *             id = index.  Values are ranked in numeric order; -0.0 ranks as 0.0 and a
+ *             NaN above +infinity (psi itself is never negative or NaN).
  *   n         1 <= n < 2^31 - 1
  *   k         1 <= k <= min(n, 4096); larger k is PSI_ERR_INVALID_ARG
- *   ids_out   device pointer, k int32 user ids; vals_out device pointer, k FP64 (or NULL)
+ *   ids_out   device pointer, k int32 user ids; vals_out device pointer, k FP64 (or NULL):
+ *             vals_out[i] = psi_in[ids_out[i]]
  *   stream    cudaStream_t to queue the work on (NULL = legacy default stream)
  * The work is queued and the call returns without waiting; results are complete when the
- * stream reaches that point.  Host pointers are PSI_ERR_INVALID_ARG.
+ * stream reaches that point.  Host pointers, and device memory of a GPU other than the
+ * current one, are PSI_ERR_INVALID_ARG (managed memory is accepted).  A CUDA error left
+ * pending by earlier work is reported as PSI_ERR_CUDA without being cleared, and nothing
+ * is launched.
  * Working memory is one fixed 50,432-byte device array inside the library (held on every
  * device that loads it until the process exits).  All calls share it and it keeps the
  * last call's contents (each call clears what must start at zero), so calls whose work

@@ -49,8 +49,14 @@ struct Scratch {
   uint32_t* q;
 };
 
+// Order key of psi[i]: unsigned comparison of p follows the numeric order of the values
+// (sign bit flipped for values >= 0, all bits flipped for negative ones); -0.0 is ranked as
+// +0.0 (adding +0.0 turns it into +0.0) and every NaN as the canonical positive NaN, above
+// +infinity.  q = ~i ranks equal values by ascending id.
 __device__ __forceinline__ void na_key(const double* psi, int64_t i, uint64_t& p, uint32_t& q) {
-  p = (uint64_t)__double_as_longlong(psi[i]);
+  const double v = psi[i] + 0.0;
+  uint64_t b = v != v ? 0x7FF8000000000000ull : (uint64_t)__double_as_longlong(v);
+  p = (b >> 63) ? ~b : (b | 0x8000000000000000ull);
   q = 0xFFFFFFFFu - (uint32_t)i;
 }
 
@@ -131,13 +137,15 @@ __global__ void k_na_collect(const double* __restrict__ psi, int64_t n, Scratch 
 }
 
 // one block: bitonic sort of the k collected keys (descending), then the output
-__global__ void __launch_bounds__(1024) k_na_sort_emit(Scratch s, int32_t k, int32_t* ids, double* vals) {
+__global__ void __launch_bounds__(1024) k_na_sort_emit(Scratch s, int32_t k, const double* __restrict__ psi,
+                                                       int32_t* ids, double* vals) {
   __shared__ unsigned long long sp[kNoAllocMaxK];
   __shared__ uint32_t sq[kNoAllocMaxK];
   int m = 1;
   while (m < k) m <<= 1;
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
-    sp[i] = i < k ? s.p[i] : 0ull;  // padding sorts last: no real key equals (0, 0)
+    sp[i] = i < k ? s.p[i] : 0ull;  // padding sorts last: no real key equals (0, 0) (p = 0
+                                      // only for a negative NaN, which na_key replaces)
     sq[i] = i < k ? s.q[i] : 0u;
   }
   __syncthreads();
@@ -162,8 +170,9 @@ __global__ void __launch_bounds__(1024) k_na_sort_emit(Scratch s, int32_t k, int
     }
   }
   for (int i = threadIdx.x; i < k; i += blockDim.x) {
-    ids[i] = (int32_t)(0xFFFFFFFFu - sq[i]);
-    if (vals) vals[i] = __longlong_as_double((long long)sp[i]);
+    const int32_t id = (int32_t)(0xFFFFFFFFu - sq[i]);
+    ids[i] = id;
+    if (vals) vals[i] = psi[id];  // the caller's own value
   }
 }
 
@@ -188,13 +197,17 @@ cudaError_t scratch_address(void** out) {
   return cudaSuccess;
 }
 
-bool on_device(const void* p) {
+// Device memory of the current device `dev`, or managed memory (reachable from every
+// device).  Device memory of another GPU is refused: the kernels would read or write it
+// through the peer mapping, or fault where there is none.
+bool on_device(const void* p, int dev) {
   cudaPointerAttributes a{};
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-    cudaGetLastError();
+    cudaGetLastError();  // the error this lookup itself raised
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 }  // namespace
@@ -212,12 +225,27 @@ extern "C" psi_status psi_topk_noalloc(const double* psi_in, int64_t n, int32_t 
     set_last_error("psi_topk_noalloc: k must be in [1, min(n, 4096)]");
     return PSI_ERR_INVALID_ARG;
   }
-  if (!on_device(psi_in) || !on_device(ids_out) || (vals_out && !on_device(vals_out))) {
-    set_last_error("psi_topk_noalloc: psi, ids_out and vals_out must be device memory");
+  // an error left pending by earlier work of the caller is not this call's: report it
+  // without clearing it, before anything here could be blamed for it
+  cudaError_t e = cudaPeekAtLastError();
+  if (e != cudaSuccess) {
+    set_last_error(std::string("psi_topk_noalloc: a CUDA error was pending before the call (left in place): ") +
+                   cudaGetErrorString(e));
+    return PSI_ERR_CUDA;
+  }
+  int dev = 0;
+  e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_last_error(std::string("psi_topk_noalloc: cudaGetDevice failed: ") + cudaGetErrorString(e));
+    return PSI_ERR_CUDA;
+  }
+  if (!on_device(psi_in, dev) || !on_device(ids_out, dev) || (vals_out && !on_device(vals_out, dev))) {
+    set_last_error("psi_topk_noalloc: psi, ids_out and vals_out must be device memory of the current device");
     return PSI_ERR_INVALID_ARG;
   }
   void* base = nullptr;
-  cudaError_t e = scratch_address(&base);
+  e = scratch_address(&base);
   if (e != cudaSuccess) {
     cudaGetLastError();
     set_last_error(std::string("psi_topk_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
@@ -227,8 +255,7 @@ extern "C" psi_status psi_topk_noalloc(const double* psi_in, int64_t n, int32_t 
   Scratch s{reinterpret_cast<NaState*>(b + kOffState), reinterpret_cast<uint32_t*>(b + kOffHist),
             reinterpret_cast<uint64_t*>(b + kOffP), reinterpret_cast<uint32_t*>(b + kOffQ)};
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  int sms = 0, dev = 0;
-  cudaGetDevice(&dev);
+  int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   int64_t blocks = (n + 255) / 256;
   const int64_t cap = (int64_t)(sms > 0 ? sms : 1) * 8;
@@ -239,8 +266,8 @@ extern "C" psi_status psi_topk_noalloc(const double* psi_in, int64_t n, int32_t 
     k_na_choose<<<1, 32, 0, st>>>(s, level);
   }
   k_na_collect<<<(int)blocks, 256, 0, st>>>(psi_in, n, s, (uint32_t)k);
-  k_na_sort_emit<<<1, 1024, 0, st>>>(s, k, ids_out, vals_out);
-  e = cudaGetLastError();
+  k_na_sort_emit<<<1, 1024, 0, st>>>(s, k, psi_in, ids_out, vals_out);
+  e = cudaGetLastError();  // nothing was pending on entry: only these launches can have failed
   if (e != cudaSuccess) {
     set_last_error(std::string("psi_topk_noalloc: launch failed: ") + cudaGetErrorString(e));
     return PSI_ERR_CUDA;

@@ -133,3 +133,20 @@ def test_batch_tight_absolute_tolerance():
         # refinement rounds of the FP32 series: more steps than plain FP64, but boundedly
         assert out["infos"][q]["iters"] <= 2 * ref["iters"] + 10
         assert rel_l1(out["psi"][q], ref["psi"]) <= 1e-9
+
+
+def test_batch_at_the_benchmark_size_four_of_64_scenarios():
+    """The batched benchmark's configuration (64 scenarios, LogNormal(0, 1) rates, R-MAT
+    scale 22, edge factor 16); four scenarios spread over the batch against the oracle."""
+    scale, S = 22, 64
+    w = psigen.workload("rmat", seed=0, scale=scale)
+    n = w["n"]
+    lam, mu = _rates(n, S, 22)
+    out = batch_solve(n, w["follower"], w["leader"], lam, mu, 1e-8, k=100)
+    assert out["status"] == "PSI_OK"
+    for q in (0, 21, 42, 63):
+        ref = oracle.solve(n, w["follower"], w["leader"], lam[q], mu[q], eps=1e-11)
+        assert out["stats"]["m_unique"] == ref["m_unique"]
+        assert out["infos"][q]["converged"] and out["infos"][q]["gap_scaled"] <= 1e-8
+        assert rel_l1(out["psi"][q], ref["psi"]) <= 1e-6, q
+        assert_same_ranking(out["ids"][q], ref["psi"], 1e-6)

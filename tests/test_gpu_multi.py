@@ -233,3 +233,12 @@ def test_multi_tile_sizes_agree():
     assert small["stats"]["spmv_tile"] == 512 and large["stats"]["spmv_tile"] == 2048
     _check_against_oracle(w, large, eps=1e-9)
     assert rel_l1(small["psi"], large["psi"]) <= 1e-8
+
+
+def test_multi_full_recipe_every_graph():
+    """The independent-graph benchmark's configuration itself: 256 Chung-Lu graphs with
+    N ~ U{1000..100000} and 12 draws per user, every graph against the oracle."""
+    w = psigen.multi_workload(256, seed=0)
+    out = multi_solve(w, k=100)
+    assert out["status"] == "PSI_OK"
+    _check_against_oracle(w, out)

@@ -369,3 +369,27 @@ def test_tile_sizes_agree_and_the_automatic_choice():
         with pytest.raises(PsiError) as e:
             gpu_solve(*args, spmv_tile=bad)
         assert e.value.status == B.PSI_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("scale", [20, 22])
+def test_rmat_benchmark_recipe_at_scale(scale):
+    """The benchmark's own recipe (R-MAT, edge factor 16, LogNormal(0, 1.5) rates) at scales
+    the oracle solves in seconds.  At scale 22 the product uses the benchmark's tile (2048
+    nonzeros) and the edge sort's key is over 40 bits wide, so its six-pass path runs, as
+    at scale 25."""
+    w = psigen.workload("rmat", seed=0, scale=scale)
+    n = w["n"]
+    ref = oracle.solve(n, w["follower"], w["leader"], w["lam"], w["mu"], to_floor=True, max_iter=5000)
+    out = gpu_solve(n, w["follower"], w["leader"], w["lam"], w["mu"], 1e-8)
+    st = out["stats"]
+    assert out["info"]["converged"], out["info"]
+    assert out["info"]["gap_scaled"] <= 1e-8
+    assert st["m_unique"] == ref["m_unique"]
+    assert rel_l1(out["psi"], ref["psi"]) <= 1e-6
+    assert_same_ranking(out["ids"], ref["psi"], 1e-6)
+    np.testing.assert_array_equal(out["vals"], out["psi"][out["ids"]])
+    assert abs(out["info"]["psi_sum"] - ref["psi"].sum()) <= 1e-6 * ref["psi"].sum()
+    # width of the edge sort's key: the leader row field and the follower's gathered index
+    key_bits = (st["n_rows"] - 1).bit_length() + st["n_gathered"].bit_length()
+    if scale >= 22:
+        assert key_bits > 40 and st["spmv_tile"] == 2048, (key_bits, st["spmv_tile"])
