@@ -677,11 +677,12 @@ def main():
         t0 = time.perf_counter()
         h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         h0.record(stream)
-        e2e_marks, e2e_walls = [h0], []
+        e2e_marks, e2e_walls, e2e_builds = [h0], [], []
         for _ in range(args.steps):
             tw = time.perf_counter()
-            step(host_in, ids_h, vals_h)
+            _, st_e = step(host_in, ids_h, vals_h)
             e2e_walls.append(time.perf_counter() - tw)
+            e2e_builds.append(st_e["build_ms"])
             m = torch.cuda.Event(enable_timing=True)
             m.record(stream)
             e2e_marks.append(m)
@@ -692,10 +693,14 @@ def main():
         e2e_steps_ms = [round(e2e_marks[i].elapsed_time(e2e_marks[i + 1]), 3) for i in range(args.steps)]
         h2d_gbs = pinned_h2d_gbs(f_h, f_d, stream)
         placement = host_placement(f_h)
+        ms_ = torch.cuda.memory_stats()
+        alloc_stats = {k: ms_.get(k) for k in ("num_alloc_retries", "num_device_alloc", "num_device_free")}
+        alloc_stats["reserved_gib"] = round(torch.cuda.memory_reserved() / 2**30, 1)
         e2e = {"value": ws * m0 / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(2 * 4 * m0 + 2 * 8 * n),
                "d2h_bytes_per_step": int(100 * (4 + 8)), "s_per_step": e2e_s, "h2d_gbs": h2d_gbs,
                "host_buffers": placement, "steps_ms": e2e_steps_ms,
-               "steps_wall_ms": [round(x * 1e3, 3) for x in e2e_walls]}
+               "steps_wall_ms": [round(x * 1e3, 3) for x in e2e_walls],
+               "steps_build_ms": [round(x, 3) for x in e2e_builds], "torch_allocator": alloc_stats}
 
     # ---- roofline of the dominant kernel: the FP32 series step (sparse product + fix-up)
     iters = statistics.mean(i["iters"] for i in infos)
