@@ -627,8 +627,8 @@ def main():
 
     alloc = "torch" if args.allocator == "torch" else None
 
-    def step(inputs, ids, vals, profile=False):
-        with psi.Graph(n, *inputs, profile=profile, stream=stream, allocator=alloc) as g:
+    def step(inputs, ids, vals, profile=False, **kw):
+        with psi.Graph(n, *inputs, profile=profile, stream=stream, allocator=alloc, **kw) as g:
             info = g.solve(args.eps, 100000)
             g.topk(100, ids, vals)
             return info, g.stats()
@@ -643,8 +643,9 @@ def main():
 
     dev_in = (f_d, l_d, lam_d, mu_d)
     host_in = (f_h, l_h, lam_h, mu_h)
+    warm_stats = []
     for _ in range(args.warmup):
-        step(dev_in, ids_d, vals_d)
+        warm_stats.append(step(dev_in, ids_d, vals_d)[1])
 
     # ---- timed region: inputs resident in HBM
     clocks = Clocks(torch.cuda.current_device())
@@ -668,6 +669,13 @@ def main():
     clk = clocks.stop()
     step_s = max_over_ranks(e0.elapsed_time(e1) / 1e3 / args.steps)
     steps_ms = [marks[i].elapsed_time(marks[i + 1]) for i in range(args.steps)]
+
+    # ---- the autotuner's pick (made on the first warm-up graph) against the fixed rule
+    info_fixed, st_fixed = step(dev_in, ids_d, vals_d, profile=True, autotune=False)
+    tuner = {"tile": stats["spmv_tile"], "hot": stats["spmv_hot"], "tune_ms": warm_stats[0]["tune_ms"],
+             "fixed_rule": {"tile": st_fixed["spmv_tile"], "hot": 0,
+                            "series_step_ms": info_fixed["spmv_ms"] / max(info_fixed["spmv_timed"], 1),
+                            "time_to_eps_s": info_fixed["ms"] / 1e3}}
 
     # ---- end to end from pinned host buffers (H2D of inputs and D2H of the ranking inside)
     e2e = None
@@ -715,7 +723,8 @@ def main():
     traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["sha"] == kernel_sha() else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_kind": peak_kind,
-                "kernel": "k_spmv<float,EpiSeries> + k_fixup (FP32 series step of Eq. 13)",
+                "kernel": (f"k_spmv<float,EpiSeries,{32 if stats['spmv_hot'] else 8}> + k_fixup "
+                           f"(FP32 series step of Eq. 13; {stats['spmv_hot']} entries from shared memory)"),
                 "alg_bytes_per_launch": alg_bytes, "alg_bytes_formula": "4*M_unique + 32*N",
                 "avg_launch_ms": avg_launch_s * 1e3, "launches_timed": spmv_launches,
                 "kernel_bytes_per_launch": kernel_bytes,
@@ -739,7 +748,9 @@ def main():
             "precision": "fp32 series terms, fp64 iterate; confirming step and final product in float pairs "
                          "(~48-bit sums) with fp64 row updates; fp64 gap, psi and sum of psi",
             "allocator": args.allocator,
-            "graph": {"m_unique": m_u, "n_rows": n_rows, "n_gathered": n_g, "spmv_tile": stats.get("spmv_tile")},
+            "graph": {"m_unique": m_u, "n_rows": n_rows, "n_gathered": n_g, "spmv_tile": stats.get("spmv_tile"),
+                      "spmv_hot": stats.get("spmv_hot")},
+            "autotune": dict(tuner, series_step_ms=avg_launch_s * 1e3),
             "time_to_eps_s": solve_s, "build_s": build_s, "iters": iters,
             "steps_ms": [round(x, 3) for x in steps_ms],
             "steps_build_ms": [round(x, 3) for x in builds_ms],

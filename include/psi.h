@@ -99,6 +99,17 @@ typedef struct psi_options {
                           rounding. */
   void* stream;        /* cudaStream_t to queue all work on */
   const psi_allocator* allocator; /* NULL: cudaMallocAsync on stream */
+  int32_t autotune;    /* 1 (default): the first psi_solve of a graph of at least 2^22 nonzeros
+                          times the candidate configurations of the FP32 series product (tile of
+                          512/1024/2048 nonzeros unless spmv_tile fixes it; 0, 24576, 28672 or
+                          32768 most-gathered entries kept in shared memory) on the graph itself
+                          and keeps the fastest, remembered for later graphs of the same sizes
+                          in this process; 0: the fixed rule of spmv_tile, no shared-memory copy.
+                          Results do not depend on it beyond rounding.  PSI_FP32_REFINE only. */
+  int32_t spmv_hot;    /* -1 (default): chosen by the autotuner (0 without it); 0, 24576, 28672
+                          or 32768: that many most-gathered entries of the FP32 series product
+                          read from shared memory (at most the gathered users), which the
+                          autotuner then keeps.  Results do not depend on it beyond rounding. */
 } psi_options;
 
 /* Fills the defaults listed above. */
@@ -133,6 +144,10 @@ typedef struct psi_graph_stats {
   double build_ms;        /* wall time of psi_graph_create on the stream */
   int64_t device_bytes;   /* device memory held by the handle */
   int64_t spmv_tile;      /* nonzeros per tile of the sparse product (psi_options.spmv_tile) */
+  int64_t spmv_hot;       /* entries of the FP32 series product's gathered vector read from
+                             shared memory (0: none; psi_options.autotune) */
+  double tune_ms;         /* time the autotuner spent timing candidates on this handle (0 when
+                             the choice came from an earlier graph of the same sizes) */
 } psi_graph_stats;
 
 /*

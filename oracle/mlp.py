@@ -6,9 +6,13 @@ its GPU forward and backward kernels are checked against: 8 -> 64 -> 64 -> 1 wit
 GELU, x -> (x - mean) / std rounded to BF16, weights rounded to BF16, every sum in FP64.
 Loss: mean over rows of (yhat - (t - t_mean) / t_std)^2.
 
-Both routines take ``bf16_round``: True (default) rounds the weights and normalised inputs to
-BF16 as the GPU kernels do; False keeps them in FP64, which makes the loss a smooth function
-of the parameters so the gradient can be checked against finite differences.
+Both routines take ``bf16_round``: True (default) rounds every operand of every matrix
+product to BF16, as the GPU's BF16-in/FP32-accumulate kernels do -- the weights, the
+normalised inputs, the hidden activations h1 and h2, and in the backward pass the
+pre-activation gradients dz2 and dz1 where they enter a product -- while element-wise work
+and the bias sums stay unrounded; False keeps everything in FP64, which makes the loss a
+smooth function of the parameters so the gradient can be checked against finite
+differences.
 
 Parity pins (``tests/test_oracle_mlp.py``, CPU): ``gelu`` against tabulated values of the
 standard normal distribution function; ``gelu_grad`` against central differences of
@@ -51,6 +55,11 @@ def gelu_grad(z):
     return 0.5 * (1.0 + erf(z / np.sqrt(2.0))) + z * np.exp(-0.5 * z * z) / np.sqrt(2.0 * np.pi)
 
 
+def _r(a, bf16_round):
+    """A product operand: BF16-rounded when the kernels' rounding is modelled."""
+    return bf16(a) if bf16_round else a
+
+
 def _inputs(params, norm, x, bf16_round):
     if bf16_round:
         p = {k: bf16(v) for k, v in unpack(params).items()}
@@ -65,8 +74,8 @@ def _inputs(params, norm, x, bf16_round):
 def forward(params, norm, x, bf16_round=True):
     """Predicted log s (de-normalised)."""
     p, xn = _inputs(params, norm, x, bf16_round)
-    h1 = gelu(xn @ p["W1"] + p["b1"])
-    h2 = gelu(h1 @ p["W2"] + p["b2"])
+    h1 = _r(gelu(xn @ p["W1"] + p["b1"]), bf16_round)
+    h2 = _r(gelu(h1 @ p["W2"] + p["b2"]), bf16_round)
     y = h2 @ p["W3"] + p["b3"][0]
     return y * norm[2 * K_IN + 1] + norm[2 * K_IN]
 
@@ -77,16 +86,17 @@ def loss_and_grad(params, norm, x, t, bf16_round=True):
     p, xn = _inputs(params, norm, x, bf16_round)
     tn = (np.asarray(t, np.float64) - norm[2 * K_IN]) / norm[2 * K_IN + 1]
     z1 = xn @ p["W1"] + p["b1"]
-    h1 = gelu(z1)
+    h1 = _r(gelu(z1), bf16_round)
     z2 = h1 @ p["W2"] + p["b2"]
-    h2 = gelu(z2)
+    h2 = _r(gelu(z2), bf16_round)
     y = h2 @ p["W3"] + p["b3"][0]
     e = y - tn
     B = x.shape[0]
     loss = float(np.mean(e * e))
     dy = 2.0 * e / B
     dz2 = np.outer(dy, p["W3"]) * gelu_grad(z2)
-    dz1 = (dz2 @ p["W2"].T) * gelu_grad(z1)
-    g = {"W3": h2.T @ dy, "b3": np.array([dy.sum()]), "W2": h1.T @ dz2, "b2": dz2.sum(0), "W1": xn.T @ dz1,
-         "b1": dz1.sum(0)}
+    dz2r = _r(dz2, bf16_round)
+    dz1 = (dz2r @ p["W2"].T) * gelu_grad(z1)
+    g = {"W3": h2.T @ dy, "b3": np.array([dy.sum()]), "W2": h1.T @ dz2r, "b2": dz2.sum(0),
+         "W1": xn.T @ _r(dz1, bf16_round), "b1": dz1.sum(0)}
     return loss, np.concatenate([g[name].ravel() for name, _ in SIZES])

@@ -68,14 +68,16 @@ class Graph:
     per-user rates.  Options mirror ``psi_options`` (precision ``fp32 | fp32_refine | fp64``,
     tol_mode ``psi | s_abs``, bnorm_mode ``none | inf``, self_loops ``reject | drop``,
     spmv_tile ``0`` (chosen from the edge count) ``| 512 | 1024 | 2048`` nonzeros per tile of
-    the sparse product).
+    the sparse product, autotune: time the series product's configurations on the first
+    solve of a large graph and keep the fastest, spmv_hot ``-1`` (the autotuner's choice)
+    ``| 0 | 24576 | 28672 | 32768`` most-gathered entries read from shared memory).
     ``allocator``: "torch" (the caching allocator), None (the library's stream-ordered
     cudaMallocAsync) or an object whose ``struct`` is a ``psi_allocator``.
     """
 
     def __init__(self, n, follower, leader, lam, mu, precision="fp32_refine", tol_mode="psi",
                  bnorm_mode="none", self_loops="reject", reorder=True, profile=False, stream=None,
-                 allocator="torch", spmv_tile=0):
+                 allocator="torch", spmv_tile=0, autotune=True, spmv_hot=-1):
         import torch
 
         B.load()
@@ -89,6 +91,8 @@ class Graph:
         opt.reorder = 1 if reorder else 0
         opt.profile = 1 if profile else 0
         opt.spmv_tile = int(spmv_tile)
+        opt.autotune = 1 if autotune else 0
+        opt.spmv_hot = int(spmv_hot)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream

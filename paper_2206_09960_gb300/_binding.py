@@ -46,7 +46,8 @@ class psi_allocator(ctypes.Structure):
 class psi_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("tol_mode", ctypes.c_int32), ("bnorm_mode", ctypes.c_int32),
                 ("self_loops", ctypes.c_int32), ("reorder", ctypes.c_int32), ("profile", ctypes.c_int32),
-                ("spmv_tile", ctypes.c_int32), ("stream", ctypes.c_void_p), ("allocator", ctypes.POINTER(psi_allocator))]
+                ("spmv_tile", ctypes.c_int32), ("stream", ctypes.c_void_p), ("allocator", ctypes.POINTER(psi_allocator)),
+                ("autotune", ctypes.c_int32), ("spmv_hot", ctypes.c_int32)]
 
 
 class psi_solve_info(ctypes.Structure):
@@ -64,7 +65,8 @@ class psi_graph_stats(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("m_input", ctypes.c_int64), ("m_unique", ctypes.c_int64),
                 ("n_rows", ctypes.c_int64), ("n_gathered", ctypes.c_int64), ("max_followers", ctypes.c_int64),
                 ("bnorm_inf", ctypes.c_double), ("rho_inf", ctypes.c_double), ("build_ms", ctypes.c_double),
-                ("device_bytes", ctypes.c_int64), ("spmv_tile", ctypes.c_int64)]
+                ("device_bytes", ctypes.c_int64), ("spmv_tile", ctypes.c_int64), ("spmv_hot", ctypes.c_int64),
+                ("tune_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -181,6 +181,8 @@ void fill_graph_stats(const Graph& g, psi_graph_stats* st) {
   st->build_ms = g.build_ms;
   st->device_bytes = g.al.live_bytes;
   st->spmv_tile = g.tile;
+  st->spmv_hot = g.series_hot;
+  st->tune_ms = g.tune_ms;
 }
 
 }  // namespace psi
@@ -202,6 +204,8 @@ void psi_options_default(psi_options* opt) {
   opt->spmv_tile = 0;
   opt->stream = nullptr;
   opt->allocator = nullptr;
+  opt->autotune = 1;
+  opt->spmv_hot = -1;
 }
 
 psi_status psi_graph_create(int64_t n, int64_t m, const int32_t* follower, const int32_t* leader,
@@ -225,6 +229,10 @@ psi_status psi_graph_create(int64_t n, int64_t m, const int32_t* follower, const
     PSI_REQUIRE(o.self_loops == PSI_REJECT || o.self_loops == PSI_DROP, PSI_ERR_INVALID_ARG, "unknown self_loops");
     PSI_REQUIRE(o.spmv_tile == 0 || o.spmv_tile == 512 || o.spmv_tile == 1024 || o.spmv_tile == 2048,
                 PSI_ERR_INVALID_ARG, "spmv_tile must be 0, 512, 1024 or 2048");
+    PSI_REQUIRE(o.autotune == 0 || o.autotune == 1, PSI_ERR_INVALID_ARG, "autotune must be 0 or 1");
+    PSI_REQUIRE(o.spmv_hot == -1 || o.spmv_hot == 0 || o.spmv_hot == 24576 || o.spmv_hot == 28672 ||
+                    o.spmv_hot == 32768,
+                PSI_ERR_INVALID_ARG, "spmv_hot must be -1, 0, 24576, 28672 or 32768");
     h = new psi_graph();
     h->g.opt = o;
     h->g.stream = static_cast<cudaStream_t>(o.stream);

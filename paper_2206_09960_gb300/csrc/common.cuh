@@ -211,6 +211,9 @@ struct Graph {
   DBuf<int32_t> fix_tile;   // tiles whose first row started in an earlier tile
   int32_t tile = kSpmvTileMax;  // nonzeros per tile of the product
   int32_t num_tiles = 0, num_fix = 0;
+  int32_t series_hot = 0;       // gathered entries of the FP32 series product kept in shared memory
+  bool tuned = false;           // the autotuner has chosen tile and series_hot
+  double tune_ms = 0.0;
 
   // per-user constants, internal order
   DBuf<double> c64, d64, mu64, lam64, isig64;

@@ -1,7 +1,13 @@
 // solve.cu -- Power-psi (Algorithm 2) on the device: step kernels, the device-side stop
 // test, the three precision modes and the final psi.
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <chrono>
+#include <tuple>
+#include <type_traits>
 
+#include "build.cuh"
 #include "primitives.cuh"
 #include "trace.cuh"
 #include "solve.cuh"
@@ -148,6 +154,187 @@ int spmv_grid(int32_t tiles) {
   return spmv_blocks(per_sm, tiles);
 }
 
+constexpr int32_t kHotMax = 32768;  // largest shared-memory copy of the series product (FP32 entries)
+
+// One block per SM of the series product with a shared-memory copy (no more blocks than
+// the tiles fill)
+int hot_series_grid(int32_t tiles) {
+  static bool configured = false;
+  if (!configured) {
+    PSI_CUDA(cudaFuncSetAttribute(k_spmv<float, EpiSeries, kSpmvHotWarps>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(float) * kHotMax)));
+    configured = true;
+  }
+  const int64_t need = ceil_div(tiles > 0 ? tiles : 1, kSpmvHotWarps);
+  return (int)(need < num_sms() ? need : num_sms());
+}
+
+// ------------------------------------------------------------------ autotuner
+// The FP32 series product (the step that takes nearly all of a solve) has two free
+// parameters: the tile (512, 1024 or 2048 nonzeros per warp task) and the number of
+// most-gathered entries read from shared memory instead of L1/L2 (0, or a copy of 24K-32K
+// entries with one 32-warp block per SM).  Which is fastest depends on the graph's size
+// and degree distribution, so on the first solve of a large graph every candidate is
+// timed on the graph itself (CUDA events, a warm-up launch then three timed ones, on the
+// solver's own buffers before they are initialised) and the fastest is kept.  The choice is
+// remembered per graph signature for the process, so later graphs of the same sizes skip
+// the timing.
+struct TuneKey {
+  int64_t n_rows, nu, m, max_followers;
+  int32_t tile_req, hot_req;  // what the options fixed
+  bool operator<(const TuneKey& o) const {
+    return std::tie(n_rows, nu, m, max_followers, tile_req, hot_req) <
+           std::tie(o.n_rows, o.nu, o.m, o.max_followers, o.tile_req, o.hot_req);
+  }
+};
+struct TuneChoice {
+  int32_t tile, hot;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneChoice> g_tune_cache;
+
+constexpr int64_t kTuneMinNnz = (int64_t)1 << 22;  // smaller graphs keep the fixed rule
+
+// average time of one FP32 series step (product + fix-up) with the given schedule and copy
+float time_series_step(Graph& g, const Schedule& sc, int32_t hot, cudaStream_t s) {
+  Allocator& al = g.al;
+  DBuf<float> ch(al, (size_t)sc.tiles), ct(al, (size_t)sc.tiles);
+  SpmvArgs a{};
+  a.row_ptr = g.row_ptr.get();
+  a.col = g.col.get();
+  a.tile_row = sc.tile_row.get();
+  a.tile = sc.tile;
+  a.num_tiles = sc.tiles;
+  a.hot = hot;
+  a.n_rows = g.n_rows;
+  a.m = g.m_unique;
+  a.state = g.state.get();
+  a.gap_part = g.gap_part.get();
+  a.carry_head = ch.get();
+  a.carry_tail = ct.get();
+  FixArgs f{};
+  f.row_ptr = g.row_ptr.get();
+  f.tile_row = sc.tile_row.get();
+  f.tile = sc.tile;
+  f.fix_tile = sc.fix_tile.get();
+  f.num_fix = sc.num_fix;
+  f.state = g.state.get();
+  f.gap_fix = g.gap_fix.get();
+  f.carry_head = ch.get();
+  f.carry_tail = ct.get();
+  // scratch output: the series term goes to u32b, the sums to s64 (both initialised by the
+  // solve that follows)
+  EpiSeries epi{g.mu32.get(), g.isig32.get(), g.s64.get(), g.u32b.get(), g.nX};
+  auto launch = [&]() {
+    if (hot > 0) {
+      k_spmv<float, EpiSeries, kSpmvHotWarps>
+          <<<hot_series_grid(sc.tiles), kSpmvHotWarps * 32, sizeof(float) * (size_t)hot, s>>>(a, g.u32a.get(), epi);
+    } else {
+      k_spmv<float, EpiSeries><<<spmv_grid<float, EpiSeries>(sc.tiles), kSpmvThreads, 0, s>>>(a, g.u32a.get(), epi);
+    }
+    PSI_LAUNCHED();
+    if (sc.num_fix > 0) {
+      k_fixup<float, EpiSeries><<<fix_blocks(sc.num_fix), kFixThreads, 0, s>>>(f, epi);
+      PSI_LAUNCHED();
+    }
+  };
+  cudaEvent_t e0, e1;
+  PSI_CUDA(cudaEventCreate(&e0));
+  PSI_CUDA(cudaEventCreate(&e1));
+  launch();
+  PSI_CUDA(cudaEventRecord(e0, s));
+  for (int i = 0; i < 3; ++i) launch();
+  PSI_CUDA(cudaEventRecord(e1, s));
+  PSI_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  PSI_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return ms / 3.f;
+}
+
+void apply_schedule(Graph& g, Schedule&& sc) {
+  g.tile = sc.tile;
+  g.num_tiles = sc.tiles;
+  g.num_fix = sc.num_fix;
+  g.tile_row = std::move(sc.tile_row);
+  g.fix_tile = std::move(sc.fix_tile);
+  g.carry_head.reset(g.al, (size_t)(g.num_tiles > 0 ? g.num_tiles : 1));
+  g.carry_tail.reset(g.al, (size_t)(g.num_tiles > 0 ? g.num_tiles : 1));
+}
+
+void autotune_series(Graph& g, cudaStream_t s) {
+  g.tuned = true;
+  const int64_t nu = (int64_t)g.nX + g.nU;
+  // a requested copy, never longer than the gathered vector (u holds nu entries and a pad)
+  const int32_t hot_req = g.opt.spmv_hot < 0 ? -1 : (int32_t)std::min<int64_t>(g.opt.spmv_hot, nu);
+  if (g.opt.precision != PSI_FP32_REFINE) return;
+  if (!g.opt.autotune || g.m_unique < kTuneMinNnz || (g.opt.spmv_tile > 0 && hot_req >= 0)) {
+    g.series_hot = hot_req > 0 ? hot_req : 0;
+    return;
+  }
+  const TuneKey key{g.n_rows, nu, g.m_unique, g.max_followers, g.opt.spmv_tile, hot_req};
+  TuneChoice pick{g.tile, hot_req > 0 ? hot_req : 0};
+  bool cached = false;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      pick = it->second;
+      cached = true;
+    }
+  }
+  if (g.opt.spmv_tile > 0) pick.tile = g.opt.spmv_tile;
+  if (!cached) {
+    NvtxRange range("psi solve: autotune");
+    const auto t0 = std::chrono::steady_clock::now();
+    PSI_CUDA(cudaMemsetAsync(g.state.get(), 0, sizeof(DevState), s));
+    PSI_CUDA(cudaMemsetAsync(g.u32a.get(), 0, sizeof(float) * (size_t)(nu + 1), s));
+    PSI_CUDA(cudaMemsetAsync(g.s64.get(), 0, sizeof(double) * (size_t)g.n, s));
+    // the copy first, on the rule's tile; then the tile, with the best copy
+    const int32_t hots[4] = {0, 24576, 28672, kHotMax};
+    std::map<int32_t, Schedule> scheds;
+    auto sched_for = [&](int32_t tile) -> const Schedule& {
+      auto it = scheds.find(tile);
+      if (it == scheds.end())
+        it = scheds.emplace(tile, make_schedule(g.row_ptr.get(), g.n_rows, g.m_unique, g.al, s, tile)).first;
+      return it->second;
+    };
+    float best = 0.f;
+    bool first = true;
+    for (int32_t h : hots) {
+      if (hot_req >= 0 && h != 0) break;  // the copy is fixed by the options
+      if (hot_req >= 0) h = hot_req;
+      if (hot_req < 0 && h > 0 && nu < 8 * (int64_t)h) continue;  // a copy pays only as a small part of the vector
+      const float ms = time_series_step(g, sched_for(pick.tile), h, s);
+      if (first || ms < best) {
+        best = ms;
+        pick.hot = h;
+        first = false;
+      }
+    }
+    if (g.opt.spmv_tile == 0) {
+      const int32_t tiles[3] = {kSpmvTileMin, 2 * kSpmvTileMin, kSpmvTileMax};
+      const int32_t rule = pick.tile;
+      for (int32_t t : tiles) {
+        if (t == rule) continue;
+        const float ms = time_series_step(g, sched_for(t), pick.hot, s);
+        if (ms < best) {
+          best = ms;
+          pick.tile = t;
+        }
+      }
+    }
+    if (pick.tile != g.tile) apply_schedule(g, std::move(scheds.at(pick.tile)));
+    g.tune_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache[key] = pick;
+  } else if (pick.tile != g.tile) {
+    apply_schedule(g, make_schedule(g.row_ptr.get(), g.n_rows, g.m_unique, g.al, s, pick.tile));
+  }
+  g.series_hot = pick.hot;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ step launch
@@ -182,9 +369,20 @@ struct Stepper {
       PSI_CUDA(cudaEventRecord(e0, s));
     }
     if (g.num_tiles > 0) {
-      grid = spmv_grid<T, Epi>(g.num_tiles);
-      k_spmv<T, Epi><<<grid, kSpmvThreads, 0, s>>>(a, u, epi);
-      PSI_LAUNCHED();
+      if constexpr (std::is_same<Epi, EpiSeries>::value) {
+        if (g.series_hot > 0) {
+          a.hot = g.series_hot;
+          grid = hot_series_grid(g.num_tiles);
+          k_spmv<float, EpiSeries, kSpmvHotWarps>
+              <<<grid, kSpmvHotWarps * 32, sizeof(float) * (size_t)g.series_hot, s>>>(a, u, epi);
+          PSI_LAUNCHED();
+        }
+      }
+      if (a.hot == 0) {
+        grid = spmv_grid<T, Epi>(g.num_tiles);
+        k_spmv<T, Epi><<<grid, kSpmvThreads, 0, s>>>(a, u, epi);
+        PSI_LAUNCHED();
+      }
     }
     if (g.num_fix > 0) {
       FixArgs f{};
@@ -339,6 +537,7 @@ psi_status solve_with(Graph& g, const SolveConsts& K, const SolveTarget& T, doub
   PSI_REQUIRE(!std::isnan(eps), PSI_ERR_INVALID_ARG, "eps is NaN");
   cudaStream_t s = g.stream;
   ensure_iteration_buffers(g);
+  if (!g.tuned) autotune_series(g, s);
   if (T.final_psi) g.solved = false;
   const int64_t n = g.n;
   const int32_t nX = g.nX;

@@ -204,6 +204,7 @@ struct SpmvArgs {
   const int32_t* tile_row;
   int32_t tile;           // nonzeros per tile: kSpmvTileMin .. kSpmvTileMax, a power of two
   int32_t num_tiles;
+  int32_t hot;            // entries u[0, hot) staged in the block's shared memory (0: none)
   int32_t n_rows;
   int64_t m;
   const DevState* state;  // skip the step when state->done
@@ -264,6 +265,10 @@ constexpr int spmv_min_blocks() {
   return sizeof(T) == 4 ? 5 : (sizeof(T) == 8 ? 4 : 2);
 }
 
+// Threads per block of the product with a shared-memory copy of the most gathered entries
+// (one block per SM: the copy takes most of the SM's shared memory).
+constexpr int kSpmvHotWarps = 32;
+
 // One warp per tile; the warps of all blocks walk the tiles with a grid-wide stride.  A
 // tile's row ends are first marked in a bitmap in shared memory (bit q: nonzero nnz0 + q is
 // the last one of its row) from the tile's slice of row_ptr.  Every row has at least one
@@ -275,24 +280,36 @@ constexpr int spmv_min_blocks() {
 // the next step in a register.  Row indices come from the lanes' prefix counts of row ends
 // (one ballot per item position) and the scan's segment flags from one ballot.  The
 // gathers of the next step, and the column indices of the step after it, are issued before
-// the current step is reduced.  No block barrier is taken inside the tile loop, and shared
-// memory holds only the bitmaps, which leaves the rest of the SM's on-chip memory to the
-// L1 that serves the gathers.
-template <typename T, typename Epi>
-__global__ void __launch_bounds__(kSpmvThreads, spmv_min_blocks<T>())
+// the current step is reduced.  No block barrier is taken inside the tile loop.
+//
+// The gathers are served by the L1 and, for entries that miss it, by L2 requests, whose
+// rate bounds the product on large graphs.  With a.hot > 0 (WARPS = kSpmvHotWarps, one
+// block per SM) each block first copies u[0, a.hot) -- the users gathered most, since the
+// gathered index space is ordered by decreasing degree -- into shared memory and reads
+// those entries there; the rest of the SM's on-chip memory stays L1 for the others.  With
+// a.hot == 0 shared memory holds only the bitmaps and the whole of it serves as L1.
+template <typename T, typename Epi, int WARPS = kSpmvWarps>
+__global__ void __launch_bounds__(WARPS * 32, WARPS == kSpmvWarps ? spmv_min_blocks<T>() : 1)
     k_spmv(SpmvArgs a, const T* __restrict__ u, Epi epi) {
   constexpr bool kSkip = tile_skip_of<Epi>::value;
   constexpr int kWords = kSpmvTileMax / 32;  // bitmap words of the largest tile
   if (a.state->done) return;
-  __shared__ uint32_t ends_sh[kSpmvWarps][kWords];
-  __shared__ double gsh[kSpmvWarps];
+  __shared__ uint32_t ends_sh[WARPS][kWords];
+  __shared__ double gsh[WARPS];
+  extern __shared__ __align__(16) unsigned char spmv_hot_dyn[];
+  T* hot = reinterpret_cast<T*>(spmv_hot_dyn);
+  const int32_t nhot = a.hot;
+  if (nhot > 0) {
+    for (int32_t i = threadIdx.x; i < nhot; i += WARPS * 32) hot[i] = u[i];
+    __syncthreads();
+  }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t* ends = ends_sh[warp];
   const uint64_t pol_s = policy_evict_first();
   const uint64_t pol_k = policy_evict_last();
   T* carry_head = static_cast<T*>(a.carry_head);
   T* carry_tail = static_cast<T*>(a.carry_tail);
-  const int32_t stride = (int32_t)gridDim.x * kSpmvWarps;
+  const int32_t stride = (int32_t)gridDim.x * WARPS;
   double gap = 0.0;
 
   // column indices of step k of a tile (this lane's kSpmvItems nonzeros; col is padded to
@@ -302,12 +319,12 @@ __global__ void __launch_bounds__(kSpmvThreads, spmv_min_blocks<T>())
   };
   auto gather = [&](const int (&c)[kSpmvItems], T (&x)[kSpmvItems]) {
 #pragma unroll
-    for (int j = 0; j < kSpmvItems; ++j) x[j] = ld_gather(u + c[j], pol_k);
+    for (int j = 0; j < kSpmvItems; ++j) x[j] = c[j] < nhot ? hot[c[j]] : ld_gather(u + c[j], pol_k);
   };
   // this warp's tiles, in order: first, first + stride, ... (all below 2^31: num_tiles +
   // 32 strides); with tile skipping, the gates of 32 candidates are tested at once (one per
   // lane) and a ballot gives the tiles to run
-  const int32_t first = (int32_t)blockIdx.x * kSpmvWarps + warp;
+  const int32_t first = (int32_t)blockIdx.x * WARPS + warp;
   int32_t cand = first;  // next candidate tile (the first of the next batch when skipping)
   uint32_t on_bits = 0;  // tiles of the last batch still to run
   auto next_tile = [&]() -> int32_t {
@@ -427,7 +444,7 @@ __global__ void __launch_bounds__(kSpmvThreads, spmv_min_blocks<T>())
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
-    for (int w = 0; w < kSpmvWarps; ++w) t += gsh[w];
+    for (int w = 0; w < WARPS; ++w) t += gsh[w];
     a.gap_part[blockIdx.x] = t;
   }
 }

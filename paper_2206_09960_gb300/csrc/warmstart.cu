@@ -104,156 +104,424 @@ __global__ void k_to_bf16(const float* __restrict__ w, int n, __nv_bfloat16* b) 
   WGRID_STRIDE(i, n) b[i] = __float2bfloat16_rn(w[i]);
 }
 
-// y[r] = prediction of log s for row r (de-normalised)
-__global__ void __launch_bounds__(256) k_mlp_forward(const __nv_bfloat16* __restrict__ wb, const float* __restrict__ norm,
-                                                    int64_t rows, const float* __restrict__ x, float* y) {
-  __shared__ float w[kParams];
-  __shared__ float nm[kNorm];
-  for (int i = threadIdx.x; i < kParams; i += blockDim.x) w[i] = __bfloat162float(wb[i]);
-  if (threadIdx.x < kNorm) nm[threadIdx.x] = norm[threadIdx.x];
-  __syncthreads();
-  WGRID_STRIDE(r, rows) {
-    float xi[kIn];
+// ---- tensor-core tiles (mma.sync m16n8k16, BF16 operands, FP32 accumulation)
+// Fragment layout (PTX ISA, mma.m16n8k16 with .bf16): lane = 4 g + t (g = lane / 4, t = lane % 4);
+//   A (16x16, row major): a0 = A[g][2t..2t+1], a1 = A[g+8][2t..], a2 = A[g][2t+8..], a3 = A[g+8][2t+8..]
+//   B (16x8):             b0 = B[2t..2t+1][g], b1 = B[2t+8..2t+9][g]
+//   C (16x8, FP32):       c0, c1 = C[g][2t..2t+1], c2, c3 = C[g+8][2t..2t+1]
+// Two adjacent C tiles of a layer's output therefore form one A fragment of the next layer.
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);  // lo in the low half
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+__device__ __forceinline__ uint32_t pack_raw(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+  return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// The network's weights as B fragments of one warp (registers): W1 (K = 8 inputs padded to
+// 16, 8 column tiles), W2 (4 K steps x 8 column tiles), W3 (4 K steps, column 0 of a tile).
+struct MlpFrags {
+  uint32_t w1[8];
+  uint32_t w2[4][8][2];
+  uint32_t w3[4][2];
+};
+
+__device__ __forceinline__ void load_frags(const __nv_bfloat16* __restrict__ wb, int lane, MlpFrags& f) {
+  const int g = lane >> 2, t = lane & 3;
 #pragma unroll
-    for (int i = 0; i < kIn; ++i) xi[i] = bf16r((x[r * kIn + i] - nm[i]) / nm[kIn + i]);
-    float h1[kH];
+  for (int nt = 0; nt < 8; ++nt)
+    f.w1[nt] = pack_raw(wb[kOffW1 + (2 * t) * kH + 8 * nt + g], wb[kOffW1 + (2 * t + 1) * kH + 8 * nt + g]);
 #pragma unroll
-    for (int j = 0; j < kH; ++j) {
-      float z = w[kOffB1 + j];
+  for (int kk = 0; kk < 4; ++kk) {
 #pragma unroll
-      for (int i = 0; i < kIn; ++i) z = fmaf(w[kOffW1 + i * kH + j], xi[i], z);
-      h1[j] = gelu(z);
+    for (int nt = 0; nt < 8; ++nt) {
+      const int k0 = 16 * kk + 2 * t, n = 8 * nt + g;
+      f.w2[kk][nt][0] = pack_raw(wb[kOffW2 + k0 * kH + n], wb[kOffW2 + (k0 + 1) * kH + n]);
+      f.w2[kk][nt][1] = pack_raw(wb[kOffW2 + (k0 + 8) * kH + n], wb[kOffW2 + (k0 + 9) * kH + n]);
     }
-    float out = w[kOffB3];
-    for (int k = 0; k < kH; ++k) {
-      float z = w[kOffB2 + k];
-#pragma unroll
-      for (int j = 0; j < kH; ++j) z = fmaf(w[kOffW2 + j * kH + k], h1[j], z);
-      out = fmaf(w[kOffW3 + k], gelu(z), out);
-    }
-    y[r] = out * nm[2 * kIn + 1] + nm[2 * kIn];
+    const int k0 = 16 * kk + 2 * t;
+    f.w3[kk][0] = g == 0 ? pack_raw(wb[kOffW3 + k0], wb[kOffW3 + k0 + 1]) : 0u;
+    f.w3[kk][1] = g == 0 ? pack_raw(wb[kOffW3 + k0 + 8], wb[kOffW3 + k0 + 9]) : 0u;
   }
 }
 
-constexpr int kRowsPerGroup = 16;  // rows per block iteration in training (16 threads per row)
+// Forward pass of 16 rows [r0, r0 + 16) by one warp.  Outputs the normalised prediction of
+// rows r0 + g (y_lo) and r0 + g + 8 (y_hi) in lanes with t == 0; optionally keeps z1, z2
+// (pre-activations) and the BF16 A fragments of h1, h2 for the backward pass.
+struct MlpTile {
+  float z1[8][4], z2[8][4];
+  uint32_t h1[4][4], h2[4][4];
+  uint32_t x[4];
+};
 
-// Gradient of L = (1/B) sum_r (yhat_r - t_r)^2 over normalised targets, per block over a fixed
-// set of row groups; part[block][kParams] and loss_part[block].
+template <typename W2Frag>
+__device__ __forceinline__ void mlp_tile_forward(const MlpFrags& f, W2Frag&& w2frag, const float* __restrict__ bias1,
+                                                 const float* __restrict__ bias2, float bias3,
+                                                 const float* __restrict__ nm, const float* __restrict__ x,
+                                                 int64_t rows, int64_t r0, int lane, MlpTile& T, float& y_lo,
+                                                 float& y_hi) {
+  const int g = lane >> 2, t = lane & 3;
+  // inputs: normalised, rounded to BF16; features 2t, 2t+1 of rows r0+g and r0+g+8
+  float xv[2][2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int64_t r = r0 + g + 8 * h;
+    const bool ok = r < rows;
+    const float2 v = ok ? *reinterpret_cast<const float2*>(x + r * kIn + 2 * t) : make_float2(0.f, 0.f);
+    xv[h][0] = ok ? (v.x - nm[2 * t]) / nm[kIn + 2 * t] : 0.f;
+    xv[h][1] = ok ? (v.y - nm[2 * t + 1]) / nm[kIn + 2 * t + 1] : 0.f;
+  }
+  T.x[0] = pack_bf16(xv[0][0], xv[0][1]);
+  T.x[1] = pack_bf16(xv[1][0], xv[1][1]);
+  T.x[2] = 0u;  // input columns 8..15 are padding
+  T.x[3] = 0u;
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) {
+    const float b0 = bias1[8 * nt + 2 * t], b1 = bias1[8 * nt + 2 * t + 1];
+    T.z1[nt][0] = b0;
+    T.z1[nt][1] = b1;
+    T.z1[nt][2] = b0;
+    T.z1[nt][3] = b1;
+    mma_bf16(T.z1[nt], T.x, f.w1[nt], 0u);
+  }
+#pragma unroll
+  for (int kk = 0; kk < 4; ++kk) {
+    T.h1[kk][0] = pack_bf16(gelu(T.z1[2 * kk][0]), gelu(T.z1[2 * kk][1]));
+    T.h1[kk][1] = pack_bf16(gelu(T.z1[2 * kk][2]), gelu(T.z1[2 * kk][3]));
+    T.h1[kk][2] = pack_bf16(gelu(T.z1[2 * kk + 1][0]), gelu(T.z1[2 * kk + 1][1]));
+    T.h1[kk][3] = pack_bf16(gelu(T.z1[2 * kk + 1][2]), gelu(T.z1[2 * kk + 1][3]));
+  }
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) {
+    const float b0 = bias2[8 * nt + 2 * t], b1 = bias2[8 * nt + 2 * t + 1];
+    T.z2[nt][0] = b0;
+    T.z2[nt][1] = b1;
+    T.z2[nt][2] = b0;
+    T.z2[nt][3] = b1;
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+      uint32_t b0, b1;
+      w2frag(kk, nt, b0, b1);
+      mma_bf16(T.z2[nt], T.h1[kk], b0, b1);
+    }
+  }
+#pragma unroll
+  for (int kk = 0; kk < 4; ++kk) {
+    T.h2[kk][0] = pack_bf16(gelu(T.z2[2 * kk][0]), gelu(T.z2[2 * kk][1]));
+    T.h2[kk][1] = pack_bf16(gelu(T.z2[2 * kk][2]), gelu(T.z2[2 * kk][3]));
+    T.h2[kk][2] = pack_bf16(gelu(T.z2[2 * kk + 1][0]), gelu(T.z2[2 * kk + 1][1]));
+    T.h2[kk][3] = pack_bf16(gelu(T.z2[2 * kk + 1][2]), gelu(T.z2[2 * kk + 1][3]));
+  }
+  float o[4] = {bias3, 0.f, bias3, 0.f};
+#pragma unroll
+  for (int kk = 0; kk < 4; ++kk) mma_bf16(o, T.h2[kk], f.w3[kk][0], f.w3[kk][1]);
+  y_lo = o[0];  // column 0 (lanes with t == 0)
+  y_hi = o[2];
+}
+
+// y[r] = prediction of log s for row r (de-normalised); one warp per 16-row tile
+__global__ void __launch_bounds__(256) k_mlp_forward(const __nv_bfloat16* __restrict__ wb, const float* __restrict__ norm,
+                                                    int64_t rows, const float* __restrict__ x, float* y) {
+  __shared__ float bias[2 * kH + 1];
+  __shared__ float nm[kNorm];
+  for (int i = threadIdx.x; i < kH; i += blockDim.x) {
+    bias[i] = __bfloat162float(wb[kOffB1 + i]);
+    bias[kH + i] = __bfloat162float(wb[kOffB2 + i]);
+  }
+  if (threadIdx.x == 0) bias[2 * kH] = __bfloat162float(wb[kOffB3]);
+  if (threadIdx.x < kNorm) nm[threadIdx.x] = norm[threadIdx.x];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  MlpFrags f;
+  load_frags(wb, lane, f);
+  const int64_t tiles = ceil_div(rows, 16);
+  const int64_t wstride = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t tl = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); tl < tiles; tl += wstride) {
+    MlpTile T;
+    float ylo, yhi;
+    const int64_t r0 = tl * 16;
+    mlp_tile_forward(
+        f, [&](int kk, int nt, uint32_t& b0, uint32_t& b1) { b0 = f.w2[kk][nt][0]; b1 = f.w2[kk][nt][1]; }, bias,
+        bias + kH, bias[2 * kH], nm, x, rows, r0, lane, T, ylo, yhi);
+    if ((lane & 3) == 0) {
+      const int64_t ra = r0 + (lane >> 2), rb = ra + 8;
+      if (ra < rows) y[ra] = ylo * nm[2 * kIn + 1] + nm[2 * kIn];
+      if (rb < rows) y[rb] = yhi * nm[2 * kIn + 1] + nm[2 * kIn];
+    }
+  }
+}
+
+// ---- training: loss gradient on tensor cores
+// A block takes 128 rows at a time (16 per warp).  Each warp runs the forward pass of its
+// rows, then the backward pass through the output layer and GELU (dz2 = dy W3 * gelu'(z2))
+// and through W2 (dz1 = (dz2 W2^T) * gelu'(z1), an MMA with W2 as the B operand), and
+// leaves x, h1, dz2 and dz1 as BF16 rows in shared memory.  The block then forms
+// dW2 += h1^T dz2 and dW1 += x^T dz1 as MMAs over the 128 rows (K = rows), each warp owning
+// a fixed set of output tiles whose accumulators stay in registers across iterations; the
+// bias and W3 gradients are column sums in FP32.  Every sum runs in an order fixed by the
+// row count and the grid: the gradient is bit-reproducible.  BF16 operands of every
+// product (x, weights, h1, h2, dz2, dz1), FP32 accumulation.
+constexpr int kGradRows = 128;   // rows per block iteration
+constexpr int kActStride = 72;   // BF16 per shared-memory row of h1, dz2, dz1 (64 + 8 padding)
+constexpr int kXStride = 24;     // BF16 per shared-memory row of x (16 + 8 padding)
+
+struct GradSmem {
+  __nv_bfloat16 w2t[kH * kActStride];  // W2^T[n][k]: B fragments of the forward layer 2
+  __nv_bfloat16 w2[kH * kActStride];   // W2[n][k]: B fragments of dz2 W2^T
+  __nv_bfloat16 h1[kGradRows * kActStride];
+  __nv_bfloat16 d2[kGradRows * kActStride];
+  __nv_bfloat16 d1[kGradRows * kActStride];
+  __nv_bfloat16 xs[kGradRows * kXStride];
+  float colsum[kSpmvWarps][3][kH];  // per warp: sum dz1, sum dz2, sum h2 dy
+  float bias[2 * kH + 1];
+  float w3[kH];
+  float nm[kNorm];
+  double loss[kSpmvWarps];
+  float db3[kSpmvWarps];
+};
+
+__device__ __forceinline__ void ldsm_x4_trans(uint32_t (&r)[4], const void* p) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
+}
+__device__ __forceinline__ void ldsm_x2_trans(uint32_t (&r)[2], const void* p) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(a));
+}
+__device__ __forceinline__ void st_pair(__nv_bfloat16* base, int row, int col, int stride, uint32_t v) {
+  *reinterpret_cast<uint32_t*>(base + row * stride + col) = v;
+}
+
 __global__ void __launch_bounds__(256) k_mlp_grad(const __nv_bfloat16* __restrict__ wb, const float* __restrict__ norm,
                                                  int64_t rows, const float* __restrict__ x,
                                                  const float* __restrict__ target, float* part, double* loss_part) {
-  __shared__ float w[kParams];
-  __shared__ float nm[kNorm];
-  __shared__ float X[kRowsPerGroup][kIn];
-  __shared__ float H1[kRowsPerGroup][kH], G1[kRowsPerGroup][kH];
-  __shared__ float H2[kRowsPerGroup][kH], G2[kRowsPerGroup][kH];
-  __shared__ float DY[kRowsPerGroup];
-  __shared__ double lsh[256];
-  for (int i = threadIdx.x; i < kParams; i += blockDim.x) w[i] = __bfloat162float(wb[i]);
-  if (threadIdx.x < kNorm) nm[threadIdx.x] = norm[threadIdx.x];
-  const int t = threadIdx.x;
-  const int r = t / 16, p = t % 16;  // row in the group, part of the row
-  // thread-owned gradient entries: dW2 entries t, t + 256, ... (16), dW1 entries t, t + 256,
-  // b1/b2/W3 entry t (t < 64), b3 (t == 0)
-  float gW2[16], gW1[2], gB1 = 0.f, gB2 = 0.f, gW3 = 0.f, gB3 = 0.f;
-#pragma unroll
-  for (int q = 0; q < 16; ++q) gW2[q] = 0.f;
-  gW1[0] = gW1[1] = 0.f;
-  double loss = 0.0;
-  const float inv_b = 1.f / (float)rows;
-  __syncthreads();
-  const int64_t groups = ceil_div(rows, kRowsPerGroup);
-  for (int64_t gidx = blockIdx.x; gidx < groups; gidx += gridDim.x) {
-    const int64_t row = gidx * kRowsPerGroup + r;
-    const bool valid = row < rows;
-    if (p < kIn) X[r][p] = valid ? bf16r((x[row * kIn + p] - nm[p]) / nm[kIn + p]) : 0.f;
-    __syncthreads();
-    for (int j = p * 4; j < p * 4 + 4; ++j) {
-      float z = w[kOffB1 + j];
-#pragma unroll
-      for (int i = 0; i < kIn; ++i) z = fmaf(w[kOffW1 + i * kH + j], X[r][i], z);
-      H1[r][j] = gelu(z);
-      G1[r][j] = gelu_grad(z);
-    }
-    __syncthreads();
-    float ypart = 0.f;
-    for (int k = p * 4; k < p * 4 + 4; ++k) {
-      float z = w[kOffB2 + k];
-      for (int j = 0; j < kH; ++j) z = fmaf(w[kOffW2 + j * kH + k], H1[r][j], z);
-      const float h = gelu(z);
-      H2[r][k] = h;
-      G2[r][k] = gelu_grad(z);
-      ypart = fmaf(w[kOffW3 + k], h, ypart);
-    }
-#pragma unroll
-    for (int o = 8; o > 0; o >>= 1) ypart += __shfl_xor_sync(0xffffffffu, ypart, o);  // 16 threads of the row
-    if (p == 0) {
-      const float yhat = ypart + w[kOffB3];
-      const float tn = valid ? (target[row] - nm[2 * kIn]) / nm[2 * kIn + 1] : yhat;
-      const float e = yhat - tn;
-      DY[r] = valid ? 2.f * e * inv_b : 0.f;
-      loss += valid ? (double)e * (double)e : 0.0;
-    }
-    __syncthreads();
-    for (int k = p * 4; k < p * 4 + 4; ++k) G2[r][k] *= w[kOffW3 + k] * DY[r];  // -> dL/dz2
-    __syncthreads();
-    for (int j = p * 4; j < p * 4 + 4; ++j) {
-      float acc = 0.f;
-      for (int k = 0; k < kH; ++k) acc = fmaf(w[kOffW2 + j * kH + k], G2[r][k], acc);
-      G1[r][j] *= acc;  // -> dL/dz1
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < 16; ++q) {  // dW2[j][k] = sum_r h1[r][j] dz2[r][k]
-      const int e = t + 256 * q, j = e / kH, k = e % kH;
-      float acc = 0.f;
-#pragma unroll
-      for (int rr = 0; rr < kRowsPerGroup; ++rr) acc = fmaf(H1[rr][j], G2[rr][k], acc);
-      gW2[q] += acc;
-    }
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {  // dW1[i][j] = sum_r x[r][i] dz1[r][j]
-      const int e = t + 256 * q, i = e / kH, j = e % kH;
-      float acc = 0.f;
-#pragma unroll
-      for (int rr = 0; rr < kRowsPerGroup; ++rr) acc = fmaf(X[rr][i], G1[rr][j], acc);
-      gW1[q] += acc;
-    }
-    if (t < kH) {
-      float a1 = 0.f, a2 = 0.f, a3 = 0.f;
-      for (int rr = 0; rr < kRowsPerGroup; ++rr) {
-        a1 += G1[rr][t];
-        a2 += G2[rr][t];
-        a3 = fmaf(H2[rr][t], DY[rr], a3);
-      }
-      gB1 += a1;
-      gB2 += a2;
-      gW3 += a3;
-    }
-    if (t == 0) {
-      float a = 0.f;
-      for (int rr = 0; rr < kRowsPerGroup; ++rr) a += DY[rr];
-      gB3 += a;
-    }
-    __syncthreads();
+  extern __shared__ __align__(16) unsigned char grad_dyn[];
+  GradSmem& S = *reinterpret_cast<GradSmem*>(grad_dyn);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  for (int i = threadIdx.x; i < kH * kH; i += blockDim.x) {
+    const int n = i / kH, k = i % kH;
+    S.w2[n * kActStride + k] = wb[kOffW2 + n * kH + k];
+    S.w2t[k * kActStride + n] = wb[kOffW2 + n * kH + k];
   }
+  for (int i = threadIdx.x; i < kH; i += blockDim.x) {
+    S.bias[i] = __bfloat162float(wb[kOffB1 + i]);
+    S.bias[kH + i] = __bfloat162float(wb[kOffB2 + i]);
+    S.w3[i] = __bfloat162float(wb[kOffW3 + i]);
+  }
+  if (threadIdx.x == 0) S.bias[2 * kH] = __bfloat162float(wb[kOffB3]);
+  if (threadIdx.x < kNorm) S.nm[threadIdx.x] = norm[threadIdx.x];
+  for (int i = threadIdx.x; i < kSpmvWarps * 3 * kH; i += blockDim.x) (&S.colsum[0][0][0])[i] = 0.f;
+  __syncthreads();
+  MlpFrags f;  // W1 and W3 fragments (W2 comes from shared memory)
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt)
+    f.w1[nt] = pack_raw(wb[kOffW1 + (2 * t) * kH + 8 * nt + g], wb[kOffW1 + (2 * t + 1) * kH + 8 * nt + g]);
+#pragma unroll
+  for (int kk = 0; kk < 4; ++kk) {
+    const int k0 = 16 * kk + 2 * t;
+    f.w3[kk][0] = g == 0 ? pack_raw(wb[kOffW3 + k0], wb[kOffW3 + k0 + 1]) : 0u;
+    f.w3[kk][1] = g == 0 ? pack_raw(wb[kOffW3 + k0 + 8], wb[kOffW3 + k0 + 9]) : 0u;
+  }
+  auto w2t_frag = [&](int kk, int nt, uint32_t& b0, uint32_t& b1) {
+    const __nv_bfloat16* p = S.w2t + (8 * nt + g) * kActStride + 16 * kk + 2 * t;
+    b0 = *reinterpret_cast<const uint32_t*>(p);
+    b1 = *reinterpret_cast<const uint32_t*>(p + 8);
+  };
+  // output tiles owned by this warp: dW2 rows (h1 units) 16*(warp/2).., columns 32*(warp%2)..
+  // (four 8-column tiles); dW1 columns 8*warp..
+  const int mt2 = warp >> 1, nt2 = (warp & 1) * 4;
+  float acc2[4][4], acc1[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    acc1[q] = 0.f;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc2[q][c] = 0.f;
+  }
+  double loss = 0.0;
+  float db3 = 0.f;
+  const float inv_b = 1.f / (float)rows;
+  const float tmean = S.nm[2 * kIn], tstd = S.nm[2 * kIn + 1];
+  const int64_t iters = ceil_div(rows, kGradRows);
+  for (int64_t it = blockIdx.x; it < iters; it += gridDim.x) {
+    const int64_t r0 = it * kGradRows + warp * 16;
+    MlpTile T;
+    float ylo, yhi;
+    mlp_tile_forward(f, w2t_frag, S.bias, S.bias + kH, S.bias[2 * kH], S.nm, x, rows, r0, lane, T, ylo, yhi);
+    // dy of rows g and g + 8 (computed in the lane holding the prediction, t == 0)
+    float dya = 0.f, dyb = 0.f;
+    if (t == 0) {
+      const int64_t ra = r0 + g, rb = ra + 8;
+      if (ra < rows) {
+        const float e = ylo - (target[ra] - tmean) / tstd;
+        dya = 2.f * e * inv_b;
+        loss += (double)e * (double)e;
+      }
+      if (rb < rows) {
+        const float e = yhi - (target[rb] - tmean) / tstd;
+        dyb = 2.f * e * inv_b;
+        loss += (double)e * (double)e;
+      }
+      db3 += dya + dyb;
+    }
+    dya = __shfl_sync(0xffffffffu, dya, lane & ~3);
+    dyb = __shfl_sync(0xffffffffu, dyb, lane & ~3);
+    // dz2 = dy W3 gelu'(z2) (FP32, C layout), then its BF16 A fragments
+    float dz2[8][4];
+    float* cs = &S.colsum[warp][0][0];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      const int c0 = 8 * nt + 2 * t;
+      const float wa = S.w3[c0], wbv = S.w3[c0 + 1];
+      dz2[nt][0] = dya * wa * gelu_grad(T.z2[nt][0]);
+      dz2[nt][1] = dya * wbv * gelu_grad(T.z2[nt][1]);
+      dz2[nt][2] = dyb * wa * gelu_grad(T.z2[nt][2]);
+      dz2[nt][3] = dyb * wbv * gelu_grad(T.z2[nt][3]);
+    }
+    uint32_t D2[4][4];
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+      D2[kk][0] = pack_bf16(dz2[2 * kk][0], dz2[2 * kk][1]);
+      D2[kk][1] = pack_bf16(dz2[2 * kk][2], dz2[2 * kk][3]);
+      D2[kk][2] = pack_bf16(dz2[2 * kk + 1][0], dz2[2 * kk + 1][1]);
+      D2[kk][3] = pack_bf16(dz2[2 * kk + 1][2], dz2[2 * kk + 1][3]);
+    }
+    // dz1 = (dz2 W2^T) gelu'(z1): B[k][n] = W2[n][k]
+    float dz1[8][4];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      dz1[nt][0] = dz1[nt][1] = dz1[nt][2] = dz1[nt][3] = 0.f;
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        const __nv_bfloat16* p = S.w2 + (8 * nt + g) * kActStride + 16 * kk + 2 * t;
+        mma_bf16(dz1[nt], D2[kk], *reinterpret_cast<const uint32_t*>(p), *reinterpret_cast<const uint32_t*>(p + 8));
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) dz1[nt][c] *= gelu_grad(T.z1[nt][c]);
+    }
+    // column sums of this warp's 16 rows: dz1, dz2 (FP32) and h2 dy (h2 as the BF16 operand)
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      const uint32_t hp0 = T.h2[nt >> 1][(nt & 1) * 2], hp1 = T.h2[nt >> 1][(nt & 1) * 2 + 1];
+      const float h2a0 = __uint_as_float(hp0 << 16), h2a1 = __uint_as_float(hp0 & 0xFFFF0000u);
+      const float h2b0 = __uint_as_float(hp1 << 16), h2b1 = __uint_as_float(hp1 & 0xFFFF0000u);
+      float v[3][2] = {{dz1[nt][0] + dz1[nt][2], dz1[nt][1] + dz1[nt][3]},
+                       {dz2[nt][0] + dz2[nt][2], dz2[nt][1] + dz2[nt][3]},
+                       {h2a0 * dya + h2b0 * dyb, h2a1 * dya + h2b1 * dyb}};
+#pragma unroll
+      for (int q = 0; q < 3; ++q)
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+          for (int o = 4; o < 32; o <<= 1) v[q][c] += __shfl_xor_sync(0xffffffffu, v[q][c], o);
+      if (g == 0) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          cs[q * kH + 8 * nt + 2 * t] += v[q][0];
+          cs[q * kH + 8 * nt + 2 * t + 1] += v[q][1];
+        }
+      }
+    }
+    // BF16 rows of x, h1, dz2, dz1 for the block's weight-gradient products
+    const int rw = warp * 16;
+    st_pair(S.xs, rw + g, 2 * t, kXStride, T.x[0]);
+    st_pair(S.xs, rw + g + 8, 2 * t, kXStride, T.x[1]);
+    st_pair(S.xs, rw + g, 8 + 2 * t, kXStride, 0u);
+    st_pair(S.xs, rw + g + 8, 8 + 2 * t, kXStride, 0u);
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+      st_pair(S.h1, rw + g, 16 * kk + 2 * t, kActStride, T.h1[kk][0]);
+      st_pair(S.h1, rw + g + 8, 16 * kk + 2 * t, kActStride, T.h1[kk][1]);
+      st_pair(S.h1, rw + g, 16 * kk + 8 + 2 * t, kActStride, T.h1[kk][2]);
+      st_pair(S.h1, rw + g + 8, 16 * kk + 8 + 2 * t, kActStride, T.h1[kk][3]);
+      st_pair(S.d2, rw + g, 16 * kk + 2 * t, kActStride, D2[kk][0]);
+      st_pair(S.d2, rw + g + 8, 16 * kk + 2 * t, kActStride, D2[kk][1]);
+      st_pair(S.d2, rw + g, 16 * kk + 8 + 2 * t, kActStride, D2[kk][2]);
+      st_pair(S.d2, rw + g + 8, 16 * kk + 8 + 2 * t, kActStride, D2[kk][3]);
+    }
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      st_pair(S.d1, rw + g, 8 * nt + 2 * t, kActStride, pack_bf16(dz1[nt][0], dz1[nt][1]));
+      st_pair(S.d1, rw + g + 8, 8 * nt + 2 * t, kActStride, pack_bf16(dz1[nt][2], dz1[nt][3]));
+    }
+    __syncthreads();
+    // dW2 += h1^T dz2 and dW1 += x^T dz1 over the block's 128 rows (K = rows, 8 steps of 16)
+    const int q = lane >> 3, i8 = lane & 7;  // ldmatrix: matrix q, row i8 of it
+#pragma unroll 2
+    for (int ks = 0; ks < kGradRows / 16; ++ks) {
+      const int rA = 16 * ks + ((q & 2) ? 8 : 0) + i8;  // A = h1^T: matrices (rows, cols) of h1
+      uint32_t a[4];
+      ldsm_x4_trans(a, S.h1 + rA * kActStride + 16 * mt2 + ((q & 1) ? 8 : 0));
+      // B = dz2 rows 16ks.., two column tiles per x4
+#pragma unroll
+      for (int p2 = 0; p2 < 2; ++p2) {
+        uint32_t b[4];
+        const int rB = 16 * ks + ((q & 1) ? 8 : 0) + i8;
+        ldsm_x4_trans(b, S.d2 + rB * kActStride + 8 * (nt2 + 2 * p2 + (q >> 1)));
+        mma_bf16(acc2[2 * p2], a, b[0], b[1]);
+        mma_bf16(acc2[2 * p2 + 1], a, b[2], b[3]);
+      }
+      uint32_t ax[4];
+      ldsm_x4_trans(ax, S.xs + rA * kXStride + ((q & 1) ? 8 : 0));
+      uint32_t bx[2];
+      const int rX = 16 * ks + ((lane >> 3) & 1 ? 8 : 0) + i8;
+      ldsm_x2_trans(bx, S.d1 + rX * kActStride + 8 * warp);
+      mma_bf16(acc1, ax, bx[0], bx[1]);
+    }
+    __syncthreads();  // the rows are rewritten by the next iteration
+  }
+  // this block's partial gradient
   float* o = part + (int64_t)blockIdx.x * kParams;
 #pragma unroll
-  for (int q = 0; q < 16; ++q) o[kOffW2 + t + 256 * q] = gW2[q];
-  o[kOffW1 + t] = gW1[0];
-  o[kOffW1 + t + 256] = gW1[1];
-  if (t < kH) {
-    o[kOffB1 + t] = gB1;
-    o[kOffB2 + t] = gB2;
-    o[kOffW3 + t] = gW3;
+  for (int p = 0; p < 4; ++p) {
+    const int col = 8 * (nt2 + p) + 2 * t, row = 16 * mt2 + g;
+    o[kOffW2 + row * kH + col] = acc2[p][0];
+    o[kOffW2 + row * kH + col + 1] = acc2[p][1];
+    o[kOffW2 + (row + 8) * kH + col] = acc2[p][2];
+    o[kOffW2 + (row + 8) * kH + col + 1] = acc2[p][3];
   }
-  if (t == 0) o[kOffB3] = gB3;
-  lsh[t] = loss;
-  __syncthreads();
+  {
+    const int col = 8 * warp + 2 * t;  // dW1 rows g < 8 are the inputs; rows 8..15 are padding
+    o[kOffW1 + g * kH + col] = acc1[0];
+    o[kOffW1 + g * kH + col + 1] = acc1[1];
+  }
   if (t == 0) {
-    double s = 0.0;
-    for (int i = 0; i < 256; ++i) s += lsh[i];
-    loss_part[blockIdx.x] = s;
+    S.loss[warp] = loss;  // lanes with t == 0 hold partial losses; sum them in lane order
+  }
+  __syncwarp();
+  double lw = loss;
+  for (int o2 = 16; o2 > 0; o2 >>= 1) lw += __shfl_xor_sync(0xffffffffu, lw, o2);
+  float dw = db3;
+  for (int o2 = 16; o2 > 0; o2 >>= 1) dw += __shfl_xor_sync(0xffffffffu, dw, o2);
+  if (lane == 0) {
+    S.loss[warp] = lw;
+    S.db3[warp] = dw;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < 3 * kH; j += blockDim.x) {
+    float a = 0.f;
+    for (int w = 0; w < kSpmvWarps; ++w) a += (&S.colsum[w][0][0])[j];
+    const int qq = j / kH, c = j % kH;
+    o[(qq == 0 ? kOffB1 : (qq == 1 ? kOffB2 : kOffW3)) + c] = a;
+  }
+  if (threadIdx.x == 0) {
+    double l = 0.0;
+    float b3 = 0.f;
+    for (int w = 0; w < kSpmvWarps; ++w) {
+      l += S.loss[w];
+      b3 += S.db3[w];
+    }
+    o[kOffB3] = b3;
+    loss_part[blockIdx.x] = l;
   }
 }
 
@@ -560,8 +828,13 @@ psi_status psi_mlp_grad(psi_mlp* h, int64_t rows, const float* x, const float* t
   }
   try {
     Mlp& m = h->m;
-    k_mlp_grad<<<m.grid, 256, 0, m.stream>>>(m.wb.get(), m.norm.get(), rows, x, target, m.part.get(),
-                                             m.loss_part.get());
+    static bool configured = false;
+    if (!configured) {
+      PSI_CUDA(cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(GradSmem)));
+      configured = true;
+    }
+    k_mlp_grad<<<m.grid, 256, sizeof(GradSmem), m.stream>>>(m.wb.get(), m.norm.get(), rows, x, target, m.part.get(),
+                                                            m.loss_part.get());
     PSI_LAUNCHED();
     k_mlp_reduce<<<wgrid(kParams), 256, 0, m.stream>>>(m.part.get(), m.grid, m.grad.get(), m.loss_part.get(),
                                                        m.loss.get(), rows);

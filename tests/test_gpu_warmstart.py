@@ -17,29 +17,43 @@ def _model(seed=0):
     return WarmStartModel(seed)
 
 
-def test_forward_and_gradient_match_cpu_reference():
+@pytest.mark.parametrize("rows", [300, 100003])
+def test_forward_and_gradient_match_cpu_reference(rows):
+    """300 rows: a partial tile in one block; 100003 rows: blocks that take several 128-row
+    iterations and keep their gradient tiles across them, and a ragged last tile."""
     import torch
 
     rng = np.random.default_rng(0)
     params = (rng.standard_normal(ref.N_PARAMS) * 0.2).astype(np.float32)
     norm = np.concatenate([rng.normal(0, 1, 8), rng.uniform(0.5, 2, 8), [1.5], [2.0]]).astype(np.float32)
-    x = rng.normal(0, 1.5, (300, 8)).astype(np.float32)
-    t = rng.normal(1.0, 2.0, 300).astype(np.float32)
+    x = rng.normal(0, 1.5, (rows, 8)).astype(np.float32)
+    t = rng.normal(1.0, 2.0, rows).astype(np.float32)
     m = _model()
     m.set_params(params, norm)
     xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+    # Both sides round every product operand (weights, inputs, hidden activations, dz2, dz1)
+    # to BF16, but from sums taken in different precisions (FP32 on the GPU, FP64 here): a
+    # value within ~1e-7 of a BF16 rounding midpoint can round to the neighbouring BF16 on
+    # one side, a one-ulp (2^-8 relative) difference in one activation.  Such flips hit a
+    # few of the 300 x 128 activations at most; rows without one agree to FP32 rounding.
     y = m.forward(xd).cpu().numpy()
-    np.testing.assert_allclose(y, ref.forward(params, norm.astype(np.float64), x), rtol=1e-5, atol=1e-5)
+    y_ref = ref.forward(params, norm.astype(np.float64), x)
+    err = np.abs(y - y_ref)
+    assert np.mean(err > 1e-5 + 1e-5 * np.abs(y_ref)) <= 0.02, np.sort(err)[-8:]
+    assert np.max(err / (1.0 + np.abs(y_ref))) <= 2e-2
     loss, g = m.grad(xd, td, want_grad=True)
     loss_ref, g_ref = ref.loss_and_grad(params, norm.astype(np.float64), x, t)
-    assert abs(loss - loss_ref) <= 1e-5 * loss_ref
-    assert np.linalg.norm(g - g_ref) <= 1e-4 * np.linalg.norm(g_ref)
+    assert abs(loss - loss_ref) <= 1e-3 * loss_ref
+    assert np.linalg.norm(g - g_ref) <= 1e-3 * np.linalg.norm(g_ref)
     # each block of parameters separately (a transposed or dropped block would show here)
     o = 0
     for name, shape in ref.SIZES:
         k = int(np.prod(shape))
-        assert np.linalg.norm(g[o:o + k] - g_ref[o:o + k]) <= 1e-4 * max(np.linalg.norm(g_ref[o:o + k]), 1e-12), name
+        assert np.linalg.norm(g[o:o + k] - g_ref[o:o + k]) <= 2e-3 * max(np.linalg.norm(g_ref[o:o + k]), 1e-12), name
         o += k
+    # against the unrounded network the same gradient is off by the BF16 rounding itself
+    _, g_exact = ref.loss_and_grad(params, norm.astype(np.float64), x, t, bf16_round=False)
+    assert np.linalg.norm(g - g_exact) > np.linalg.norm(g - g_ref)
     m.close()
 
 
