@@ -58,7 +58,8 @@ enum {
   PSI_FP32 = 0,        /* Algorithm 2 literally, iterate stored and summed in FP32;
                           stalls near the FP32 rounding floor for tight eps */
   PSI_FP32_REFINE = 1, /* default: the series of Eq. 13 with FP32 terms summed into an
-                          FP64 iterate, then FP64 residual steps near eps (see psi_solve) */
+                          FP64 iterate, then confirming steps from that iterate near eps (see
+                          psi_solve) */
   PSI_FP64 = 2         /* Algorithm 2 literally in FP64 */
 };
 /* psi_options.tol_mode: scale applied to eps_t before the test of Eq. 16 */
@@ -118,7 +119,7 @@ void psi_options_default(psi_options* opt);
 typedef struct psi_solve_info {
   int32_t iters;          /* power-iteration steps t performed (each yields s_t) */
   int32_t converged;      /* 1 if the scaled gap met eps */
-  int32_t refinements;    /* FP64 residual steps taken (PSI_FP32_REFINE) */
+  int32_t refinements;    /* confirming steps taken (PSI_FP32_REFINE) */
   int32_t spmv_launches;  /* sparse products run (iterations + final psi product) */
   double gap_s_l1;        /* eps_t = ||s_t - s_{t-1}||_1 of the last step */
   double gap_scaled;      /* the value compared with eps (tol_mode, bnorm_mode) */
@@ -128,8 +129,8 @@ typedef struct psi_solve_info {
   double spmv_ms;         /* profile == 1: summed duration of the main-precision steps (FP32
                              series or FP32/FP64 Algorithm 2 steps): sparse product + fix-up */
   int32_t spmv_timed;     /* profile == 1: number of steps in spmv_ms */
-  int32_t refine_timed;   /* profile == 1: number of FP64 refinement steps in refine_ms */
-  double refine_ms;       /* profile == 1: summed duration of the FP64 refinement steps */
+  int32_t refine_timed;   /* profile == 1: number of confirming steps in refine_ms */
+  double refine_ms;       /* profile == 1: summed duration of the confirming steps */
 } psi_solve_info;
 
 typedef struct psi_graph_stats {
@@ -167,9 +168,14 @@ psi_status psi_graph_create(int64_t n, int64_t m, const int32_t* follower, const
  * resume; the fixed point does not change).  Returns OK or NOT_CONVERGED (psi is then
  * computed from the last iterate).  info may be NULL.
  * PSI_FP32_REFINE: the terms c^T A^t of Eq. 13 are formed in FP32 and summed into an
- * FP64 s; when their gap meets eps, one FP64 step s <- s A + c is taken and its gap is
- * the one tested (repeating the FP32 series from its residual if needed), so the
- * returned gap is an FP64 gap of Algorithm 2.
+ * FP64 s; when their gap meets eps, one confirming step s <- s A + c is taken from that s
+ * and its gap is the one tested (repeating the FP32 series from its residual if needed), so
+ * the returned gap is a gap of Algorithm 2 taken at the confirming step's precision.  The
+ * confirming step and the final product sum the gathered values as float pairs (hi + lo
+ * FP32, about 48 significant bits; each pair sum errs by at most ~2^-46 of the magnitudes
+ * summed) and update s and psi in FP64, whenever the target gap eps/scale is at least
+ * 2^-30 * n (true of the default psi tolerance for eps >= 1e-9); tighter targets, such as
+ * an absolute s-tolerance of 1e-9 on millions of users, take FP64 products throughout.
  */
 psi_status psi_solve(psi_graph* g, double eps, int32_t max_iter, const double* init_s,
                      psi_solve_info* info);
@@ -219,7 +225,8 @@ psi_status psi_pagerank(psi_graph* g, double alpha, double eps, int32_t max_iter
  * together.  Each scenario is an independent Power-psi problem (Algorithm 2 with its own
  * A, B, c, d from Sec. II, its own gap, stop test and step count); one sparse product per
  * step serves every scenario, so each column index fetched feeds S values.  Precision is
- * always PSI_FP32_REFINE (FP32 series, FP64 iterate and confirming step, FP64 psi).
+ * always PSI_FP32_REFINE (FP32 series, FP64 iterate, confirming step and final product in
+ * float pairs or FP64 as for psi_solve, FP64 psi).
  */
 typedef struct psi_batch psi_batch; /* opaque; owns all of its device memory */
 
@@ -249,7 +256,7 @@ void psi_batch_destroy(psi_batch* b);
 /* ------------------------------------------------------------------------------------
  * Independent graphs: G follower graphs of their own (own users, N_g, edges, rates), each
  * solved as its own Power-psi problem (Algorithm 2 with its own N_g in psi = (.)/N_g and in
- * the psi tolerance, its own gap, stop test, step count and FP64 confirming step), all in
+ * the psi tolerance, its own gap, stop test, step count and confirming step), all in
  * one object: the graphs are built together as one block-diagonal graph and stepped
  * together, graphs that have met their test skipping their part of each product, from a
  * CUDA graph of captured steps.  Precision is always PSI_FP32_REFINE.

@@ -39,6 +39,25 @@ __device__ __forceinline__ D2 ld_gather(const D2* p, uint64_t pol) {
   asm volatile("ld.global.nc.L2::cache_hint.v2.f64 {%0,%1}, [%2], %3;" : "=d"(x), "=d"(y) : "l"(p), "l"(pol));
   return D2(x, y);
 }
+// Four FP32 sums carried through one product (16-byte gathers).
+struct F4 {
+  float x, y, z, w;
+  F4() = default;
+  __device__ __forceinline__ F4(int v) : x((float)v), y((float)v), z((float)v), w((float)v) {}
+  __device__ __forceinline__ F4(float a, float b, float c, float d) : x(a), y(b), z(c), w(d) {}
+};
+__device__ __forceinline__ F4 operator+(F4 a, F4 b) { return F4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
+__device__ __forceinline__ F4& operator+=(F4& a, F4 b) {
+  a = a + b;
+  return a;
+}
+__device__ __forceinline__ F4 ld_gather(const F4* p, uint64_t pol) {
+  float a, b, c, d;
+  asm volatile("ld.global.nc.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;"
+               : "=f"(a), "=f"(b), "=f"(c), "=f"(d)
+               : "l"(p), "l"(pol));
+  return F4(a, b, c, d);
+}
 template <typename T>
 __device__ __forceinline__ T shfl_up_t(T v, int o) { return __shfl_up_sync(0xffffffffu, v, o); }
 template <>
@@ -68,6 +87,11 @@ template <>
 __device__ __forceinline__ DF2 shfl_xor_t<DF2>(DF2 v, int o) {
   return DF2(shfl_xor_t(v.a, o), shfl_xor_t(v.b, o));
 }
+template <>
+__device__ __forceinline__ F4 shfl_up_t<F4>(F4 v, int o) {
+  return F4(__shfl_up_sync(0xffffffffu, v.x, o), __shfl_up_sync(0xffffffffu, v.y, o),
+            __shfl_up_sync(0xffffffffu, v.z, o), __shfl_up_sync(0xffffffffu, v.w, o));
+}
 template <typename T>
 __device__ __forceinline__ T shfl_idx_t(T v, int src) { return __shfl_sync(0xffffffffu, v, src); }
 template <>
@@ -81,6 +105,11 @@ __device__ __forceinline__ DF shfl_idx_t<DF>(DF v, int src) {
 template <>
 __device__ __forceinline__ DF2 shfl_idx_t<DF2>(DF2 v, int src) {
   return DF2(shfl_idx_t(v.a, src), shfl_idx_t(v.b, src));
+}
+template <>
+__device__ __forceinline__ F4 shfl_idx_t<F4>(F4 v, int src) {
+  return F4(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src),
+            __shfl_sync(0xffffffffu, v.z, src), __shfl_sync(0xffffffffu, v.w, src));
 }
 
 // ------------------------------------------------------------------ epilogues

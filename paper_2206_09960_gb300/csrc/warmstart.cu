@@ -65,29 +65,27 @@ __global__ void k_base_features(const int32_t* __restrict__ row_ptr, int32_t n_r
   }
 }
 
-__global__ void k_features_to_u(const float* __restrict__ x, int32_t nX, int32_t nR, int64_t nu, D2* f01, D2* f23) {
+// the four base features of every gathered user (X then U), zero at the pad entry
+__global__ void k_features_to_u(const float* __restrict__ x, int32_t nX, int32_t nR, int64_t nu, F4* f) {
   WGRID_STRIDE(i, nu + 1) {
     if (i == nu) {
-      f01[i] = D2(0.0, 0.0);
-      f23[i] = D2(0.0, 0.0);
+      f[i] = F4(0);
     } else {
       const int64_t user = i < nX ? i : i + nR;
-      const float* o = x + user * kIn;
-      f01[i] = D2((double)o[0], (double)o[1]);
-      f23[i] = D2((double)o[2], (double)o[3]);
+      const float4 o = *reinterpret_cast<const float4*>(x + user * kIn);
+      f[i] = F4(o.x, o.y, o.z, o.w);
     }
   }
 }
 
-// mean over the followers of row r of a pair of base features, into columns c0, c0 + 1
-struct EpiMean2 {
+
+// mean over the followers of row r of the four base features, into columns 4..7
+struct EpiMean4 {
   const int32_t* row_ptr;
   float* x;
-  int c0;
-  __device__ __forceinline__ void row(int32_t r, D2 y, double&, uint64_t, uint64_t) const {
-    const double len = (double)(row_ptr[r + 1] - row_ptr[r]);
-    x[(int64_t)r * kIn + c0] = (float)(y.a / len);
-    x[(int64_t)r * kIn + c0 + 1] = (float)(y.b / len);
+  __device__ __forceinline__ void row(int32_t r, F4 y, double&, uint64_t, uint64_t) const {
+    const float inv = 1.f / (float)(row_ptr[r + 1] - row_ptr[r]);
+    *reinterpret_cast<float4*>(x + (int64_t)r * kIn + 4) = make_float4(y.x * inv, y.y * inv, y.z * inv, y.w * inv);
   }
 };
 
@@ -574,7 +572,8 @@ __global__ void k_warm_s0(const float* __restrict__ yhat, const float* __restric
 
 // ---------------------------------------------------------------- host side
 
-// [n][8] features, internal order, into x (device)
+// [n][8] features, internal order, into x (device): the four base features, then their
+// means over each user's followers in one load-balanced product with four FP32 sums
 void compute_features(Graph& g, float* x) {
   cudaStream_t s = g.stream;
   Allocator& al = g.al;
@@ -584,52 +583,46 @@ void compute_features(Graph& g, float* x) {
                                            n, x);
   PSI_LAUNCHED();
   if (g.num_tiles == 0) return;
-  DBuf<D2> f01(al, (size_t)nu + 1), f23(al, (size_t)nu + 1);
-  k_features_to_u<<<wgrid(nu + 1), 256, 0, s>>>(x, g.nX, g.nR, nu, f01.get(), f23.get());
+  DBuf<F4> f(al, (size_t)nu + 1);
+  k_features_to_u<<<wgrid(nu + 1), 256, 0, s>>>(x, g.nX, g.nR, nu, f.get());
   PSI_LAUNCHED();
-  Schedule sc;  // view of the graph's own schedule
-  sc.tiles = g.num_tiles;
-  sc.num_fix = g.num_fix;
   DBuf<DevState> st(al, 1);
   PSI_CUDA(cudaMemsetAsync(st.get(), 0, sizeof(DevState), s));
   int per_sm = 0;
-  PSI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmv<D2, EpiMean2>, kSpmvThreads, 0));
+  PSI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmv<F4, EpiMean4>, kSpmvThreads, 0));
   const int grid = spmv_blocks(per_sm, g.num_tiles);
   DBuf<double> gap_part(al, (size_t)grid);
-  DBuf<D2> ch(al, (size_t)g.num_tiles), ct(al, (size_t)g.num_tiles);
-  for (int c0 = 4; c0 <= 6; c0 += 2) {
-    const D2* u = c0 == 4 ? f01.get() : f23.get();
-    EpiMean2 epi{g.row_ptr.get(), x, c0};
-    SpmvArgs a{};
-    a.row_ptr = g.row_ptr.get();
-    a.col = g.col.get();
-    a.tile_row = g.tile_row.get();
-    a.tile = g.tile;
-    a.num_tiles = g.num_tiles;
-    a.n_rows = g.n_rows;
-    a.m = g.m_unique;
-    a.state = st.get();
-    a.gap_part = gap_part.get();
-    a.carry_head = ch.get();
-    a.carry_tail = ct.get();
-    k_spmv<D2, EpiMean2><<<grid, kSpmvThreads, 0, s>>>(a, u, epi);
+  DBuf<F4> ch(al, (size_t)g.num_tiles), ct(al, (size_t)g.num_tiles);
+  EpiMean4 epi{g.row_ptr.get(), x};
+  SpmvArgs a{};
+  a.row_ptr = g.row_ptr.get();
+  a.col = g.col.get();
+  a.tile_row = g.tile_row.get();
+  a.tile = g.tile;
+  a.num_tiles = g.num_tiles;
+  a.n_rows = g.n_rows;
+  a.m = g.m_unique;
+  a.state = st.get();
+  a.gap_part = gap_part.get();
+  a.carry_head = ch.get();
+  a.carry_tail = ct.get();
+  k_spmv<F4, EpiMean4><<<grid, kSpmvThreads, 0, s>>>(a, f.get(), epi);
+  PSI_LAUNCHED();
+  if (g.num_fix > 0) {
+    int fgrid = fix_blocks(g.num_fix);
+    DBuf<double> gap_fix(al, (size_t)fgrid);
+    FixArgs fa{};
+    fa.row_ptr = g.row_ptr.get();
+    fa.tile_row = g.tile_row.get();
+    fa.tile = g.tile;
+    fa.fix_tile = g.fix_tile.get();
+    fa.num_fix = g.num_fix;
+    fa.state = st.get();
+    fa.gap_fix = gap_fix.get();
+    fa.carry_head = ch.get();
+    fa.carry_tail = ct.get();
+    k_fixup<F4, EpiMean4><<<fgrid, kFixThreads, 0, s>>>(fa, epi);
     PSI_LAUNCHED();
-    if (g.num_fix > 0) {
-      int fgrid = fix_blocks(g.num_fix);
-      DBuf<double> gap_fix(al, (size_t)fgrid);
-      FixArgs f{};
-      f.row_ptr = g.row_ptr.get();
-      f.tile_row = g.tile_row.get();
-      f.tile = g.tile;
-      f.fix_tile = g.fix_tile.get();
-      f.num_fix = g.num_fix;
-      f.state = st.get();
-      f.gap_fix = gap_fix.get();
-      f.carry_head = ch.get();
-      f.carry_tail = ct.get();
-      k_fixup<D2, EpiMean2><<<fgrid, kFixThreads, 0, s>>>(f, epi);
-      PSI_LAUNCHED();
-    }
   }
 }
 
