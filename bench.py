@@ -326,8 +326,8 @@ def run_batch(args, S=64, plain_sample=8):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / 1e3 / reps, outs[-1]
 
-    def batched():
-        with psi.Batch(n, f_d, l_d, lam_d, mu_d, stream=stream) as b:
+    def batched(profile=False):
+        with psi.Batch(n, f_d, l_d, lam_d, mu_d, stream=stream, profile=profile) as b:
             status, infos = b.solve(args.eps, 100000)
             st = b.stats()
         return status, infos, st
@@ -339,8 +339,22 @@ def run_batch(args, S=64, plain_sample=8):
                 infos.append(g.solve(args.eps, 100000))
         return infos
 
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
     t_batch, (status, infos, st) = timed(batched, args.steps)
+    clk = clocks.stop()
+    _, pinfo, _ = batched(profile=True)
     t_plain, pinfos = timed(plain, 1)
+    # series product of the batch: 4 B per nonzero, the compulsory read of every gathered
+    # user's 64-value row, and per row mu, 1/sigma, s (read and write) and the new term for
+    # each scenario
+    step_ms = pinfo[0]["spmv_ms"] / max(pinfo[0]["spmv_timed"], 1)
+    alg = 4 * st["m_unique"] + 4 * (st["n_rows"] + 1) + 4 * S * st["n_gathered"] + 28 * S * st["n_rows"]
+    peak, peak_kind = measured_peaks()
+    roofline = {"bound": "hbm", "achieved": alg / step_ms / 1e6, "peak": peak, "unit": "GB/s",
+                "frac": alg / step_ms / 1e6 / peak, "traffic": None, "peak_kind": peak_kind,
+                "kernel": "k_spmm<float2,EpiSeriesS> + fix-up (batched FP32 series step)",
+                "alg_bytes_per_launch": alg, "avg_launch_ms": step_ms, "launches_timed": pinfo[0]["spmv_timed"]}
     t_plain_all = t_plain * S / plain_sample
     solve_batch = infos[0]["ms"] / 1e3
     solve_plain = sum(i["ms"] for i in pinfos) / 1e3 * S / plain_sample
@@ -353,8 +367,22 @@ def run_batch(args, S=64, plain_sample=8):
             "iters_mean": sum(i["iters"] for i in infos) / S,
             "batch_solve_s": solve_batch, "plain_s_for_64": t_plain_all, "plain_solve_s_for_64": solve_plain,
             "speedup_total": t_plain_all / t_batch, "speedup_solve": solve_plain / solve_batch,
-            "plain_sample": plain_sample}
+            "plain_sample": plain_sample, "clocks": clk, "roofline": roofline}
     print(json.dumps(line), flush=True)
+
+
+def multi_roofline(st, solve_s, iters):
+    """Whole-solve roofline of the independent-graph object: every step reads each graph's
+    column indices and per-user vectors once (4M + 32N per step while the graph steps,
+    averaged over the graphs' step counts), divided by the solve time; the replayed CUDA
+    graphs leave no per-launch timing."""
+    peak, peak_kind = measured_peaks()
+    mean_steps = sum(iters) / len(iters)
+    alg = (4 * st["m_unique"] + 32 * st["n"]) * mean_steps
+    return {"bound": "hbm", "achieved": alg / solve_s / 1e9, "peak": peak, "unit": "GB/s",
+            "frac": alg / solve_s / 1e9 / peak, "traffic": None, "peak_kind": peak_kind,
+            "kernel": "whole solve (series products, confirming steps, stop tests, final product)",
+            "alg_bytes_per_solve": alg, "solve_ms": solve_s * 1e3}
 
 
 def run_multi(args, G=256, plain_sample=32):
@@ -406,7 +434,10 @@ def run_multi(args, G=256, plain_sample=32):
         return infos
 
     launches0 = psi._binding.load().psi_kernel_launches()
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
     t_multi, (status, infos, st) = timed(together, args.steps)
+    clk = clocks.stop()
     if args.profile_solve:  # one more solve of the built object inside a profiler range (for ncu)
         with psi.Multi(n_g, m_g, *dev, stream=stream) as mg:
             mg.solve(args.eps, 100000)
@@ -430,7 +461,8 @@ def run_multi(args, G=256, plain_sample=32):
             "status": status, "iters_min": min(iters), "iters_max": max(iters), "iters_mean": sum(iters) / G,
             "multi_solve_s": solve_multi, "plain_s_for_256": t_plain_all, "plain_solve_s_for_256": solve_plain,
             "speedup_total": t_plain_all / t_multi, "speedup_solve": solve_plain / solve_multi,
-            "plain_sample": len(sample), "gpu_launches": launches, "build_ms": st["build_ms"]}
+            "plain_sample": len(sample), "gpu_launches": launches, "build_ms": st["build_ms"], "clocks": clk,
+            "roofline": multi_roofline(st, solve_multi, iters)}
     print(json.dumps(line), flush=True)
 
 
@@ -468,14 +500,26 @@ def run_pagerank(args, alpha=0.85, eps=1e-9):
         return sum(ts) / len(ts), res
 
     out = {}
-    with psi.Graph(n, dev[0], dev[1], dev[2], dev[3], tol_mode="s_abs", stream=stream) as g:
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    with psi.Graph(n, dev[0], dev[1], dev[2], dev[3], tol_mode="s_abs", stream=stream, profile=True) as g:
         out["psi_heterogeneous"] = timed(lambda: g.solve(eps, 100000))
         out["pagerank"] = timed(lambda: g.pagerank(alpha, eps, 100000)[1])
+        st = g.stats()
     with psi.Graph(n, dev[0], dev[1], hom[0], hom[1], tol_mode="s_abs", stream=stream) as g:
         out["psi_homogeneous"] = timed(lambda: g.solve(eps, 100000))
         psi_h = g.scores()
         pi, _ = g.pagerank(alpha, eps, 100000)
         diff = float((psi_h - pi).abs().sum() / pi.abs().sum())
+    clk = clocks.stop()
+    pinfo = out["pagerank"][1]
+    step_ms = pinfo["spmv_ms"] / max(pinfo["spmv_timed"], 1)
+    alg = 4 * st["m_unique"] + 32 * n
+    peak, peak_kind = measured_peaks()
+    roofline = {"bound": "hbm", "achieved": alg / step_ms / 1e6, "peak": peak, "unit": "GB/s",
+                "frac": alg / step_ms / 1e6 / peak, "traffic": None, "peak_kind": peak_kind,
+                "kernel": "k_spmv<float,EpiSeries> + k_fixup (PageRank step of Eq. 22 in series form)",
+                "alg_bytes_per_launch": alg, "avg_launch_ms": step_ms, "launches_timed": pinfo["spmv_timed"]}
     line = {"metric": "Table IV comparison: solve time of PageRank (Eq. 22) and Power-psi at eps=1e-9",
             "value": out["psi_heterogeneous"][0], "unit": "s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "higher_is_better": False, "dtype": "f32", "data": "synthetic",
@@ -486,7 +530,7 @@ def run_pagerank(args, alpha=0.85, eps=1e-9):
             "pagerank_s": out["pagerank"][0], "pagerank_iters": out["pagerank"][1]["iters"],
             "psi_homogeneous_s": out["psi_homogeneous"][0],
             "psi_homogeneous_iters": out["psi_homogeneous"][1]["iters"],
-            "homogeneous_psi_vs_pagerank_rel_l1": diff}
+            "homogeneous_psi_vs_pagerank_rel_l1": diff, "clocks": clk, "roofline": roofline}
     print(json.dumps(line), flush=True)
 
 
@@ -519,7 +563,10 @@ def run_warmstart(args, n_train=200, eval_scale=23, train_steps=1500):
     args_d = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (w["follower"], w["leader"], w["lam"], w["mu"])]
     stream = torch.cuda.current_stream()
     res = {}
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
     with psi.Graph(w["n"], *args_d, stream=stream) as g:
+        n_rows = g.stats()["n_rows"]
         for name in ("cold", "warm"):
             ts, its = [], []
             for rep in range(args.warmup + args.steps):
@@ -536,7 +583,34 @@ def run_warmstart(args, n_train=200, eval_scale=23, train_steps=1500):
         psi_warm = g.scores().cpu().numpy()
         g.solve(args.eps, 100000)
         psi_cold = g.scores().cpu().numpy()
+    clk = clocks.stop()
     rel = float(np.abs(psi_warm - psi_cold).sum() / np.abs(psi_cold).sum())
+    # the network on tensor cores: one forward pass over the held-out graph's rows and one
+    # gradient over a training batch, each timed with CUDA events
+    xr = torch.randn(n_rows, 8, device="cuda")
+    tr = torch.randn(1 << 16, device="cuda")
+
+    def ev_time(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / reps
+
+    fwd_s = ev_time(lambda: model.forward(xr))
+    grad_s = ev_time(lambda: model.grad(xr[: 1 << 16], tr))
+    flop_row = 2 * (8 * 64 + 64 * 64 + 64)  # multiply-adds of the three layers, x2
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+        bf16_peak = float(json.load(fh).get("bf16_tflops", 1900.0))
+    net = {"bound": "tensor", "achieved": n_rows * flop_row / fwd_s / 1e12, "peak": bf16_peak, "unit": "TFLOP/s",
+           "frac": n_rows * flop_row / fwd_s / 1e12 / bf16_peak, "traffic": None, "peak_kind": "measured",
+           "kernel": "k_mlp_forward (mma.sync m16n8k16 BF16, FP32 accumulate)", "rows": n_rows,
+           "forward_ms": fwd_s * 1e3, "grad_ms_65536_rows": grad_s * 1e3,
+           "grad_tflops": 3 * (1 << 16) * flop_row / grad_s / 1e12}
     line = {"metric": "warm start: Power-psi time and steps to L1<1e-8 from the network's s_0 vs s_0 = c",
             "value": res["warm"][0], "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": False, "dtype": "f32", "data": "synthetic",
@@ -545,7 +619,8 @@ def run_warmstart(args, n_train=200, eval_scale=23, train_steps=1500):
             "cold_s": res["cold"][0], "cold_iters": res["cold"][1], "warm_s": res["warm"][0],
             "warm_iters": res["warm"][1], "converged": [res["cold"][2], res["warm"][2]],
             "psi_rel_l1_warm_vs_cold": rel, "loss_first": float(np.mean(losses[:10])),
-            "loss_last": float(np.mean(losses[-50:])), "data_s": t_data, "train_s": t_train}
+            "loss_last": float(np.mean(losses[-50:])), "data_s": t_data, "train_s": t_train, "clocks": clk,
+            "roofline": net}
     print(json.dumps(line), flush=True)
 
 
@@ -573,6 +648,9 @@ def main():
                     help="multi workload: run one extra solve between cudaProfilerStart/Stop (ncu --profile-from-start off)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", action="store_true", help="skip the oracle parity check after the timed steps")
+    ap.add_argument("--spmv-tile", type=int, default=0, help="fix the product's tile (0: autotuner / rule)")
+    ap.add_argument("--spmv-hot", type=int, default=-1,
+                    help="fix the series product's shared-memory copy (-1: autotuner's choice)")
     ap.add_argument("--workload", default="rmat", choices=["rmat", "batch", "warmstart", "multi", "pagerank"],
                     help="rmat: the single-graph step (default); batch: 64 activity scenarios on one graph; "
                          "warmstart: train the start-vector network and compare steps and time to eps")
@@ -628,6 +706,8 @@ def main():
     alloc = "torch" if args.allocator == "torch" else None
 
     def step(inputs, ids, vals, profile=False, **kw):
+        kw.setdefault("spmv_tile", args.spmv_tile)
+        kw.setdefault("spmv_hot", args.spmv_hot)
         with psi.Graph(n, *inputs, profile=profile, stream=stream, allocator=alloc, **kw) as g:
             info = g.solve(args.eps, 100000)
             g.topk(100, ids, vals)
@@ -671,7 +751,7 @@ def main():
     steps_ms = [marks[i].elapsed_time(marks[i + 1]) for i in range(args.steps)]
 
     # ---- the autotuner's pick (made on the first warm-up graph) against the fixed rule
-    info_fixed, st_fixed = step(dev_in, ids_d, vals_d, profile=True, autotune=False)
+    info_fixed, st_fixed = step(dev_in, ids_d, vals_d, profile=True, autotune=False, spmv_tile=0, spmv_hot=-1)
     tuner = {"tile": stats["spmv_tile"], "hot": stats["spmv_hot"], "tune_ms": warm_stats[0]["tune_ms"],
              "fixed_rule": {"tile": st_fixed["spmv_tile"], "hot": 0,
                             "series_step_ms": info_fixed["spmv_ms"] / max(info_fixed["spmv_timed"], 1),

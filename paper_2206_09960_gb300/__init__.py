@@ -181,7 +181,7 @@ class Batch:
     ``lam``/``mu`` are [S, n] FP64 (scenario-major), host or device; 1 <= S <= 64."""
 
     def __init__(self, n, follower, leader, lam, mu, tol_mode="psi", bnorm_mode="none", self_loops="reject",
-                 reorder=True, stream=None, allocator="torch", spmv_tile=0):
+                 reorder=True, stream=None, allocator="torch", spmv_tile=0, profile=False):
         import torch
 
         B.load()
@@ -193,6 +193,7 @@ class Batch:
         opt.bnorm_mode = B.BNORM_MODE[bnorm_mode]
         opt.self_loops = B.SELF_LOOPS[self_loops]
         opt.reorder = 1 if reorder else 0
+        opt.profile = 1 if profile else 0
         opt.spmv_tile = int(spmv_tile)
         if stream is None:
             stream = torch.cuda.current_stream()

@@ -221,6 +221,7 @@ struct Batch {
   DBuf<double2> carry_head64, carry_tail64;
   DBuf<double> gap_part, gap_fix;
   int grid = 0, fgrid = 0;
+  int32_t keep_rows = 0;  // gathered rows kept in L2 by the products' load policy
   bool solved = false;
 };
 
@@ -336,6 +337,16 @@ void batch_buffers(Batch& b) {
   PSI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmm<float2, EpiSeriesS>, 256, 0));
   b.grid = (int)num_sms() * (per_sm > 0 ? per_sm : 1);
   b.fgrid = (int)num_sms() * 2;
+  {
+    // the most gathered rows get about 60% of L2 (a row: kSp FP32 values in the series, twice
+    // that for the float-pair products, which then keep fewer of them resident)
+    int dev = 0, l2 = 0;
+    PSI_CUDA(cudaGetDevice(&dev));
+    PSI_CUDA(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev));
+    const int64_t rows = (int64_t)(0.6 * (double)l2) / (int64_t)(kSp * sizeof(float));
+    const int64_t nu = (int64_t)g.nX + g.nU + 1;
+    b.keep_rows = (int32_t)(rows < nu ? rows : nu);
+  }
   b.gap_part.reset(al, (size_t)b.grid * 8 * kSp);
   b.gap_fix.reset(al, (size_t)b.fgrid * 8 * kSp);
 }
@@ -357,6 +368,7 @@ SpmmArgs spmm_args(Batch& b) {
   a.carry_tail = b.carry_tail.get();
   a.carry_head64 = b.carry_head64.get();
   a.carry_tail64 = b.carry_tail64.get();
+  a.keep_rows = b.keep_rows;
   return a;
 }
 
@@ -461,6 +473,12 @@ psi_status batch_solve(Batch& b, double eps, int32_t max_iter, psi_solve_info* i
   float* vb[2] = {b.va.get(), b.vb.get()};
   std::vector<int32_t> h_conv, h_iters, h_ok;
   const int batch = 4;
+  // profile: CUDA events around every FP32 series product; only the steps some scenario
+  // executed are counted (launches queued past the stop test exit at once)
+  const bool prof = g.opt.profile != 0;
+  std::vector<cudaEvent_t> pev;
+  double series_ms = 0.0;
+  int32_t series_timed = 0;
   while (iterate) {
     // FP32 series for the scenarios still active (Eq. 13), terms summed into s64
     PSI_CUDA(cudaMemsetAsync(b.ok.get(), 0, sizeof(int32_t) * kSp, s));
@@ -472,11 +490,39 @@ psi_status batch_solve(Batch& b, double eps, int32_t max_iter, psi_solve_info* i
         EpiSeriesS e{reinterpret_cast<const float2*>(b.mu32.get()), reinterpret_cast<const float2*>(b.isig32.get()),
                      reinterpret_cast<double2*>(b.s64.get()), reinterpret_cast<float2*>(vb[k & 1]), nX};
         const float* vin = k == 0 ? b.v0.get() : vb[(k + 1) & 1];
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (prof) {
+          PSI_CUDA(cudaEventCreate(&e0));
+          PSI_CUDA(cudaEventCreate(&e1));
+          PSI_CUDA(cudaEventRecord(e0, s));
+        }
         batch_step<float2, EpiSeriesS>(b, reinterpret_cast<const float2*>(vin), e);
+        if (prof) {
+          PSI_CUDA(cudaEventRecord(e1, s));
+          pev.push_back(e0);
+          pev.push_back(e1);
+        }
       }
       PSI_CUDA(cudaMemcpyAsync(b.host, b.state.get(), sizeof(BatchState), cudaMemcpyDeviceToHost, s));
       PSI_CUDA(cudaStreamSynchronize(s));
       if (b.host[0].done) break;
+    }
+    if (prof) {
+      std::vector<int32_t> ph;
+      read_vec(ph, b.phase_it.get(), kSp, s);
+      int32_t ran = 0;
+      for (int q = 0; q < S; ++q) ran = ph[q] > ran ? ph[q] : ran;
+      for (size_t i = 0; i + 1 < pev.size(); i += 2) {
+        if ((int32_t)(i / 2) < ran) {
+          float e = 0.f;
+          PSI_CUDA(cudaEventElapsedTime(&e, pev[i], pev[i + 1]));
+          series_ms += e;
+          ++series_timed;
+        }
+        cudaEventDestroy(pev[i]);
+        cudaEventDestroy(pev[i + 1]);
+      }
+      pev.clear();
     }
     u_current = false;
     read_vec(h_ok, b.ok.get(), kSp, s);
@@ -578,6 +624,8 @@ psi_status batch_solve(Batch& b, double eps, int32_t max_iter, psi_solve_info* i
       for (int c = 0; c < cs_blocks; ++c) ps += hp[(size_t)c * kSp + q];
       o.psi_sum = ps;
       o.ms = ms;
+      o.spmv_ms = series_ms;
+      o.spmv_timed = series_timed;
     }
   }
   return all_conv ? PSI_OK : PSI_ERR_NOT_CONVERGED;
