@@ -17,7 +17,11 @@
 //   * the step pairs are captured once into a CUDA graph and replayed until every graph is
 //     DONE, with no host work between steps.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <cstring>
 #include <vector>
 
@@ -448,6 +452,8 @@ struct Multi {
   int pairs_per_replay = 4;
   int launches_per_replay[2] = {0, 0};
   bool solved = false;
+  bool tile_fixed = false;  // psi_options.spmv_tile chose the tile
+  bool tuned = false;
 };
 
 // Per-graph ||B||_inf from sigma and beta, formed while the follower-grouped CSR exists.
@@ -736,7 +742,7 @@ int capture_pairs(Multi& M, cudaGraphExec_t* exec) {
 
 }  // namespace
 
-psi_status multi_solve(Multi& M, double eps, int32_t max_iter, psi_solve_info* info) {
+psi_status multi_solve_once(Multi& M, double eps, int32_t max_iter, psi_solve_info* info) {
   NvtxRange nvtx_range("psi_multi_solve");
   PSI_REQUIRE(max_iter >= 0 && !std::isnan(eps), PSI_ERR_INVALID_ARG, "bad eps or max_iter");
   Graph& g = M.g;
@@ -904,6 +910,75 @@ psi_status multi_solve(Multi& M, double eps, int32_t max_iter, psi_solve_info* i
   return all_conv ? PSI_OK : PSI_ERR_NOT_CONVERGED;
 }
 
+// Cuts the union's nonzeros into tiles of `tile` (schedule, carries, the graph ranges of
+// every tile) and drops the captured step pairs, which hold the old schedule.
+void multi_retile(Multi& M, int32_t tile) {
+  Graph& g = M.g;
+  cudaStream_t s = g.stream;
+  PSI_CUDA(cudaStreamSynchronize(s));
+  for (auto& e : M.exec) {
+    if (e) cudaGraphExecDestroy(e);
+    e = nullptr;
+  }
+  Schedule sc = make_schedule(g.row_ptr.get(), g.n_rows, g.m_unique, g.al, s, tile);
+  g.tile = sc.tile;
+  g.num_tiles = sc.tiles;
+  g.num_fix = sc.num_fix;
+  g.tile_row = std::move(sc.tile_row);
+  g.fix_tile = std::move(sc.fix_tile);
+  const size_t nt = (size_t)(g.num_tiles > 0 ? g.num_tiles : 1);
+  g.carry_head.reset(g.al, nt);
+  g.carry_tail.reset(g.al, nt);
+  M.tile_g.reset(g.al, nt);
+  if (g.num_tiles > 0) {
+    k_tile_groups<<<mgrid(g.num_tiles), 256, 0, s>>>(g.tile_row.get(), g.num_tiles, M.gid.get(), g.nX, M.tile_g.get());
+    PSI_LAUNCHED();
+  }
+}
+
+// The autotuner of the independent-graph object: its product has one free parameter, the
+// tile, and how well a tile fits depends on how the graphs stop one after another (a
+// stopped graph's tiles are skipped), so each candidate is timed on a whole solve of the
+// object (the first solve's eps and step cap), and the fastest is kept for this object and
+// remembered for objects of the same sizes.
+std::mutex g_mtune_mu;
+std::map<std::tuple<int32_t, int64_t, int64_t>, int32_t> g_mtune_cache;
+
+void multi_autotune(Multi& M, double eps, int32_t max_iter) {
+  Graph& g = M.g;
+  M.tuned = true;
+  if (!g.opt.autotune || M.tile_fixed || g.m_unique < ((int64_t)1 << 22)) return;
+  const auto key = std::make_tuple((int32_t)M.G, (int64_t)g.n, (int64_t)g.m_unique);
+  int32_t pick = 0;
+  {
+    std::lock_guard<std::mutex> lock(g_mtune_mu);
+    auto it = g_mtune_cache.find(key);
+    if (it != g_mtune_cache.end()) pick = it->second;
+  }
+  if (pick == 0) {
+    const auto t0 = std::chrono::steady_clock::now();
+    std::vector<psi_solve_info> inf((size_t)M.G);
+    double best = 0.0;
+    for (int32_t tile : {kSpmvTileMin, 2 * kSpmvTileMin, kSpmvTileMax}) {
+      if (tile != g.tile) multi_retile(M, tile);
+      multi_solve_once(M, eps, max_iter, inf.data());
+      if (pick == 0 || inf[0].ms < best) {
+        best = inf[0].ms;
+        pick = tile;
+      }
+    }
+    g.tune_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    std::lock_guard<std::mutex> lock(g_mtune_mu);
+    g_mtune_cache[key] = pick;
+  }
+  if (pick != g.tile) multi_retile(M, pick);
+}
+
+psi_status multi_solve(Multi& M, double eps, int32_t max_iter, psi_solve_info* info) {
+  if (!M.tuned) multi_autotune(M, eps, max_iter);
+  return multi_solve_once(M, eps, max_iter, info);
+}
+
 }  // namespace psi
 
 namespace psi {
@@ -990,7 +1065,8 @@ psi_status psi_multi_create(int32_t G, const int64_t* n_g, const int64_t* m_g, c
                 PSI_ERR_INVALID_ARG, "spmv_tile must be 0, 512, 1024 or 2048");
     o.precision = PSI_FP32_REFINE;
     // small tiles: once most graphs have stopped, the few still stepping own few nonzeros,
-    // and every tile is walked by one warp
+    // and every tile is walked by one warp (the autotuner may pick another on the first solve)
+    const bool tile_fixed = o.spmv_tile != 0;
     if (o.spmv_tile == 0) o.spmv_tile = 512;
     h = new psi_multi();
     Multi& M = h->m;
@@ -1005,6 +1081,7 @@ psi_status psi_multi_create(int32_t G, const int64_t* n_g, const int64_t* m_g, c
     }
     cudaStream_t s = g.stream;
     M.G = G;
+    M.tile_fixed = tile_fixed;
     M.h_noff = noff;
     M.noff.reset(g.al, (size_t)G + 1);
     PSI_CUDA(cudaMemcpyAsync(M.noff.get(), noff.data(), sizeof(int64_t) * (G + 1), cudaMemcpyHostToDevice, s));

@@ -242,3 +242,9 @@ def test_multi_full_recipe_every_graph():
     out = multi_solve(w, k=100)
     assert out["status"] == "PSI_OK"
     _check_against_oracle(w, out)
+    # the union has over 2^22 nonzeros, so its first solve timed the three tiles and kept one;
+    # the fixed tile gives the same psi up to rounding
+    assert out["stats"]["spmv_tile"] in (512, 1024, 2048) and out["stats"]["tune_ms"] > 0
+    fixed = multi_solve(w, k=100, spmv_tile=512)
+    assert fixed["stats"]["tune_ms"] == 0
+    assert rel_l1(out["psi"], fixed["psi"]) <= 1e-7
