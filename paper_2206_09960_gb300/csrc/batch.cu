@@ -221,7 +221,6 @@ struct Batch {
   DBuf<double2> carry_head64, carry_tail64;
   DBuf<double> gap_part, gap_fix;
   int grid = 0, fgrid = 0;
-  int32_t keep_rows = 0;  // gathered rows kept in L2 by the products' load policy
   bool solved = false;
 };
 
@@ -337,16 +336,7 @@ void batch_buffers(Batch& b) {
   PSI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmm<float2, EpiSeriesS>, 256, 0));
   b.grid = (int)num_sms() * (per_sm > 0 ? per_sm : 1);
   b.fgrid = (int)num_sms() * 2;
-  {
-    // the most gathered rows get about 60% of L2 (a row: kSp FP32 values in the series, twice
-    // that for the float-pair products, which then keep fewer of them resident)
-    int dev = 0, l2 = 0;
-    PSI_CUDA(cudaGetDevice(&dev));
-    PSI_CUDA(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev));
-    const int64_t rows = (int64_t)(0.6 * (double)l2) / (int64_t)(kSp * sizeof(float));
-    const int64_t nu = (int64_t)g.nX + g.nU + 1;
-    b.keep_rows = (int32_t)(rows < nu ? rows : nu);
-  }
+
   b.gap_part.reset(al, (size_t)b.grid * 8 * kSp);
   b.gap_fix.reset(al, (size_t)b.fgrid * 8 * kSp);
 }
@@ -368,7 +358,6 @@ SpmmArgs spmm_args(Batch& b) {
   a.carry_tail = b.carry_tail.get();
   a.carry_head64 = b.carry_head64.get();
   a.carry_tail64 = b.carry_tail64.get();
-  a.keep_rows = b.keep_rows;
   return a;
 }
 

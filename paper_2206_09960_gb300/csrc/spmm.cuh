@@ -31,9 +31,6 @@ struct SpmmArgs {
   int32_t S;                   // padded scenario count (64)
   const int32_t* active;       // [S]: 1 while a scenario still steps
   const int32_t* done;         // nonzero: no scenario steps, skip the launch
-  int32_t keep_rows;           // gathered rows below this index are loaded evict-last, the
-                               // rest evict-first: the most gathered rows (the gathered index
-                               // space is ordered by decreasing degree) keep L2 for themselves
   double* gap_part;            // [warps][S]
   float2* carry_head;          // [num_chunks][S/2] (FP32 products)
   float2* carry_tail;
@@ -196,7 +193,7 @@ __global__ void __launch_bounds__(256) k_spmm(SpmmArgs a, const V* __restrict__ 
 #pragma unroll
         for (int i = 0; i < 8; ++i) {  // eight row gathers in flight per lane
           const int j = __shfl_sync(0xffffffffu, my_col, i0 + i);
-          x[i] = ld_row(u + (int64_t)j * 32 + lane, j < a.keep_rows ? pol_k : pol_s);
+          x[i] = ld_row(u + (int64_t)j * 32 + lane, pol_k);
         }
 #pragma unroll
         for (int i = 0; i < 8; ++i) {

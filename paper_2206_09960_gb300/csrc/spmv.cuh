@@ -88,6 +88,11 @@ __device__ __forceinline__ DF2 shfl_xor_t<DF2>(DF2 v, int o) {
   return DF2(shfl_xor_t(v.a, o), shfl_xor_t(v.b, o));
 }
 template <>
+__device__ __forceinline__ F4 shfl_xor_t<F4>(F4 v, int o) {
+  return F4(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o),
+            __shfl_xor_sync(0xffffffffu, v.z, o), __shfl_xor_sync(0xffffffffu, v.w, o));
+}
+template <>
 __device__ __forceinline__ F4 shfl_up_t<F4>(F4 v, int o) {
   return F4(__shfl_up_sync(0xffffffffu, v.x, o), __shfl_up_sync(0xffffffffu, v.y, o),
             __shfl_up_sync(0xffffffffu, v.z, o), __shfl_up_sync(0xffffffffu, v.w, o));
@@ -487,9 +492,16 @@ inline int fix_blocks(int32_t num_fix) {
   return (int)(need < cap ? need : cap);
 }
 
-// Closes rows that began in an earlier tile, one row per thread: y = the sum of the tile
-// carries in tile order (four interleaved partial sums, joined pairwise) plus the partial
-// of the tile where the row ends.
+// Rows spanning more tiles than this are summed by a whole warp in the fix-up.
+constexpr int32_t kFixLongSpan = 128;
+
+// Closes rows that began in an earlier tile: y = the sum of the carries of the tiles the row
+// crosses, in tile order, plus the partial of the tile where it ends.  A row is one lane's
+// task (four interleaved partial sums over its tiles, joined pairwise) unless it spans more
+// than kFixLongSpan tiles; such a row (a leader with hundreds of thousands of followers and
+// more) is summed by its whole warp -- lane l takes tiles l, l + 32, ... in order, then a
+// fixed shuffle tree -- so its cost grows with span / 32 instead of span / 4.  Both orders are
+// fixed by the graph: results stay bit-reproducible.
 template <typename T, typename Epi>
 __global__ void __launch_bounds__(kFixThreads) k_fixup(FixArgs a, Epi epi) {
   if (a.state->done) return;
@@ -500,19 +512,40 @@ __global__ void __launch_bounds__(kFixThreads) k_fixup(FixArgs a, Epi epi) {
   const T* ch = static_cast<const T*>(a.carry_head);
   const T* ct = static_cast<const T*>(a.carry_tail);
   double gap = 0.0;
-  for (int32_t q = blockIdx.x * kFixThreads + threadIdx.x; q < a.num_fix; q += gridDim.x * kFixThreads) {
-    const int32_t k = a.fix_tile[q];
-    const int32_t r0 = a.tile_row[k];
-    int32_t kk = a.row_ptr[r0] / a.tile;  // tile where row r0 begins
-    T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
-    for (; kk + 4 <= k; kk += 4) {
-      s0 += ct[kk];
-      s1 += ct[kk + 1];
-      s2 += ct[kk + 2];
-      s3 += ct[kk + 3];
+  for (int32_t b = blockIdx.x * kFixThreads + warp * 32; b < a.num_fix; b += gridDim.x * kFixThreads) {
+    const int32_t q = b + lane;
+    int32_t k = 0, r0 = 0, kk0 = 0;
+    if (q < a.num_fix) {
+      k = a.fix_tile[q];
+      r0 = a.tile_row[k];
+      kk0 = a.row_ptr[r0] / a.tile;  // tile where row r0 begins
     }
-    for (; kk < k; ++kk) s0 += ct[kk];
-    epi.row(r0, ((s0 + s1) + (s2 + s3)) + ch[k], gap, pol_s, pol_k);
+    const bool is_long = q < a.num_fix && k - kk0 > kFixLongSpan;
+    if (q < a.num_fix && !is_long) {
+      int32_t kk = kk0;
+      T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+      for (; kk + 4 <= k; kk += 4) {
+        s0 += ct[kk];
+        s1 += ct[kk + 1];
+        s2 += ct[kk + 2];
+        s3 += ct[kk + 3];
+      }
+      for (; kk < k; ++kk) s0 += ct[kk];
+      epi.row(r0, ((s0 + s1) + (s2 + s3)) + ch[k], gap, pol_s, pol_k);
+    }
+    uint32_t longs = __ballot_sync(0xffffffffu, is_long);
+    while (longs) {  // long rows of this batch, one after another, by the whole warp
+      const int src = __ffs(longs) - 1;
+      longs &= longs - 1;
+      const int32_t kl = __shfl_sync(0xffffffffu, k, src);
+      const int32_t rl = __shfl_sync(0xffffffffu, r0, src);
+      const int32_t kb = __shfl_sync(0xffffffffu, kk0, src);
+      T acc = T(0);
+      for (int32_t kk = kb + lane; kk < kl; kk += 32) acc += ct[kk];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc = acc + shfl_xor_t(acc, o);
+      if (lane == 0) epi.row(rl, acc + ch[kl], gap, pol_s, pol_k);
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) gap += __shfl_xor_sync(0xffffffffu, gap, o);

@@ -174,15 +174,17 @@ def _run_pair(n, f, l, lam, mu, precision="fp32_refine", **kw):
 
 
 @pytest.mark.parametrize("lengths", [[1] * 50, [31, 32, 33], [4096, 1, 2048, 2049, 5], [20000], [2047, 2048, 2049],
-                                     [511, 512, 513, 1023, 1024, 1025], [255, 256, 257, 1, 1, 767]],
+                                     [511, 512, 513, 1023, 1024, 1025], [255, 256, 257, 1, 1, 767],
+                                     [70001, 3, 66049, 1]],
                          ids=["ones", "warpish", "tiles", "one_long_row", "tile_edges", "small_tile_edges",
-                              "step_edges"])
+                              "step_edges", "rows_over_128_tiles"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
 @pytest.mark.parametrize("spmv_tile", [512, 2048])
 def test_row_length_bins(lengths, precision, spmv_tile):
     """Rows (followers per leader) of chosen lengths, including one row spanning many tiles,
     rows ending exactly on tile and step boundaries and ragged tails, for the smallest and
-    the largest tile of the product."""
+    the largest tile of the product; with 512-nonzero tiles the last case has two rows that
+    span more than 128 tiles, which the fix-up sums with a whole warp."""
     rng = np.random.default_rng(sum(lengths))
     n = max(lengths) + len(lengths) + 10
     f, l = [], []
