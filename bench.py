@@ -37,9 +37,10 @@ METRIC = "Power-ψ time-to-L1<1e-8 and GTEPS/iter at N=2^25; % of HBM peak"
 FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes per launch of the FP32 series step (k_spmv + fix-up) from one ncu capture,
 # valid only while the kernel sources hash to `sha`.
-NCU_TRAFFIC = {"sha": "7bef0330ec15c30e", "bytes_per_launch": 2895861632,
-               "note": "k_spmv<float,EpiSeries> 2.731 GB read + 0.118 GB write (mean of 2 launches), k_fixup 0.047 GB; "
-                       "R-MAT scale 25 bench step, one ncu capture of 3 launches (1-pass metrics)"}
+NCU_TRAFFIC = {"sha": "a79666bafee8b9b9", "bytes_per_launch": 2466689006,
+               "note": "k_spmv<float,EpiSeries,32> (tile 1024, 28672 entries in shared memory) DRAM read + write on "
+                       "R-MAT scale 23 (one --set full capture: 623.5 MB = 0.940 x the kernel's own bytes), scaled "
+                       "to the scale-25 launch by its kernel bytes (2.624 GB)"}
 KERNEL_SOURCES = ["paper_2206_09960_gb300/csrc/spmv.cuh", "paper_2206_09960_gb300/csrc/common.cuh"]
 CPU_SAMPLE_SCALE = 20
 ONE_THREAD_SCALE = 18
@@ -462,6 +463,7 @@ def run_multi(args, G=256, plain_sample=32):
             "multi_solve_s": solve_multi, "plain_s_for_256": t_plain_all, "plain_solve_s_for_256": solve_plain,
             "speedup_total": t_plain_all / t_multi, "speedup_solve": solve_plain / solve_multi,
             "plain_sample": len(sample), "gpu_launches": launches, "build_ms": st["build_ms"], "clocks": clk,
+            "spmv_tile": st["spmv_tile"],
             "roofline": multi_roofline(st, solve_multi, iters)}
     print(json.dumps(line), flush=True)
 
@@ -800,7 +802,9 @@ def main():
     kernel_bytes = 4 * m_u + 32 * n_rows + 4 * n_g  # what this kernel has to touch (rows, gathered users)
     peak, peak_kind = measured_peaks()
     achieved = alg_bytes / avg_launch_s / 1e9
-    traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["sha"] == kernel_sha() else None
+    # the stored figure holds only for the kernel sources and the configuration it was taken on
+    same_cfg = (stats.get("spmv_tile"), stats.get("spmv_hot")) == (1024, 28672)
+    traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["sha"] == kernel_sha() and same_cfg else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_kind": peak_kind,
                 "kernel": (f"k_spmv<float,EpiSeries,{32 if stats['spmv_hot'] else 8}> + k_fixup "
