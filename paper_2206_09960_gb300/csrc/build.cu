@@ -79,13 +79,23 @@ __device__ __forceinline__ uint32_t block_sum(uint32_t v) {
   return r;
 }
 
-// lambda, mu finite, >= 0 and lambda + mu > 0 (the model needs c, d defined)
+// lambda, mu finite, >= 0 and lambda + mu > 0 (the model needs c, d defined).  Tested on
+// the bit patterns with integer operations (this part's FP64 pipe is narrow): a rate is
+// valid when its exponent field is not all ones (finite) and it is either non-negative or
+// a zero (-0.0 >= 0 holds); the pair when not both are zeros.
+__device__ __forceinline__ bool rate_ok(uint64_t b) {
+  const uint64_t mag = b & 0x7FFFFFFFFFFFFFFFull;
+  return (mag >> 52) != 0x7FFull && ((b >> 63) == 0 || mag == 0);
+}
 __global__ void k_check_rates(const double* __restrict__ lam, const double* __restrict__ mu, int64_t n,
                               uint32_t* err) {
   uint32_t bad = 0;
+  const unsigned long long* lb = reinterpret_cast<const unsigned long long*>(lam);
+  const unsigned long long* mb = reinterpret_cast<const unsigned long long*>(mu);
   grid_stride4(n, [&](int64_t i) {
-    const double x = lam[i], y = mu[i];
-    if (!(isfinite(x) && isfinite(y) && x >= 0.0 && y >= 0.0 && x + y > 0.0)) bad = kErrRate;
+    const uint64_t x = lb[i], y = mb[i];
+    const bool both_zero = ((x | y) & 0x7FFFFFFFFFFFFFFFull) == 0;
+    if (!(rate_ok(x) && rate_ok(y)) || both_zero) bad = kErrRate;
   });
   if (bad) atomicOr(err, bad);
 }
@@ -328,6 +338,21 @@ __global__ void k_leader_weights_df(const double* __restrict__ lam_i, const doub
   GRID_STRIDE(k, n + 1) w[k] = k < n ? DF2(df_from(lam_i[k] + mu_i[k]), df_from(lam_i[k])) : DF2(0);
 }
 
+// 1/v for a positive finite v: an FP32 reciprocal as the seed (relative error <= 2^-24), then
+// two steps of Newton's iteration for the reciprocal, r <- r + r (1 - v r), each of which
+// squares the relative error (2^-48, then below FP64 rounding): the result is within about
+// an ulp of 1/v.  Outside the FP32 normal range the FP64 division is used.
+__device__ __forceinline__ double recip64(double v) {
+  if (v > 1e-37 && v < 1e37) {
+    double r = (double)(1.0f / (float)v);
+    double e = fma(-v, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-v, r, 1.0);
+    return fma(r, e, r);
+  }
+  return 1.0 / v;
+}
+
 // c_j = mu_j/(lambda_j+mu_j), d_j = lambda_j/(lambda_j+mu_j), 1/sigma_j (0 without leaders)
 __global__ void k_user_vectors(const double* __restrict__ lam_i, const double* __restrict__ mu_i,
                                const double* __restrict__ sigma, const double* __restrict__ beta, int64_t n,
@@ -336,12 +361,12 @@ __global__ void k_user_vectors(const double* __restrict__ lam_i, const double* _
                                unsigned long long* bnorm_bits, unsigned long long* rho_bits) {
   double bn = 0.0, rho = 0.0;
   grid_stride4(n, [&](int64_t k) {
-    // two FP64 divisions per user (FP64 division is a long instruction sequence and FP64
-    // throughput is low on this part); c and d within an ulp of mu/(lambda+mu), lambda/(lambda+mu)
+    // two FP64 reciprocals per user (FP64 throughput is low on this part, and division is
+    // a long FP64 sequence); c and d within about an ulp of mu/(lambda+mu), lambda/(lambda+mu)
     const double x = lam_i[k], y = mu_i[k], sg = sigma[k];
-    const double inv = 1.0 / (x + y);
+    const double inv = recip64(x + y);
     const double c = y * inv, d = x * inv;
-    const double is = sg > 0.0 ? 1.0 / sg : 0.0;
+    const double is = sg > 0.0 ? recip64(sg) : 0.0;
     c64[k] = c;
     d64[k] = d;
     isig64[k] = is;

@@ -433,3 +433,22 @@ def test_autotuner_choice_changes_results_only_by_rounding():
     for name in ("tuned", "again", "hot"):
         assert rel_l1(runs[name]["psi"], runs["fixed"]["psi"]) <= 1e-7, name
     np.testing.assert_array_equal(runs["again"]["psi"], runs["tuned"]["psi"])  # same choice: same bits
+
+
+def test_start_vector_is_c_to_an_ulp_for_any_rates():
+    """With no step taken (max_iter = 0), s_0 = c: c_j = mu_j / (lambda_j + mu_j) from the
+    device's reciprocals, within 3 ulp of the FP64 quotient, for rates across the whole FP64
+    range (the FP32-seeded reciprocal and its FP64 fallback)."""
+    rng = np.random.default_rng(21)
+    n = 4000
+    lam = 10.0 ** rng.uniform(-300, 300, n)
+    mu = 10.0 ** rng.uniform(-300, 300, n)
+    lam[:1000] = rng.uniform(1e-3, 1e3, 1000)
+    mu[:1000] = rng.uniform(1e-3, 1e3, 1000)
+    lam[1000:1010] = 0.0  # lambda = 0 alone is allowed: c = 1
+    f = rng.integers(0, n, 20000).astype(np.int32)
+    l = rng.integers(0, n, 20000).astype(np.int32)
+    keep = f != l
+    out = gpu_solve(n, f[keep], l[keep], lam, mu, 1e-8, max_iter=0, precision="fp64")
+    want = mu / (lam + mu)
+    np.testing.assert_allclose(out["s"], want, rtol=6.7e-16, atol=0)
