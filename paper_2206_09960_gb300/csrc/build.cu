@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "primitives.cuh"
@@ -36,6 +37,20 @@ int grid_for(int64_t n, int threads = 256) {
   int64_t g = ceil_div(n > 0 ? n : 1, threads);
   int64_t cap = num_sms() * 16;
   return (int)(g < cap ? g : cap);
+}
+
+// Per-device streams and events for staging host inputs (see build_graph).
+struct CopyLane {
+  std::mutex mu;
+  cudaStream_t cs[2] = {nullptr, nullptr};
+  std::vector<cudaEvent_t> ev;
+};
+CopyLane& copy_lane() {
+  static CopyLane lanes[64];
+  int dev = 0;
+  PSI_CUDA(cudaGetDevice(&dev));
+  PSI_REQUIRE(dev >= 0 && dev < 64, PSI_ERR_CUDA, "device ordinal out of range");
+  return lanes[dev];
 }
 
 #define GRID_STRIDE(i, n) \
@@ -570,43 +585,43 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
     dmu = mu_buf.get();
   }
   const bool any_host = f_host || l_host || lam_host || mu_host;
-  // two copy streams, so that two copy engines move the follower and the leader arrays at once
-  cudaStream_t cs[2] = {nullptr, nullptr};
+  // two copy streams, so that two copy engines move the follower and the leader arrays at
+  // once; they and their events belong to the device's copy lane (created once, kept for the
+  // process: creating and destroying them on every build measured up to ~250 ms per build on
+  // hosts whose memory was being compacted), held for the whole staging by one build at a time
+  CopyLane& lane = copy_lane();
+  std::unique_lock<std::mutex> lane_lock(lane.mu, std::defer_lock);
+  cudaStream_t* cs = lane.cs;
   // [0]: buffers ready, [1], [2]: lambda, mu arrived, [3 + 2c], [4 + 2c]: follower / leader
   // chunk c arrived
-  std::vector<cudaEvent_t> arrived;
+  std::vector<cudaEvent_t>& arrived = lane.ev;
   const int64_t chunk = (int64_t)1 << 25;
   const int64_t n_chunks = m > 0 ? ceil_div(m, chunk) : 0;
   auto release_copies = [&]() {
-    for (cudaStream_t& c : cs) {
-      if (c) cudaStreamSynchronize(c);
-    }
-    for (cudaEvent_t e : arrived) cudaEventDestroy(e);
-    arrived.clear();
-    for (cudaStream_t& c : cs) {
-      if (c) cudaStreamDestroy(c);
-      c = nullptr;
-    }
+    if (!lane_lock.owns_lock()) return;
+    for (int i = 0; i < 2; ++i) cudaStreamSynchronize(cs[i]);
+    lane_lock.unlock();
   };
   struct CopyGuard {
     decltype(release_copies)& f;
     ~CopyGuard() { f(); }
   } copy_guard{release_copies};  // waits for the copies before the staging buffers go
   if (any_host) {
-    for (cudaStream_t& c : cs) PSI_CUDA(cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking));
-    cudaEvent_t ready;
-    PSI_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
-    arrived.push_back(ready);  // the staging buffers exist (stream-ordered allocation on s)
-    PSI_CUDA(cudaEventRecord(ready, s));
-    for (cudaStream_t c : cs) PSI_CUDA(cudaStreamWaitEvent(c, ready, 0));
-    if (lam_host) PSI_CUDA(cudaMemcpyAsync(lam_buf.get(), lambda, sizeof(double) * n, cudaMemcpyHostToDevice, cs[0]));
-    if (mu_host) PSI_CUDA(cudaMemcpyAsync(mu_buf.get(), mu, sizeof(double) * n, cudaMemcpyHostToDevice, cs[1]));
-    auto mark = [&](cudaStream_t c) {
+    lane_lock.lock();
+    for (int i = 0; i < 2; ++i)
+      if (!cs[i]) PSI_CUDA(cudaStreamCreateWithFlags(&cs[i], cudaStreamNonBlocking));
+    while ((int64_t)arrived.size() < 3 + 2 * n_chunks) {
       cudaEvent_t ev;
       PSI_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
       arrived.push_back(ev);
-      PSI_CUDA(cudaEventRecord(ev, c));
-    };
+    }
+    int next_ev = 0;
+    cudaEvent_t ready = arrived[next_ev++];  // the staging buffers exist (stream-ordered allocation on s)
+    PSI_CUDA(cudaEventRecord(ready, s));
+    for (int i = 0; i < 2; ++i) PSI_CUDA(cudaStreamWaitEvent(cs[i], ready, 0));
+    if (lam_host) PSI_CUDA(cudaMemcpyAsync(lam_buf.get(), lambda, sizeof(double) * n, cudaMemcpyHostToDevice, cs[0]));
+    if (mu_host) PSI_CUDA(cudaMemcpyAsync(mu_buf.get(), mu, sizeof(double) * n, cudaMemcpyHostToDevice, cs[1]));
+    auto mark = [&](cudaStream_t c) { PSI_CUDA(cudaEventRecord(arrived[next_ev++], c)); };
     mark(cs[0]);  // [1]: lambda
     mark(cs[1]);  // [2]: mu
     for (int64_t c = 0; c < n_chunks; ++c) {
