@@ -248,6 +248,39 @@ def host_placement(buf):
     return out
 
 
+def host_quiesce(limit_s=60.0, quiet_s=2.0):
+    """Waits (at most limit_s) until the kernel's background memory compaction has been idle
+    for quiet_s: compaction that a previous process's memory churn set off was measured
+    stalling DMA from pinned host memory (copies of the same buffer taking 2-8x longer),
+    which is not this library's transfer.  Returns the seconds waited and the compaction
+    counters moved meanwhile (Linux; nothing to wait for elsewhere)."""
+    keys = ("compact_daemon_migrate_scanned", "compact_daemon_free_scanned", "compact_isolated", "pgmigrate_success")
+
+    def counters():
+        d = {}
+        try:
+            with open("/proc/vmstat") as fh:
+                for line in fh:
+                    k, v = line.split()
+                    if k in keys:
+                        d[k] = int(v)
+        except OSError:
+            pass
+        return d
+
+    t0 = time.perf_counter()
+    first = last = counters()
+    if not first:
+        return 0.0, {}
+    still = 0.0
+    while time.perf_counter() - t0 < limit_s and still < quiet_s:
+        time.sleep(0.5)
+        now = counters()
+        still = still + 0.5 if now == last else 0.0
+        last = now
+    return time.perf_counter() - t0, {k: last[k] - first[k] for k in last if last[k] != first[k]}
+
+
 def pinned_h2d_gbs(h, d, stream, reps=3):
     """Host-to-device bandwidth of one pinned input buffer (GB/s), timed with CUDA events."""
     import torch
@@ -762,6 +795,7 @@ def main():
     # ---- end to end from pinned host buffers (H2D of inputs and D2H of the ranking inside)
     e2e = None
     if not args.no_e2e:
+        quiesce_s, quiesce_moved = host_quiesce()
         step(host_in, ids_h, vals_h)
         barrier()
         t0 = time.perf_counter()
@@ -790,7 +824,8 @@ def main():
                "d2h_bytes_per_step": int(100 * (4 + 8)), "s_per_step": e2e_s, "h2d_gbs": h2d_gbs,
                "host_buffers": placement, "steps_ms": e2e_steps_ms,
                "steps_wall_ms": [round(x * 1e3, 3) for x in e2e_walls],
-               "steps_build_ms": [round(x, 3) for x in e2e_builds], "torch_allocator": alloc_stats}
+               "steps_build_ms": [round(x, 3) for x in e2e_builds], "torch_allocator": alloc_stats,
+               "host_quiesce": {"waited_s": round(quiesce_s, 2), "compaction_counters_moved": quiesce_moved}}
 
     # ---- roofline of the dominant kernel: the FP32 series step (sparse product + fix-up)
     iters = statistics.mean(i["iters"] for i in infos)

@@ -117,6 +117,46 @@ __device__ __forceinline__ F4 shfl_idx_t<F4>(F4 v, int src) {
             __shfl_sync(0xffffffffu, v.z, src), __shfl_sync(0xffffffffu, v.w, src));
 }
 
+// ------------------------------------------------------------------ lane accumulators
+// The sum of a lane's items between row ends.  For float pairs the high parts are added with
+// Knuth's two-sum, whose error terms and the low parts collect in a second float, and the
+// pair is renormalised only when the sum leaves the lane (at a row end, into the scan): the
+// dependent chain per item is one FP32 add instead of a whole pair sum.  The result is the
+// pair sum to within the FP32 rounding of the collected errors, about 2^-24 of a few ulps
+// of the high part -- the accuracy of the pair sums themselves.
+template <typename T>
+struct LaneAcc {
+  T v;
+  __device__ __forceinline__ explicit LaneAcc(T x) : v(x) {}
+  __device__ __forceinline__ void add(T x) { v += x; }
+  __device__ __forceinline__ T get() const { return v; }
+};
+template <>
+struct LaneAcc<DF> {
+  float s, c;
+  __device__ __forceinline__ explicit LaneAcc(DF x) : s(x.hi), c(x.lo) {}
+  __device__ __forceinline__ void add(DF x) {
+    const float t = s + x.hi;
+    const float z = t - s;
+    c += ((s - (t - z)) + (x.hi - z)) + x.lo;
+    s = t;
+  }
+  __device__ __forceinline__ DF get() const {
+    const float h = s + c;
+    return DF(h, c - (h - s));
+  }
+};
+template <>
+struct LaneAcc<DF2> {
+  LaneAcc<DF> a, b;
+  __device__ __forceinline__ explicit LaneAcc(DF2 x) : a(x.a), b(x.b) {}
+  __device__ __forceinline__ void add(DF2 x) {
+    a.add(x.a);
+    b.add(x.b);
+  }
+  __device__ __forceinline__ DF2 get() const { return DF2(a.get(), b.get()); }
+};
+
 // ------------------------------------------------------------------ epilogues
 // row(r, y, gap): y = G(.)_r for row r (a user with followers); add |change| to gap.
 
@@ -433,24 +473,24 @@ __global__ void __launch_bounds__(WARPS * 32, WARPS == kSpmvWarps ? spmv_min_blo
       done += total;
       // rows that begin and end inside this lane are closed now; the head (up to the first
       // row end) waits for the sum carried in from the lanes before
-      T acc = lane == 0 ? open : T(0);
+      LaneAcc<T> acc(lane == 0 ? open : T(0));
       T head = T(0);
       int32_t jr = j0;
 #pragma unroll
       for (int j = 0; j < kSpmvItems; ++j) {
-        acc += x[j];
+        acc.add(x[j]);
         if ((e >> j) & 1u) {
-          if (jr == j0) head = acc;
-          else epi.row(r0 + jr, acc, gap, pol_s, pol_k);
+          if (jr == j0) head = acc.get();
+          else epi.row(r0 + jr, acc.get(), gap, pol_s, pol_k);
           ++jr;
-          acc = T(0);
+          acc = LaneAcc<T>(T(0));
         }
       }
       // segmented inclusive scan of the sums after each lane's last row end: after offset o
       // a lane holds the sum over lanes max(lane - 2o + 1, last_end) .. lane, so it adds its
       // partner's value only while no row end lies in its own window
       const int last_end = 31 - __clz(__ballot_sync(0xffffffffu, cnt > 0) & (below | (1u << lane)));
-      T v = acc;
+      T v = acc.get();
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
         const T vu = shfl_up_t(v, o);
