@@ -220,6 +220,20 @@ const char* psi_last_error(void);
 psi_status psi_pagerank(psi_graph* g, double alpha, double eps, int32_t max_iter, double* pi_out,
                         psi_solve_info* info);
 
+/*
+ * psi_power_nf -- Power-NF (Algorithm 1), the method Power-psi replaces, for small graphs
+ * (n <= 4096): for every origin user i, the newsfeed vector of Eq. 8, p_i <- A p_i + b_i from
+ * p_i = b_i, until ||p_i^t - p_i^{t-1}||_1 <= eps (each origin on its own test; a gap of 1
+ * before the first step) or max_iter steps; then q_i = C p_i + d_i (Eq. 7) and
+ * psi_i = (1/N) sum_n q_i^(n) (Eq. 1), in FP64.  All origins step together as the columns
+ * of an n x n matrix.  psi_out: n FP64 values in input order, host or device (may be
+ * NULL).  info (may be NULL): iters = the most steps any origin took, spmv_launches = the
+ * matrix-vector products of Algorithm 1 (steps summed over origins), gap_s_l1 = the largest
+ * last gap, converged, ms.  The handle's psi scores are left as they were.
+ * Returns OK, NOT_CONVERGED (psi still written) or an error (INVALID_ARG for n > 4096).
+ */
+psi_status psi_power_nf(psi_graph* g, double eps, int32_t max_iter, double* psi_out, psi_solve_info* info);
+
 /* ------------------------------------------------------------------------------------
  * Scenario batches: S sets of activity rates (lambda, mu) on one follower graph, solved
  * together.  Each scenario is an independent Power-psi problem (Algorithm 2 with its own

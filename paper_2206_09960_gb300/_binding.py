@@ -33,7 +33,7 @@ EXPORTS = ["psi_options_default", "psi_graph_create", "psi_solve", "psi_scores",
            "psi_features", "psi_mlp_create", "psi_mlp_set_params", "psi_mlp_get_params", "psi_mlp_forward",
            "psi_mlp_grad", "psi_mlp_adam_step", "psi_mlp_destroy", "psi_solve_warm", "psi_multi_create",
            "psi_multi_solve", "psi_multi_scores", "psi_multi_topk", "psi_multi_get_stats", "psi_multi_destroy",
-           "psi_pagerank", "psi_trim_memory"]
+           "psi_pagerank", "psi_trim_memory", "psi_power_nf"]
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -133,6 +133,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.psi_trim_memory.restype = i32
         lib.psi_pagerank.argtypes = [vp, dbl, dbl, i32, vp, vp]
         lib.psi_pagerank.restype = i32
+        lib.psi_power_nf.argtypes = [vp, dbl, i32, vp, vp]
+        lib.psi_power_nf.restype = i32
         lib.psi_multi_create.argtypes = [i32, vp, vp, vp, vp, vp, vp, ctypes.POINTER(psi_options),
                                          ctypes.POINTER(vp)]
         lib.psi_multi_create.restype = i32
@@ -269,6 +271,13 @@ def psi_batch_get_stats(h) -> psi_graph_stats:
 
 def psi_batch_destroy(h):
     load().psi_batch_destroy(h)
+
+
+def psi_power_nf(h, eps, max_iter, out_ptr):
+    info = psi_solve_info()
+    st = load().psi_power_nf(h, float(eps), int(max_iter), out_ptr, ctypes.byref(info))
+    _check(st, allow=(PSI_OK, PSI_ERR_NOT_CONVERGED))
+    return st, info.as_dict()
 
 
 def psi_pagerank(h, alpha, eps, max_iter, out_ptr):
