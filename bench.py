@@ -569,6 +569,68 @@ def run_pagerank(args, alpha=0.85, eps=1e-9):
     print(json.dumps(line), flush=True)
 
 
+def run_powernf(args, eps=1e-12):
+    """The comparison of the paper's Table III on small graphs: Power-NF (Algorithm 1, one
+    newsfeed vector per origin, per-origin stop test eps) against Power-psi (Algorithm 2,
+    FP64, s-tolerance eps) on the same graph handle, solve times only, the largest psi
+    difference between the two, and the oracle's Power-NF on the host beside them."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import psigen
+    import paper_2206_09960_gb300 as psi
+
+    psi.load(build_if_missing=False)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        res = None
+        ts = []
+        for rep in range(args.warmup + args.steps):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if rep >= args.warmup:
+                ts.append(e0.elapsed_time(e1) / 1e3)
+        return sum(ts) / len(ts), res
+
+    cases = [("poisson1000_k10_uniform0.1-1", psigen.workload("poisson1000", seed=args.seed)),
+             ("chunglu_n4096_gamma2.1_lognormal1", psigen.workload("chunglu", seed=args.seed, scale=12))]
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    rows = []
+    for name, w in cases:
+        n = w["n"]
+        dev = [torch.from_numpy(np.ascontiguousarray(w[k])).cuda() for k in ("follower", "leader", "lam", "mu")]
+        with psi.Graph(n, *dev, precision="fp64", tol_mode="s_abs", stream=stream) as g:
+            t_nf, (nf_psi, nf) = timed(lambda: g.power_nf(eps, 100000))
+            t_ps, pinfo = timed(lambda: g.solve(eps, 100000))
+            ps = g.scores()
+            diff = float(((nf_psi - ps).abs() / ps.abs().clamp_min(1.0 / n)).max())
+        t0 = time.perf_counter()
+        with oracle.Model(n, w["follower"], w["leader"], w["lam"], w["mu"]) as m:
+            _, mv_cpu = m.power_nf(eps)
+        t_cpu = time.perf_counter() - t0
+        rows.append({"workload": name, "n": n, "edges": int(len(w["follower"])),
+                     "power_nf_s": t_nf, "power_nf_matvecs": nf["spmv_launches"], "power_nf_steps_max": nf["iters"],
+                     "power_psi_s": t_ps, "power_psi_iters": pinfo["iters"], "nf_over_psi_time": t_nf / t_ps,
+                     "max_rel_psi_diff": diff, "oracle_power_nf_s": t_cpu, "oracle_matvecs": mv_cpu})
+    clk = clocks.stop()
+    line = {"metric": "Table III comparison: solve time of Power-NF (Algorithm 1) and Power-psi at eps=1e-12",
+            "value": rows[0]["power_psi_s"], "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": False, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "+".join(r["workload"] for r in rows), "eps": eps,
+                       "tolerance": "per-origin ||p_t - p_t-1||_1 (Power-NF), ||s_t - s_t-1||_1 (Power-psi)"},
+            "cases": rows, "clocks": clk,
+            "cpu_baseline": {"value": rows[0]["oracle_power_nf_s"], "unit": "s", "cores": 1, "kind": "oracle",
+                             "sample": f"{rows[0]['workload']}: the oracle's Power-NF once"}}
+    print(json.dumps(line), flush=True)
+
+
 def run_warmstart(args, n_train=200, eval_scale=23, train_steps=1500):
     """Train the warm-start network on solves of `n_train` seeded R-MAT graphs of scale 16-20
     (the benchmark's rate law), then time Power-psi to eps on a held-out R-MAT graph of scale
@@ -686,7 +748,7 @@ def main():
     ap.add_argument("--spmv-tile", type=int, default=0, help="fix the product's tile (0: autotuner / rule)")
     ap.add_argument("--spmv-hot", type=int, default=-1,
                     help="fix the series product's shared-memory copy (-1: autotuner's choice)")
-    ap.add_argument("--workload", default="rmat", choices=["rmat", "batch", "warmstart", "multi", "pagerank"],
+    ap.add_argument("--workload", default="rmat", choices=["rmat", "batch", "warmstart", "multi", "pagerank", "powernf"],
                     help="rmat: the single-graph step (default); batch: 64 activity scenarios on one graph; "
                          "warmstart: train the start-vector network and compare steps and time to eps")
     args = ap.parse_args()
@@ -705,6 +767,9 @@ def main():
         return
     if args.workload == "pagerank":
         run_pagerank(args)
+        return
+    if args.workload == "powernf":
+        run_powernf(args)
         return
 
     import numpy as np
