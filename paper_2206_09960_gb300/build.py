@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libpsi_gb300.so")
-SOURCES = ["api.cu", "build.cu", "solve.cu", "topk.cu", "primitives.cu", "topk_noalloc.cu", "batch.cu", "warmstart.cu", "multi.cu", "pagerank.cu", "powernf.cu"]
+SOURCES = ["api.cu", "build.cu", "solve.cu", "topk.cu", "primitives.cu", "topk_noalloc.cu", "batch.cu", "warmstart.cu", "multi.cu", "pagerank.cu", "powernf.cu", "leader_sums.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

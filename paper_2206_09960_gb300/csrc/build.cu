@@ -26,6 +26,7 @@
 #include "solve.cuh"
 #include "spmv.cuh"
 #include "build.cuh"
+#include "leader_sums.cuh"
 
 namespace psi {
 
@@ -102,17 +103,34 @@ __device__ __forceinline__ bool rate_ok(uint64_t b) {
   const uint64_t mag = b & 0x7FFFFFFFFFFFFFFFull;
   return (mag >> 52) != 0x7FFull && ((b >> 63) == 0 || mag == 0);
 }
+// Also the range of the biased exponents of the nonzero rates (a subnormal rate counts as
+// exponent 0): exp_range[0] = min (start at ~0), exp_range[1] = max (start at 0).
 __global__ void k_check_rates(const double* __restrict__ lam, const double* __restrict__ mu, int64_t n,
-                              uint32_t* err) {
-  uint32_t bad = 0;
+                              uint32_t* err, uint32_t* exp_range) {
+  uint32_t bad = 0, emin = 0xFFFFFFFFu, emax = 0;
   const unsigned long long* lb = reinterpret_cast<const unsigned long long*>(lam);
   const unsigned long long* mb = reinterpret_cast<const unsigned long long*>(mu);
   grid_stride4(n, [&](int64_t i) {
     const uint64_t x = lb[i], y = mb[i];
     const bool both_zero = ((x | y) & 0x7FFFFFFFFFFFFFFFull) == 0;
     if (!(rate_ok(x) && rate_ok(y)) || both_zero) bad = kErrRate;
+    const uint64_t xm = x & 0x7FFFFFFFFFFFFFFFull, ym = y & 0x7FFFFFFFFFFFFFFFull;
+    if (xm) {
+      emin = min(emin, (uint32_t)(xm >> 52));
+      emax = max(emax, (uint32_t)(xm >> 52));
+    }
+    if (ym) {
+      emin = min(emin, (uint32_t)(ym >> 52));
+      emax = max(emax, (uint32_t)(ym >> 52));
+    }
   });
   if (bad) atomicOr(err, bad);
+  emin = __reduce_min_sync(0xffffffffu, emin);
+  emax = __reduce_max_sync(0xffffffffu, emax);
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(exp_range, emin);
+    atomicMax(exp_range + 1, emax);
+  }
 }
 
 // Validates every edge and marks, exactly, who has followers (fol_bits) and who has leaders
@@ -221,11 +239,6 @@ __global__ void k_edge_keys(const int32_t* __restrict__ f, const int32_t* __rest
   });
 }
 
-__device__ __forceinline__ bool first_of_run(const uint64_t* key, int64_t e, uint64_t sentinel) {
-  uint64_t k = key[e];
-  return k != sentinel && (e == 0 || key[e - 1] != k);
-}
-
 // Duplicate merge and CSR of the sorted edge keys as one stream compaction over tiles of
 // kUqTile keys: k_unique_count counts the unique keys of every tile, an exclusive scan of
 // those counts gives each tile its output offset, and k_unique_write writes the unique keys
@@ -235,14 +248,29 @@ constexpr int kUqThreads = 256;
 constexpr int kUqItems = 16;
 constexpr int kUqTile = kUqThreads * kUqItems;
 
+// With exact leader sums (DUPS): every repeat of a key takes its leader's rates and one count
+// back out of its follower's sums, which counted all edges.
+template <bool DUPS>
 __global__ void __launch_bounds__(kUqThreads) k_unique_count(const uint64_t* __restrict__ key, int64_t m,
-                                                             uint64_t sentinel, uint32_t* __restrict__ count) {
+                                                             uint64_t sentinel, uint32_t* __restrict__ count, int bf,
+                                                             const FixedRow* __restrict__ rows,
+                                                             unsigned long long* acc_s, unsigned long long* acc_b,
+                                                             uint32_t* acc_c) {
   const int64_t base = (int64_t)blockIdx.x * kUqTile;
   uint32_t c = 0;
 #pragma unroll 4
   for (int j = 0; j < kUqItems; ++j) {
     const int64_t e = base + (int64_t)j * kUqThreads + threadIdx.x;
-    if (e < m && first_of_run(key, e, sentinel)) ++c;
+    if (e < m) {
+      const uint64_t k = key[e];
+      if (k != sentinel) {
+        if (e == 0 || key[e - 1] != k) {
+          ++c;
+        } else if (DUPS) {
+          fixed_sub_row(ld_fixed_row(rows + (k >> bf)), acc_s, acc_b, acc_c, (uint32_t)(k & ((1ull << bf) - 1)));
+        }
+      }
+    }
   }
   c = block_sum(c);
   if (threadIdx.x == 0) count[blockIdx.x] = c;
@@ -285,7 +313,7 @@ __global__ void __launch_bounds__(kUqThreads) k_unique_write(const uint64_t* __r
     if (uniq) {
       const uint32_t o = run + before + __popc(bal & lt_mask);
       const int32_t r = (int32_t)(k >> b);
-      li[o] = r;
+      if (li) li[o] = r;
       col[o] = (int32_t)(k & low);
       if (first_in_row) {
         row_ptr[r] = (int32_t)o;
@@ -641,6 +669,9 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
   // ---- 1. validation and raw degrees
   DBuf<uint32_t> err(al, 8);  // [0] error bits, [1..4] class counts, [5] rows seen, [6..7] spare
   PSI_CUDA(cudaMemsetAsync(err.get(), 0, 8 * sizeof(uint32_t), s));
+  DBuf<uint32_t> exp_range(al, 2);  // biased exponents of the nonzero rates: min, max
+  PSI_CUDA(cudaMemsetAsync(exp_range.get(), 0xFF, sizeof(uint32_t), s));
+  PSI_CUDA(cudaMemsetAsync(exp_range.get() + 1, 0, sizeof(uint32_t), s));
   DBuf<uint32_t> in_deg(al, (size_t)n), out_deg(al, (size_t)n);
   const size_t n_words = (size_t)ceil_div(n, 32);
   DBuf<uint32_t> fol_bits(al, n_words), lead_bits(al, n_words);
@@ -652,7 +683,7 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
     PSI_CUDA(cudaStreamWaitEvent(s, arrived[1], 0));
     PSI_CUDA(cudaStreamWaitEvent(s, arrived[2], 0));
   }
-  k_check_rates<<<grid_for(n), 256, 0, s>>>(dlam, dmu, n, err.get());
+  k_check_rates<<<grid_for(n), 256, 0, s>>>(dlam, dmu, n, err.get(), exp_range.get());
   PSI_LAUNCHED();
   if (m > 0) {
     // degree sample: every edge up to 2^26 edges, then a fixed 1-in-2^k subset
@@ -691,8 +722,9 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
   out_deg.release();
   fol_bits.release();
   lead_bits.release();
-  uint32_t cls[4];
+  uint32_t cls[4], erange[2];
   PSI_CUDA(cudaMemcpyAsync(cls, err.get() + 1, sizeof(cls), cudaMemcpyDeviceToHost, s));
+  PSI_CUDA(cudaMemcpyAsync(erange, exp_range.get(), sizeof(erange), cudaMemcpyDeviceToHost, s));
   PSI_CUDA(cudaStreamSynchronize(s));
   g.nX = (int32_t)cls[0];
   g.nR = (int32_t)cls[1];
@@ -713,6 +745,14 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
   const uint64_t sentinel = ((uint64_t)1 << (bl + bf)) - 1;
   int64_t mu_count = 0;
   DBuf<int32_t> li;
+  // sigma and beta of a single graph as exact sums (leader_sums.cuh) when the rates allow:
+  // formed from the keys half-way through the sort, no follower-grouped CSR
+  const bool exact = hook == nullptr && nu > 0 && m > 0 && exact_sums_apply(erange[0], erange[1]);
+  ExactLeaderSums xs;
+  DBuf<double> lam_i(al, (size_t)n), mu_i(al, (size_t)n);
+  k_permute_rates<<<grid_for(n), 256, 0, s>>>(dlam, dmu, perm32.get(), n, lam_i.get(), mu_i.get());
+  PSI_LAUNCHED();
+  if (exact) exact_sums_prepare(xs, lam_i.get(), mu_i.get(), g.n_rows, (int32_t)nu, erange[0], al, s);
   {
     DBuf<int32_t> inv(al, (size_t)n);
     k_invert<<<grid_for(n), 256, 0, s>>>(perm32.get(), n, inv.get());
@@ -725,13 +765,28 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
     inv.release();
     fbuf.release();
     lbuf.release();
-    bool alt = radix_sort<uint64_t>(k0.get(), k1.get(), nullptr, nullptr, m, bl + bf, al, s);
+    bool alt;
+    if (exact) {  // the follower field first; between the two halves the keys are grouped by follower
+      const bool a1 = radix_sort_bits<uint64_t>(k0.get(), k1.get(), nullptr, nullptr, m, 0, bf, al, s);
+      uint64_t* mid = a1 ? k1.get() : k0.get();
+      exact_sums_groups(xs, mid, m, bf, (int32_t)nu, s);
+      const bool a2 = radix_sort_bits<uint64_t>(mid, a1 ? k0.get() : k1.get(), nullptr, nullptr, m, bf, bf + bl, al, s);
+      alt = a1 != a2;
+    } else {
+      alt = radix_sort<uint64_t>(k0.get(), k1.get(), nullptr, nullptr, m, bl + bf, al, s);
+    }
     const uint64_t* keys = alt ? k1.get() : k0.get();
     const int64_t uq_tiles = ceil_div(m, kUqTile);
     DBuf<uint32_t> uq_off(al, (size_t)(uq_tiles > 0 ? uq_tiles : 1));
     DBuf<uint32_t> total(al, 1);
     if (m > 0) {
-      k_unique_count<<<(unsigned)uq_tiles, kUqThreads, 0, s>>>(keys, m, sentinel, uq_off.get());
+      if (exact)
+        k_unique_count<true><<<(unsigned)uq_tiles, kUqThreads, 0, s>>>(keys, m, sentinel, uq_off.get(), bf,
+                                                                      xs.rows.get(), xs.s.get(), xs.b.get(),
+                                                                      xs.cnt.get());
+      else
+        k_unique_count<false><<<(unsigned)uq_tiles, kUqThreads, 0, s>>>(keys, m, sentinel, uq_off.get(), bf, nullptr,
+                                                                       nullptr, nullptr, nullptr);
       PSI_LAUNCHED();
       exclusive_scan_u32(uq_off.get(), uq_off.get(), uq_tiles, al, s, total.get());
       mu_count = read1(total.get(), s);
@@ -743,7 +798,7 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
     g.num_tiles = (int32_t)ceil_div(mu_count, g.tile);
     const int64_t padded = ceil_div(mu_count, kSpmvTileMax) * kSpmvTileMax;
     g.col.reset(al, (size_t)(padded > 0 ? padded : 4));
-    li.reset(al, (size_t)(mu_count > 0 ? mu_count : 1));
+    if (!exact) li.reset(al, (size_t)(mu_count > 0 ? mu_count : 1));  // leader rows, for the follower sort
     g.row_ptr.reset(al, (size_t)g.n_rows + 1);
     if (mu_count > 0) {
       k_unique_write<<<(unsigned)uq_tiles, kUqThreads, 0, s>>>(keys, m, sentinel, uq_off.get(), bf, li.get(),
@@ -770,11 +825,8 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
   }
 
   phases.next("psi build 4: sigma and beta");
-  // ---- 4. leader sums per follower: (sigma, beta) = L (lambda + mu, lambda), one
-  //         load-balanced product over the follower-grouped CSR (rows X then U)
-  DBuf<double> lam_i(al, (size_t)n), mu_i(al, (size_t)n);
-  k_permute_rates<<<grid_for(n), 256, 0, s>>>(dlam, dmu, perm32.get(), n, lam_i.get(), mu_i.get());
-  PSI_LAUNCHED();
+  // ---- 4. leader sums per follower: (sigma, beta) = L (lambda + mu, lambda): exact sums
+  //         (above), or one load-balanced product over the follower-grouped CSR (rows X then U)
   perm32.release();
   lam_buf.release();
   mu_buf.release();
@@ -783,7 +835,10 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
   PSI_CUDA(cudaMemsetAsync(g.n_leaders.get(), 0, sizeof(int32_t) * n, s));
   PSI_CUDA(cudaMemsetAsync(sigma.get(), 0, sizeof(double) * n, s));
   PSI_CUDA(cudaMemsetAsync(beta.get(), 0, sizeof(double) * n, s));
-  if (mu_count > 0) {
+  if (exact) {
+    exact_sums_finish(xs, (int32_t)nu, g.nX, g.nR, sigma.get(), beta.get(), g.n_leaders.get(), s);
+    xs = ExactLeaderSums();
+  } else if (mu_count > 0) {
     const int64_t mc = mu_count;
     const int32_t n_f = g.nX + g.nU;  // followers: users with leaders
     const int32_t tiles_f = (int32_t)ceil_div(mc, kSpmvTileMax);

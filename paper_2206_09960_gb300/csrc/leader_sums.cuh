@@ -1,0 +1,76 @@
+// leader_sums.cuh -- sigma_j = sum_{l in L(j)} (lambda_l + mu_l) and beta_j = sum_{l in L(j)}
+// lambda_l (Sec. II: the denominators of a_ji and b_ji) as exact sums, for the single-graph
+// build.
+//
+// Every nonzero rate is m * 2^(e - 1075) with a 53-bit integer m and biased exponent e.  When
+// all rates of the graph have exponents in [ebase, ebase + kFixedSpan], a rate divided by
+// 2^(ebase - 1075) is the integer m << (e - ebase) < 2^94, and the sum over up to 2^31
+// leaders fits 128 bits.  Integer addition is exact and associative, so the sums can be
+// formed in any order (atomics included) and are rounded to FP64 once, at the end: the
+// result does not depend on the order of the edges, the schedule or the grouping.
+//
+// The sums are formed from the edge keys (leader row << bf | follower's gathered index)
+// while they are grouped by follower, half-way through the edge sort (all edges, duplicates
+// included), and the duplicates found after the sort are subtracted (again exact).
+#pragma once
+
+#include "common.cuh"
+
+namespace psi {
+
+constexpr int kFixedSpan = 40;  // largest exponent range of the rates the exact sums accept
+
+// lambda_l + mu_l (s) and lambda_l (b) of one leader row, each as a 128-bit integer
+struct __align__(32) FixedRow {
+  unsigned long long s_lo, s_hi, b_lo, b_hi;
+};
+
+// 128-bit add into (lo, hi) words in device memory, exact under any interleaving: the low
+// word's atomic returns the value it added to, so the carry out of that very addition goes
+// to the high word
+__device__ __forceinline__ void atomic_add128(unsigned long long* p, unsigned long long lo, unsigned long long hi) {
+  const unsigned long long old = atomicAdd(p, lo);
+  const unsigned long long carry = old + lo < old ? 1ull : 0ull;
+  if (hi + carry) atomicAdd(p + 1, hi + carry);
+}
+
+// subtract one leader row's (s, b) and one count from follower group g (modulo 2^128: the
+// final sums are non-negative, so the wrap-around is exact)
+__device__ __forceinline__ void fixed_sub_row(const FixedRow& v, unsigned long long* acc_s, unsigned long long* acc_b,
+                                              uint32_t* acc_c, uint32_t g) {
+  atomic_add128(acc_s + 2 * (size_t)g, ~v.s_lo + 1ull, ~v.s_hi + (v.s_lo == 0 ? 1ull : 0ull));
+  atomic_add128(acc_b + 2 * (size_t)g, ~v.b_lo + 1ull, ~v.b_hi + (v.b_lo == 0 ? 1ull : 0ull));
+  atomicSub(acc_c + g, 1u);
+}
+
+__device__ __forceinline__ FixedRow ld_fixed_row(const FixedRow* p) {
+  FixedRow v;
+  asm volatile("ld.global.nc.v4.u64 {%0,%1,%2,%3}, [%4];"
+               : "=l"(v.s_lo), "=l"(v.s_hi), "=l"(v.b_lo), "=l"(v.b_hi)
+               : "l"(p));
+  return v;
+}
+
+// The exact-sum state of one build.
+struct ExactLeaderSums {
+  DBuf<FixedRow> rows;           // [n_rows]
+  DBuf<unsigned long long> s, b;  // [2 * nu]: (lo, hi) per follower group
+  DBuf<uint32_t> cnt;             // [nu]: distinct leaders
+  int ebase = 0;
+};
+
+// Whether the rates' biased exponents (over the nonzero rates; 0 when one is subnormal)
+// allow exact sums.
+bool exact_sums_apply(uint32_t emin_biased, uint32_t emax_biased);
+
+// Fixed-point rows of the leaders (internal order), zeroed group sums.
+void exact_sums_prepare(ExactLeaderSums& x, const double* lam_i, const double* mu_i, int32_t n_rows, int32_t nu,
+                        uint32_t emin_biased, Allocator& al, cudaStream_t s);
+// Group sums over all m edge keys, which are sorted by their low bf bits (the follower).
+void exact_sums_groups(ExactLeaderSums& x, const uint64_t* keys, int64_t m, int bf, int32_t nu, cudaStream_t s);
+// sigma, beta (FP64, rounded once) and the number of distinct leaders of every gathered user,
+// stored at its internal id (gathered index g < nX: g; otherwise g + nR).
+void exact_sums_finish(ExactLeaderSums& x, int32_t nu, int32_t nX, int32_t nR, double* sigma, double* beta,
+                       int32_t* n_leaders, cudaStream_t s);
+
+}  // namespace psi

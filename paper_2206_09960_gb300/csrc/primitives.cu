@@ -95,7 +95,8 @@ __device__ __forceinline__ uint32_t digit_peers_ballot(int d) {
 
 template <typename K>
 __global__ void __launch_bounds__(kRsThreads) k_radix_histo(const K* __restrict__ keys, int64_t n, int shift,
-                                                           int64_t num_tiles, uint32_t* __restrict__ counts) {
+                                                           uint32_t mask, int64_t num_tiles,
+                                                           uint32_t* __restrict__ counts) {
   __shared__ uint32_t h[kRsWarps][256];  // one sub-histogram per warp: contention stays inside a warp
   for (int i = threadIdx.x; i < kRsWarps * 256; i += kRsThreads) (&h[0][0])[i] = 0;
   __syncthreads();
@@ -104,7 +105,7 @@ __global__ void __launch_bounds__(kRsThreads) k_radix_histo(const K* __restrict_
 #pragma unroll 4
   for (int i = 0; i < kRsItems; ++i) {
     int64_t idx = base + (int64_t)i * kRsThreads + threadIdx.x;
-    if (idx < n) atomicAdd(&h[warp][(uint32_t)(keys[idx] >> shift) & 0xFFu], 1u);
+    if (idx < n) atomicAdd(&h[warp][(uint32_t)(keys[idx] >> shift) & mask], 1u);
   }
   __syncthreads();
   uint32_t t = 0;
@@ -119,7 +120,8 @@ __global__ void __launch_bounds__(kRsThreads) k_radix_histo(const K* __restrict_
 template <typename K, bool VALS>
 __global__ void __launch_bounds__(kRsThreads) k_radix_scatter(const K* __restrict__ keys, const uint32_t* __restrict__ vals,
                                                              K* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
-                                                             int64_t n, int shift, int64_t num_tiles,
+                                                             int64_t n, int shift, uint32_t mask,
+                                                             int64_t num_tiles,
                                                              const uint32_t* __restrict__ offsets) {
   extern __shared__ __align__(16) unsigned char rs_dyn[];
   K* sk = reinterpret_cast<K*>(rs_dyn);
@@ -144,9 +146,10 @@ __global__ void __launch_bounds__(kRsThreads) k_radix_scatter(const K* __restric
     bool ok = idx < n;
     k[r] = ok ? keys[idx] : K(0);
     if (VALS) v[r] = ok ? vals[idx] : 0u;
-    // a key past the end takes digit 255: such keys are a suffix of the tile in ranking
-    // order, so they sort to the end of the tile's buffer and are never written out
-    const int d = ok ? (int)((uint32_t)(k[r] >> shift) & 0xFFu) : 255;
+    // a key past the end takes digit 255 (above every digit of a pass, mask <= 255): such
+    // keys are a suffix of the tile in ranking order, so they sort to the end of the tile's
+    // buffer and are never written out
+    const int d = ok ? (int)((uint32_t)(k[r] >> shift) & mask) : 255;
     const uint32_t peers = (kRsMatchEvery > 0 && r % kRsMatchEvery == 0) ? __match_any_sync(0xffffffffu, d)
                                                                           : digit_peers_ballot(d);
     uint32_t before = wh[warp][d];
@@ -191,7 +194,7 @@ __global__ void __launch_bounds__(kRsThreads) k_radix_scatter(const K* __restric
   const int valid = rem < kRsTile ? (int)rem : kRsTile;
   for (int i = threadIdx.x; i < valid; i += kRsThreads) {
     const K key = sk[i];
-    const int d = (int)((uint32_t)(key >> shift) & 0xFFu);
+    const int d = (int)((uint32_t)(key >> shift) & mask);
     const uint32_t o = tile_base[d] + (uint32_t)i - dstart[d];
     keys_out[o] = key;
     if (VALS) vals_out[o] = sv[i];
@@ -199,15 +202,16 @@ __global__ void __launch_bounds__(kRsThreads) k_radix_scatter(const K* __restric
 }
 
 template <typename K, bool VALS>
-void launch_scatter(const K* src, const uint32_t* vsrc, K* dst, uint32_t* vdst, int64_t n, int shift, int64_t tiles,
-                    const uint32_t* offsets, cudaStream_t s) {
+void launch_scatter(const K* src, const uint32_t* vsrc, K* dst, uint32_t* vdst, int64_t n, int shift, uint32_t mask,
+                    int64_t tiles, const uint32_t* offsets, cudaStream_t s) {
   const size_t dyn = (size_t)kRsTile * (sizeof(K) + (VALS ? sizeof(uint32_t) : 0));
   static bool configured = false;
   if (!configured) {
     PSI_CUDA(cudaFuncSetAttribute(k_radix_scatter<K, VALS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
     configured = true;
   }
-  k_radix_scatter<K, VALS><<<(unsigned)tiles, kRsThreads, dyn, s>>>(src, vsrc, dst, vdst, n, shift, tiles, offsets);
+  k_radix_scatter<K, VALS><<<(unsigned)tiles, kRsThreads, dyn, s>>>(src, vsrc, dst, vdst, n, shift, mask, tiles,
+                                                                     offsets);
   PSI_LAUNCHED();
 }
 
@@ -254,7 +258,13 @@ void exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, Allocator&
 template <typename K>
 bool radix_sort(K* keys, K* keys_alt, uint32_t* vals, uint32_t* vals_alt, int64_t n, int bits, Allocator& al,
                 cudaStream_t s, const K* keys_in, const uint32_t* vals_in) {
-  if (n <= 1 || bits <= 0) {
+  return radix_sort_bits(keys, keys_alt, vals, vals_alt, n, 0, bits, al, s, keys_in, vals_in);
+}
+
+template <typename K>
+bool radix_sort_bits(K* keys, K* keys_alt, uint32_t* vals, uint32_t* vals_alt, int64_t n, int lo, int hi,
+                     Allocator& al, cudaStream_t s, const K* keys_in, const uint32_t* vals_in) {
+  if (n <= 1 || hi <= lo) {
     if (keys_in && n > 0) PSI_CUDA(cudaMemcpyAsync(keys, keys_in, sizeof(K) * n, cudaMemcpyDeviceToDevice, s));
     if (vals && vals_in && n > 0)
       PSI_CUDA(cudaMemcpyAsync(vals, vals_in, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
@@ -268,13 +278,14 @@ bool radix_sort(K* keys, K* keys_alt, uint32_t* vals, uint32_t* vals_alt, int64_
   uint32_t* vsrc = vals_in ? const_cast<uint32_t*>(vals_in) : vals;
   uint32_t* vdst = vals_alt;
   bool flipped = false;
-  for (int shift = 0; shift < bits; shift += 8) {
-    k_radix_histo<K><<<(unsigned)tiles, kRsThreads, 0, s>>>(src, n, shift, tiles, counts.get());
+  for (int shift = lo; shift < hi; shift += 8) {
+    const uint32_t mask = hi - shift >= 8 ? 0xFFu : (1u << (hi - shift)) - 1u;  // bits at or above hi stay out
+    k_radix_histo<K><<<(unsigned)tiles, kRsThreads, 0, s>>>(src, n, shift, mask, tiles, counts.get());
     PSI_LAUNCHED();
     exclusive_scan_u32(counts.get(), counts.get(), tiles * 256, al, s, nullptr);
-    if (vals) launch_scatter<K, true>(src, vsrc, dst, vdst, n, shift, tiles, counts.get(), s);
-    else launch_scatter<K, false>(src, nullptr, dst, nullptr, n, shift, tiles, counts.get(), s);
-    if (shift == 0 && keys_in) {  // from now on the two buffers alternate
+    if (vals) launch_scatter<K, true>(src, vsrc, dst, vdst, n, shift, mask, tiles, counts.get(), s);
+    else launch_scatter<K, false>(src, nullptr, dst, nullptr, n, shift, mask, tiles, counts.get(), s);
+    if (shift == lo && keys_in) {  // from now on the two buffers alternate
       src = keys;
       vsrc = vals;
     }
@@ -289,6 +300,8 @@ template bool radix_sort<uint32_t>(uint32_t*, uint32_t*, uint32_t*, uint32_t*, i
                                    const uint32_t*, const uint32_t*);
 template bool radix_sort<uint64_t>(uint64_t*, uint64_t*, uint32_t*, uint32_t*, int64_t, int, Allocator&, cudaStream_t,
                                    const uint64_t*, const uint32_t*);
+template bool radix_sort_bits<uint64_t>(uint64_t*, uint64_t*, uint32_t*, uint32_t*, int64_t, int, int, Allocator&,
+                                        cudaStream_t, const uint64_t*, const uint32_t*);
 
 void sum_f64(const double* x, int64_t n, double* d_out, Allocator& al, cudaStream_t s) {
   DBuf<double> part(al, kSumBlocks);

@@ -20,6 +20,13 @@ template <typename K>
 bool radix_sort(K* keys, K* keys_alt, uint32_t* vals, uint32_t* vals_alt, int64_t n, int bits,
                 Allocator& al, cudaStream_t s, const K* keys_in = nullptr, const uint32_t* vals_in = nullptr);
 
+// The same sort on key bits [lo, hi) only (passes of 8 bits from lo, the last one
+// narrower): sorting [0, b) and then [b, hi) gives the sort on [0, hi), and between the two
+// calls the data is in the order of bits [0, b).
+template <typename K>
+bool radix_sort_bits(K* keys, K* keys_alt, uint32_t* vals, uint32_t* vals_alt, int64_t n, int lo, int hi,
+                     Allocator& al, cudaStream_t s, const K* keys_in = nullptr, const uint32_t* vals_in = nullptr);
+
 // Deterministic FP64 sum of n values (fixed order for a given n) into *d_out.
 void sum_f64(const double* x, int64_t n, double* d_out, Allocator& al, cudaStream_t s);
 
