@@ -25,21 +25,31 @@ struct __align__(32) FixedRow {
   unsigned long long s_lo, s_hi, b_lo, b_hi;
 };
 
-// 128-bit add into (lo, hi) words in device memory, exact under any interleaving: the low
-// word's atomic returns the value it added to, so the carry out of that very addition goes
-// to the high word
-__device__ __forceinline__ void atomic_add128(unsigned long long* p, unsigned long long lo, unsigned long long hi) {
-  const unsigned long long old = atomicAdd(p, lo);
-  const unsigned long long carry = old + lo < old ? 1ull : 0ull;
-  if (hi + carry) atomicAdd(p + 1, hi + carry);
+// Group sums are kept as four counters of 32-bit limbs (value = sum_k c_k 2^(32k)), so every
+// update is a plain atomic add without a returned value.  The graph has fewer than 2^31 edges,
+// so a counter (at most one limb below 2^32 per edge added, one per repeated edge subtracted)
+// stays within +-2^63 and is read back as a signed integer (leader_sums.cu).
+__device__ __forceinline__ void red_add_u64(unsigned long long* p, unsigned long long v) {
+  if (v) atomicAdd(p, v);
+}
+__device__ __forceinline__ void red_limbs(unsigned long long* c, unsigned long long lo, unsigned long long hi) {
+  red_add_u64(c, lo & 0xFFFFFFFFull);
+  red_add_u64(c + 1, lo >> 32);
+  red_add_u64(c + 2, hi & 0xFFFFFFFFull);
+  red_add_u64(c + 3, hi >> 32);
+}
+// minus a value below 2^96 (one row): each limb counter takes 2^64 - limb
+__device__ __forceinline__ void red_sub_limbs(unsigned long long* c, unsigned long long lo, unsigned long long hi) {
+  red_add_u64(c, 0ull - (lo & 0xFFFFFFFFull));
+  red_add_u64(c + 1, 0ull - (lo >> 32));
+  red_add_u64(c + 2, 0ull - (hi & 0xFFFFFFFFull));
 }
 
-// subtract one leader row's (s, b) and one count from follower group g (modulo 2^128: the
-// final sums are non-negative, so the wrap-around is exact)
+// take one leader row's (s, b) and one count back out of follower group g
 __device__ __forceinline__ void fixed_sub_row(const FixedRow& v, unsigned long long* acc_s, unsigned long long* acc_b,
                                               uint32_t* acc_c, uint32_t g) {
-  atomic_add128(acc_s + 2 * (size_t)g, ~v.s_lo + 1ull, ~v.s_hi + (v.s_lo == 0 ? 1ull : 0ull));
-  atomic_add128(acc_b + 2 * (size_t)g, ~v.b_lo + 1ull, ~v.b_hi + (v.b_lo == 0 ? 1ull : 0ull));
+  red_sub_limbs(acc_s + 4 * (size_t)g, v.s_lo, v.s_hi);
+  red_sub_limbs(acc_b + 4 * (size_t)g, v.b_lo, v.b_hi);
   atomicSub(acc_c + g, 1u);
 }
 
@@ -54,7 +64,7 @@ __device__ __forceinline__ FixedRow ld_fixed_row(const FixedRow* p) {
 // The exact-sum state of one build.
 struct ExactLeaderSums {
   DBuf<FixedRow> rows;           // [n_rows]
-  DBuf<unsigned long long> s, b;  // [2 * nu]: (lo, hi) per follower group
+  DBuf<unsigned long long> s, b;  // [4 * nu]: limb counters per follower group
   DBuf<uint32_t> cnt;             // [nu]: distinct leaders
   int ebase = 0;
 };
@@ -66,8 +76,11 @@ bool exact_sums_apply(uint32_t emin_biased, uint32_t emax_biased);
 // Fixed-point rows of the leaders (internal order), zeroed group sums.
 void exact_sums_prepare(ExactLeaderSums& x, const double* lam_i, const double* mu_i, int32_t n_rows, int32_t nu,
                         uint32_t emin_biased, Allocator& al, cudaStream_t s);
-// Group sums over all m edge keys, which are sorted by their low bf bits (the follower).
-void exact_sums_groups(ExactLeaderSums& x, const uint64_t* keys, int64_t m, int bf, int32_t nu, cudaStream_t s);
+// Group sums over all m edge keys, which are sorted by their low bf bits (the follower); also
+// the per-tile counts of the next sort digit ((key >> bf) & next_mask) into next_counts, in
+// the layout radix_sort_bits takes as first_counts.
+void exact_sums_groups(ExactLeaderSums& x, const uint64_t* keys, int64_t m, int bf, int32_t nu, uint32_t next_mask,
+                       uint32_t* next_counts, cudaStream_t s);
 // sigma, beta (FP64, rounded once) and the number of distinct leaders of every gathered user,
 // stored at its internal id (gathered index g < nX: g; otherwise g + nR).
 void exact_sums_finish(ExactLeaderSums& x, int32_t nu, int32_t nX, int32_t nR, double* sigma, double* beta,

@@ -73,6 +73,7 @@ constexpr int kRsThreads = 256;
 constexpr int kRsWarps = kRsThreads / 32;
 constexpr int kRsItems = 12;                    // measured: 12 beats 8 and 16 on the 537M-key edge sort
 constexpr int kRsTile = kRsThreads * kRsItems;  // 3072 keys per tile
+static_assert(kRsTile == kRadixTileKeys, "the tile of the published first-pass counts");
 constexpr int kRsPerWarp = 32 * kRsItems;       // 384 consecutive keys per warp
 
 // Lanes of the warp holding the same 8-bit digit.  Ballots (one per digit bit: the lanes
@@ -258,12 +259,13 @@ void exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, Allocator&
 template <typename K>
 bool radix_sort(K* keys, K* keys_alt, uint32_t* vals, uint32_t* vals_alt, int64_t n, int bits, Allocator& al,
                 cudaStream_t s, const K* keys_in, const uint32_t* vals_in) {
-  return radix_sort_bits(keys, keys_alt, vals, vals_alt, n, 0, bits, al, s, keys_in, vals_in);
+  return radix_sort_bits(keys, keys_alt, vals, vals_alt, n, 0, bits, al, s, keys_in, vals_in, nullptr);
 }
 
 template <typename K>
 bool radix_sort_bits(K* keys, K* keys_alt, uint32_t* vals, uint32_t* vals_alt, int64_t n, int lo, int hi,
-                     Allocator& al, cudaStream_t s, const K* keys_in, const uint32_t* vals_in) {
+                     Allocator& al, cudaStream_t s, const K* keys_in, const uint32_t* vals_in,
+                     uint32_t* first_counts) {
   if (n <= 1 || hi <= lo) {
     if (keys_in && n > 0) PSI_CUDA(cudaMemcpyAsync(keys, keys_in, sizeof(K) * n, cudaMemcpyDeviceToDevice, s));
     if (vals && vals_in && n > 0)
@@ -271,7 +273,9 @@ bool radix_sort_bits(K* keys, K* keys_alt, uint32_t* vals, uint32_t* vals_alt, i
     return false;
   }
   const int64_t tiles = ceil_div(n, kRsTile);
-  DBuf<uint32_t> counts(al, (size_t)(tiles * 256));
+  DBuf<uint32_t> own;
+  if (!first_counts) own.reset(al, (size_t)(tiles * 256));
+  uint32_t* counts = first_counts ? first_counts : own.get();
   // the first pass reads the separate inputs when given (they are never written)
   K* src = keys_in ? const_cast<K*>(keys_in) : keys;
   K* dst = keys_alt;
@@ -280,11 +284,13 @@ bool radix_sort_bits(K* keys, K* keys_alt, uint32_t* vals, uint32_t* vals_alt, i
   bool flipped = false;
   for (int shift = lo; shift < hi; shift += 8) {
     const uint32_t mask = hi - shift >= 8 ? 0xFFu : (1u << (hi - shift)) - 1u;  // bits at or above hi stay out
-    k_radix_histo<K><<<(unsigned)tiles, kRsThreads, 0, s>>>(src, n, shift, mask, tiles, counts.get());
-    PSI_LAUNCHED();
-    exclusive_scan_u32(counts.get(), counts.get(), tiles * 256, al, s, nullptr);
-    if (vals) launch_scatter<K, true>(src, vsrc, dst, vdst, n, shift, mask, tiles, counts.get(), s);
-    else launch_scatter<K, false>(src, nullptr, dst, nullptr, n, shift, mask, tiles, counts.get(), s);
+    if (shift != lo || !first_counts) {
+      k_radix_histo<K><<<(unsigned)tiles, kRsThreads, 0, s>>>(src, n, shift, mask, tiles, counts);
+      PSI_LAUNCHED();
+    }
+    exclusive_scan_u32(counts, counts, tiles * 256, al, s, nullptr);
+    if (vals) launch_scatter<K, true>(src, vsrc, dst, vdst, n, shift, mask, tiles, counts, s);
+    else launch_scatter<K, false>(src, nullptr, dst, nullptr, n, shift, mask, tiles, counts, s);
     if (shift == lo && keys_in) {  // from now on the two buffers alternate
       src = keys;
       vsrc = vals;
@@ -301,7 +307,7 @@ template bool radix_sort<uint32_t>(uint32_t*, uint32_t*, uint32_t*, uint32_t*, i
 template bool radix_sort<uint64_t>(uint64_t*, uint64_t*, uint32_t*, uint32_t*, int64_t, int, Allocator&, cudaStream_t,
                                    const uint64_t*, const uint32_t*);
 template bool radix_sort_bits<uint64_t>(uint64_t*, uint64_t*, uint32_t*, uint32_t*, int64_t, int, int, Allocator&,
-                                        cudaStream_t, const uint64_t*, const uint32_t*);
+                                        cudaStream_t, const uint64_t*, const uint32_t*, uint32_t*);
 
 void sum_f64(const double* x, int64_t n, double* d_out, Allocator& al, cudaStream_t s) {
   DBuf<double> part(al, kSumBlocks);
