@@ -224,54 +224,19 @@ __global__ void k_invert(const uint32_t* __restrict__ perm, int64_t n, int32_t* 
 
 // key = (leader row << bf) | follower's gathered index (X: its id, U: id - nR); a dropped
 // self-loop becomes the sentinel
-// One block per tile of kRadixTileKeys edges: the keys, and the tile's counts of the edge
-// sort's first digit (key & mask) at counts[digit * tiles + tile], so the sort skips its
-// first histogram pass.
-constexpr int kEkThreads = 256;
-constexpr int kEkItems = kRadixTileKeys / kEkThreads;
-static_assert(kEkItems * kEkThreads == kRadixTileKeys, "whole tiles");
-__global__ void __launch_bounds__(kEkThreads) k_edge_keys(const int32_t* __restrict__ f, const int32_t* __restrict__ l,
-                                                         int64_t m, const int32_t* __restrict__ inv, int32_t nX,
-                                                         int32_t nR, int bf, uint64_t sentinel, uint32_t mask,
-                                                         int64_t tiles, uint64_t* __restrict__ key,
-                                                         uint32_t* __restrict__ counts) {
-  __shared__ uint32_t h[kEkThreads / 32][256];
-  for (int i = threadIdx.x; i < (kEkThreads / 32) * 256; i += kEkThreads) (&h[0][0])[i] = 0;
-  __syncthreads();
-  const int warp = threadIdx.x >> 5;
-  const int64_t base = (int64_t)blockIdx.x * kRadixTileKeys + threadIdx.x;
-  int32_t a[kEkItems], c[kEkItems];
-#pragma unroll
-  for (int j = 0; j < kEkItems; ++j) {
-    const int64_t e = base + (int64_t)j * kEkThreads;
-    a[j] = e < m ? f[e] : 0;
-    c[j] = e < m ? l[e] : 0;
-  }
-  uint32_t fa[kEkItems], ic[kEkItems];  // all gathers of the tile issued before any use
-#pragma unroll
-  for (int j = 0; j < kEkItems; ++j) {
-    const bool gather = base + (int64_t)j * kEkThreads < m && a[j] != c[j];
-    fa[j] = gather ? (uint32_t)inv[a[j]] : 0u;
-    ic[j] = gather ? (uint32_t)inv[c[j]] : 0u;
-  }
-#pragma unroll
-  for (int j = 0; j < kEkItems; ++j) {
-    const int64_t e = base + (int64_t)j * kEkThreads;
-    if (e < m) {
-      uint64_t k = sentinel;
-      if (a[j] != c[j]) {
-        const uint32_t gi = fa[j] < (uint32_t)nX ? fa[j] : fa[j] - (uint32_t)nR;
-        k = ((uint64_t)ic[j] << bf) | (uint64_t)gi;
-      }
-      key[e] = k;
-      atomicAdd(&h[warp][(uint32_t)k & mask], 1u);
+__global__ void k_edge_keys(const int32_t* __restrict__ f, const int32_t* __restrict__ l, int64_t m,
+                            const int32_t* __restrict__ inv, int32_t nX, int32_t nR, int bf, uint64_t sentinel,
+                            uint64_t* __restrict__ key) {
+  grid_stride4(m, [&](int64_t e) {
+    const int32_t a = f[e], c = l[e];
+    if (a == c) {
+      key[e] = sentinel;
+    } else {
+      const uint32_t fi = (uint32_t)inv[a];
+      const uint32_t gi = fi < (uint32_t)nX ? fi : fi - (uint32_t)nR;
+      key[e] = ((uint64_t)(uint32_t)inv[c] << bf) | (uint64_t)gi;
     }
-  }
-  __syncthreads();
-  uint32_t t = 0;
-#pragma unroll
-  for (int w = 0; w < kEkThreads / 32; ++w) t += h[w][threadIdx.x];
-  counts[(int64_t)threadIdx.x * tiles + blockIdx.x] = t;
+  });
 }
 
 // Duplicate merge and CSR of the sorted edge keys as one stream compaction over tiles of
@@ -794,13 +759,8 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
     k_invert<<<grid_for(n), 256, 0, s>>>(perm32.get(), n, inv.get());
     PSI_LAUNCHED();
     DBuf<uint64_t> k0(al, (size_t)m), k1(al, (size_t)m);
-    const int64_t ek_tiles = ceil_div(m, kRadixTileKeys);
-    DBuf<uint32_t> first_counts(al, (size_t)(ek_tiles > 0 ? ek_tiles : 1) * 256);
-    const int sort_hi = exact ? bf : bl + bf;  // the first sort call's bit range is [0, sort_hi)
     if (m > 0) {
-      k_edge_keys<<<(unsigned)ek_tiles, kEkThreads, 0, s>>>(df, dl, m, inv.get(), g.nX, g.nR, bf, sentinel,
-                                                           radix_first_mask(0, sort_hi), ek_tiles, k0.get(),
-                                                           first_counts.get());
+      k_edge_keys<<<grid_for(m), 256, 0, s>>>(df, dl, m, inv.get(), g.nX, g.nR, bf, sentinel, k0.get());
       PSI_LAUNCHED();
     }
     inv.release();
@@ -808,16 +768,16 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
     lbuf.release();
     bool alt;
     if (exact) {  // the follower field first; between the two halves the keys are grouped by follower
-      const bool a1 = radix_sort_bits<uint64_t>(k0.get(), k1.get(), nullptr, nullptr, m, 0, bf, al, s, nullptr,
-                                                nullptr, first_counts.get());
+      const bool a1 = radix_sort_bits<uint64_t>(k0.get(), k1.get(), nullptr, nullptr, m, 0, bf, al, s);
       uint64_t* mid = a1 ? k1.get() : k0.get();
+      // the group sums also count the digit of the sort's next pass
+      DBuf<uint32_t> first_counts(al, (size_t)ceil_div(m, kRadixTileKeys) * 256);
       exact_sums_groups(xs, mid, m, bf, (int32_t)nu, radix_first_mask(bf, bf + bl), first_counts.get(), s);
       const bool a2 = radix_sort_bits<uint64_t>(mid, a1 ? k0.get() : k1.get(), nullptr, nullptr, m, bf, bf + bl, al, s,
                                                 nullptr, nullptr, first_counts.get());
       alt = a1 != a2;
     } else {
-      alt = radix_sort_bits<uint64_t>(k0.get(), k1.get(), nullptr, nullptr, m, 0, bl + bf, al, s, nullptr, nullptr,
-                                      first_counts.get());
+      alt = radix_sort<uint64_t>(k0.get(), k1.get(), nullptr, nullptr, m, bl + bf, al, s);
     }
     const uint64_t* keys = alt ? k1.get() : k0.get();
     const int64_t uq_tiles = ceil_div(m, kUqTile);
