@@ -249,7 +249,9 @@ constexpr int kUqItems = 16;
 constexpr int kUqTile = kUqThreads * kUqItems;
 
 // With exact leader sums (DUPS): every repeat of a key takes its leader's rates and one count
-// back out of its follower's sums, which counted all edges.
+// back out of its follower's sums, which counted all edges.  Repeats of one key are adjacent:
+// the lanes of a warp holding the same repeated key subtract once, times their number (a pair
+// repeated hundreds of times would otherwise queue hundreds of atomics on one address).
 template <bool DUPS>
 __global__ void __launch_bounds__(kUqThreads) k_unique_count(const uint64_t* __restrict__ key, int64_t m,
                                                              uint64_t sentinel, uint32_t* __restrict__ count, int bf,
@@ -257,19 +259,25 @@ __global__ void __launch_bounds__(kUqThreads) k_unique_count(const uint64_t* __r
                                                              unsigned long long* acc_s, unsigned long long* acc_b,
                                                              uint32_t* acc_c) {
   const int64_t base = (int64_t)blockIdx.x * kUqTile;
+  const int lane = threadIdx.x & 31;
   uint32_t c = 0;
 #pragma unroll 4
   for (int j = 0; j < kUqItems; ++j) {
     const int64_t e = base + (int64_t)j * kUqThreads + threadIdx.x;
+    bool dup = false;
+    uint64_t k = sentinel;
     if (e < m) {
-      const uint64_t k = key[e];
+      k = key[e];
       if (k != sentinel) {
-        if (e == 0 || key[e - 1] != k) {
-          ++c;
-        } else if (DUPS) {
-          fixed_sub_row(ld_fixed_row(rows + (k >> bf)), acc_s, acc_b, acc_c, (uint32_t)(k & ((1ull << bf) - 1)));
-        }
+        if (e == 0 || key[e - 1] != k) ++c;
+        else dup = DUPS;
       }
+    }
+    if (DUPS && __any_sync(0xffffffffu, dup)) {
+      const uint32_t peers = __match_any_sync(0xffffffffu, dup ? k : ~(uint64_t)lane);  // repeats of my key
+      if (dup && __ffs(peers) - 1 == lane)
+        fixed_sub_rows(ld_fixed_row(rows + (k >> bf)), (uint32_t)__popc(peers), acc_s, acc_b, acc_c,
+                       (uint32_t)(k & ((1ull << bf) - 1)));
     }
   }
   c = block_sum(c);

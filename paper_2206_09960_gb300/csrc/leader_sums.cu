@@ -103,7 +103,7 @@ __device__ __forceinline__ void st_limbs(unsigned long long* c, const U128& x) {
 }
 
 // The limb counters c_0..c_3 of a group as one 128-bit value.  A counter holds limbs of run
-// sums minus limbs of single rows, so on its own it can end below zero (carries between limbs
+// sums minus limbs of repeated rows, so on its own it can end below zero (carries between limbs
 // differ); with fewer than 2^31 edges per group it stays within +-2^63, so each counter is
 // read as a signed integer and sign-extended: the sum modulo 2^128 is the exact sum.
 __device__ __forceinline__ U128 from_limbs(const unsigned long long* c) {

@@ -27,8 +27,8 @@ struct __align__(32) FixedRow {
 
 // Group sums are kept as four counters of 32-bit limbs (value = sum_k c_k 2^(32k)), so every
 // update is a plain atomic add without a returned value.  The graph has fewer than 2^31 edges,
-// so a counter (at most one limb below 2^32 per edge added, one per repeated edge subtracted)
-// stays within +-2^63 and is read back as a signed integer (leader_sums.cu).
+// so a counter (at most one limb below 2^32 added or subtracted per edge) stays within +-2^63
+// and is read back as a signed integer (leader_sums.cu).
 __device__ __forceinline__ void red_add_u64(unsigned long long* p, unsigned long long v) {
   if (v) atomicAdd(p, v);
 }
@@ -38,19 +38,21 @@ __device__ __forceinline__ void red_limbs(unsigned long long* c, unsigned long l
   red_add_u64(c + 2, hi & 0xFFFFFFFFull);
   red_add_u64(c + 3, hi >> 32);
 }
-// minus a value below 2^96 (one row): each limb counter takes 2^64 - limb
+// minus a 128-bit value: each limb counter takes 2^64 - limb
 __device__ __forceinline__ void red_sub_limbs(unsigned long long* c, unsigned long long lo, unsigned long long hi) {
   red_add_u64(c, 0ull - (lo & 0xFFFFFFFFull));
   red_add_u64(c + 1, 0ull - (lo >> 32));
   red_add_u64(c + 2, 0ull - (hi & 0xFFFFFFFFull));
+  red_add_u64(c + 3, 0ull - (hi >> 32));
 }
 
-// take one leader row's (s, b) and one count back out of follower group g
-__device__ __forceinline__ void fixed_sub_row(const FixedRow& v, unsigned long long* acc_s, unsigned long long* acc_b,
-                                              uint32_t* acc_c, uint32_t g) {
-  red_sub_limbs(acc_s + 4 * (size_t)g, v.s_lo, v.s_hi);
-  red_sub_limbs(acc_b + 4 * (size_t)g, v.b_lo, v.b_hi);
-  atomicSub(acc_c + g, 1u);
+// take t copies of one leader row's (s, b) and t counts back out of follower group g (a row
+// value is below 2^94 and t below 2^32, so the products fit 128 bits)
+__device__ __forceinline__ void fixed_sub_rows(const FixedRow& v, uint32_t t, unsigned long long* acc_s,
+                                               unsigned long long* acc_b, uint32_t* acc_c, uint32_t g) {
+  red_sub_limbs(acc_s + 4 * (size_t)g, v.s_lo * t, v.s_hi * t + __umul64hi(v.s_lo, t));
+  red_sub_limbs(acc_b + 4 * (size_t)g, v.b_lo * t, v.b_hi * t + __umul64hi(v.b_lo, t));
+  atomicSub(acc_c + g, t);
 }
 
 __device__ __forceinline__ FixedRow ld_fixed_row(const FixedRow* p) {
