@@ -35,29 +35,43 @@ __global__ void k_nf_init(const int32_t* __restrict__ fptr, const int32_t* __res
 }
 
 // one step of every active origin: Pn[j][i] = sum_{k in L(j)} a_jk P[k][i] + b_ji, and
-// part[j][i] = |Pn[j][i] - P[j][i]|; frozen origins copy their column
-__global__ void k_nf_step(const int32_t* __restrict__ fptr, const int32_t* __restrict__ lead,
-                          const double* __restrict__ a, const double* __restrict__ b, const int32_t* __restrict__ active,
-                          int64_t n, const double* __restrict__ P, double* __restrict__ Pn, double* __restrict__ part) {
+// part[j][i] = |Pn[j][i] - P[j][i]|; frozen origins copy their column.  Block (j, column
+// tile), one column per thread; the leaders' rows are loaded kNfUnroll at a time so that
+// the loads overlap, and summed in the graph's order.
+constexpr int kNfThreads = 256;
+constexpr int kNfUnroll = 8;
+__global__ void __launch_bounds__(kNfThreads) k_nf_step(const int32_t* __restrict__ fptr,
+                                                        const int32_t* __restrict__ lead, const double* __restrict__ a,
+                                                        const double* __restrict__ b,
+                                                        const int32_t* __restrict__ active, int64_t n,
+                                                        const double* __restrict__ P, double* __restrict__ Pn,
+                                                        double* __restrict__ part) {
   const int64_t j = blockIdx.x;
-  const int32_t e0 = fptr[j], e1 = fptr[j + 1];
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-    const double old = P[j * n + i];
-    if (!active[i]) {
-      Pn[j * n + i] = old;
-      part[j * n + i] = 0.0;
-      continue;
-    }
-    double acc = 0.0, bji = 0.0;
-    for (int32_t e = e0; e < e1; ++e) {
-      const int32_t k = lead[e];
-      acc += a[e] * P[(int64_t)k * n + i];
-      if (k == i) bji = b[e];
-    }
-    const double v = acc + bji;
-    Pn[j * n + i] = v;
-    part[j * n + i] = fabs(v - old);
+  const int64_t i = (int64_t)blockIdx.y * kNfThreads + threadIdx.x;
+  if (i >= n) return;
+  const double old = P[j * n + i];
+  if (!active[i]) {
+    Pn[j * n + i] = old;
+    part[j * n + i] = 0.0;
+    return;
   }
+  const int32_t e0 = fptr[j], e1 = fptr[j + 1];
+  double acc = 0.0, bji = 0.0;
+  for (int32_t e = e0; e < e1; e += kNfUnroll) {
+    double x[kNfUnroll];
+#pragma unroll
+    for (int q = 0; q < kNfUnroll; ++q) x[q] = e + q < e1 ? P[(int64_t)lead[e + q] * n + i] : 0.0;
+#pragma unroll
+    for (int q = 0; q < kNfUnroll; ++q) {
+      if (e + q < e1) {
+        acc += a[e + q] * x[q];
+        if (lead[e + q] == i) bji = b[e + q];
+      }
+    }
+  }
+  const double v = acc + bji;
+  Pn[j * n + i] = v;
+  part[j * n + i] = fabs(v - old);
 }
 
 // gap of every active origin (rows in order), its step count and stop test; active_count
@@ -168,8 +182,8 @@ psi_status power_nf(Graph& g, double eps, int32_t max_iter, double* psi_out, psi
   // every origin steps at most max_iter times, so max_iter launches end the loop
   while (iterate && t < max_iter) {
     PSI_CUDA(cudaMemsetAsync(cnt.get(), 0, sizeof(int32_t), s));
-    k_nf_step<<<(unsigned)n, 128, 0, s>>>(dptr.get(), dlead.get(), da.get(), db.get(), active.get(), n, cur, nxt,
-                                          part.get());
+    k_nf_step<<<dim3((unsigned)n, (unsigned)ceil_div(n, kNfThreads)), kNfThreads, 0, s>>>(
+        dptr.get(), dlead.get(), da.get(), db.get(), active.get(), n, cur, nxt, part.get());
     PSI_LAUNCHED();
     k_nf_gap<<<nf_grid(n), 256, 0, s>>>(part.get(), n, eps, max_iter, active.get(), steps.get(), gap.get(),
                                         conv.get(), cnt.get());
