@@ -161,6 +161,27 @@ def oracle_seconds(w, eps, threads=None):
     return sec, out, used
 
 
+def sampled_cpu_baseline(cases, scale, sample, threads=None):
+    """The oracle as it stands (canonicalise, explicit A/B, Algorithm 2, top-100) on a bounded
+    sample of a secondary workload: `cases` are (workload dict, eps, tol_mode) solved one
+    after another on the host cores; the line's value is their seconds times `scale` (the
+    sample's share of the workload), stated in `sample`."""
+    import oracle
+
+    if threads:
+        oracle.set_threads(threads)
+    used = oracle.num_threads()
+    t = time.perf_counter()
+    for w, eps, tol in cases:
+        out = oracle.solve(w["n"], w["follower"], w["leader"], w["lam"], w["mu"], eps=eps, tol_mode=tol)
+        oracle.topk(out["psi"], 100)
+    sec = time.perf_counter() - t
+    if threads:
+        oracle.set_threads(os.cpu_count() or 1)
+    return {"value": sec * scale, "unit": "s", "cores": used, "kind": "oracle", "sample": sample,
+            "measured_s": sec, "scaled_by": scale}
+
+
 def oracle_bytes(n, draws):
     """Host memory the oracle needs for a graph: the sort keys (8 B per draw), both explicit
     CSR copies of A and B (two ids and four FP64 values per edge) and its per-user vectors."""
@@ -402,6 +423,13 @@ def run_batch(args, S=64, plain_sample=8):
             "batch_solve_s": solve_batch, "plain_s_for_64": t_plain_all, "plain_solve_s_for_64": solve_plain,
             "speedup_total": t_plain_all / t_batch, "speedup_solve": solve_plain / solve_batch,
             "plain_sample": plain_sample, "clocks": clk, "roofline": roofline}
+    if not args.no_cpu_baseline:  # one scenario of the 64 through the oracle, scaled by 64
+        import oracle
+
+        w0 = dict(n=n, follower=f, leader=l, lam=lam[0], mu=mu[0])
+        line["cpu_baseline"] = sampled_cpu_baseline(
+            [(w0, args.eps, oracle.TOL_PSI)], S, f"scenario 0 of {S} on the same graph, oracle solve to eps, "
+                                               f"times {S}")
     print(json.dumps(line), flush=True)
 
 
@@ -498,6 +526,18 @@ def run_multi(args, G=256, plain_sample=32):
             "plain_sample": len(sample), "gpu_launches": launches, "build_ms": st["build_ms"], "clocks": clk,
             "spmv_tile": st["spmv_tile"],
             "roofline": multi_roofline(st, solve_multi, iters)}
+    if not args.no_cpu_baseline:  # every 32nd graph through the oracle, scaled by its share of the edges
+        import oracle
+
+        cases, m_s = [], 0
+        for q in range(0, G, 32):
+            cases.append((dict(n=int(n_g[q]), follower=w["follower"][eo[q]:eo[q + 1]],
+                               leader=w["leader"][eo[q]:eo[q + 1]], lam=w["lam"][no[q]:no[q + 1]],
+                               mu=w["mu"][no[q]:no[q + 1]]), args.eps, oracle.TOL_PSI))
+            m_s += int(m_g[q])
+        line["cpu_baseline"] = sampled_cpu_baseline(
+            cases, float(m_g.sum()) / max(m_s, 1), f"{len(cases)} of {G} graphs (every 32nd), oracle solve "
+                                                   "to eps each, scaled by their share of the edge draws")
     print(json.dumps(line), flush=True)
 
 
@@ -566,6 +606,14 @@ def run_pagerank(args, alpha=0.85, eps=1e-9):
             "psi_homogeneous_s": out["psi_homogeneous"][0],
             "psi_homogeneous_iters": out["psi_homogeneous"][1]["iters"],
             "homogeneous_psi_vs_pagerank_rel_l1": diff, "clocks": clk, "roofline": roofline}
+    if not args.no_cpu_baseline:  # the heterogeneous Power-psi solve on a scale-20 graph of the recipe
+        import oracle
+
+        ws = psigen.workload("rmat", seed=args.seed, scale=20)
+        line["cpu_baseline"] = sampled_cpu_baseline(
+            [(ws, eps, oracle.TOL_S_ABS)], float(n) / ws["n"],
+            "R-MAT scale 20 of the same recipe (2^-5 of the edges), oracle Power-psi to the same eps on the "
+            "s-tolerance, scaled by the edge ratio 32")
     print(json.dumps(line), flush=True)
 
 

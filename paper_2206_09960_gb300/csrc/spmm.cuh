@@ -39,26 +39,32 @@ struct SpmmArgs {
 };
 
 // Series step for S scenarios: t = mu_s * y_s, s_s += t (FP64), v_s = t / sigma_s.
+// Every epilogue loads a row's operands in pre(), issued when the warp starts the row, so
+// that they arrive while its gathers are summed; row() applies them at the row's end.
 struct EpiSeriesS {
   const float2* mu;     // [users][S/2]
   const float2* isig;
   double2* s64;         // [users][S/2] as double pairs
   float2* v_new;        // [gathered][S/2]
   int32_t nX;
-  __device__ __forceinline__ void row(int32_t r, int lane, float2 y, const int* act, double2& gap) const {
+  struct Pre {
+    float2 m, is;
+    double2 s;
+  };
+  __device__ __forceinline__ Pre pre(int32_t r, int lane) const {
     const int64_t o = (int64_t)r * 32 + lane;
-    const float2 m = mu[o];
-    float2 t = make_float2(act[0] ? m.x * y.x : 0.f, act[1] ? m.y * y.y : 0.f);
-    double2 s = s64[o];
+    return Pre{mu[o], r < nX ? isig[o] : make_float2(0.f, 0.f), s64[o]};
+  }
+  __device__ __forceinline__ void row(int32_t r, int lane, float2 y, const int* act, double2& gap, const Pre& p) const {
+    const int64_t o = (int64_t)r * 32 + lane;
+    float2 t = make_float2(act[0] ? p.m.x * y.x : 0.f, act[1] ? p.m.y * y.y : 0.f);
+    double2 s = p.s;
     s.x += (double)t.x;
     s.y += (double)t.y;
     s64[o] = s;
     gap.x += fabs((double)t.x);
     gap.y += fabs((double)t.y);
-    if (r < nX) {
-      const float2 is = isig[o];
-      v_new[o] = make_float2(t.x * is.x, t.y * is.y);
-    }
+    if (r < nX) v_new[o] = make_float2(t.x * p.is.x, t.y * p.is.y);
   }
 };
 
@@ -84,10 +90,17 @@ struct EpiResidS {
   V* u_new;
   float2* v32;
   int32_t nX;
-  __device__ __forceinline__ void row(int32_t r, int lane, V yp, const int* act, double2& gap) const {
+  struct Pre {
+    double2 cc, mm, s, is;
+  };
+  __device__ __forceinline__ Pre pre(int32_t r, int lane) const {
+    const int64_t o = (int64_t)r * 32 + lane;
+    return Pre{c[o], mu[o], s64[o], r < nX ? isig[o] : make_double2(0.0, 0.0)};
+  }
+  __device__ __forceinline__ void row(int32_t r, int lane, V yp, const int* act, double2& gap, const Pre& p) const {
     const int64_t o = (int64_t)r * 32 + lane;
     const double2 y = pair_value(yp);
-    const double2 cc = c[o], mm = mu[o], s = s64[o];
+    const double2 cc = p.cc, mm = p.mm, s = p.s;
     double2 sn = make_double2(cc.x + mm.x * y.x, cc.y + mm.y * y.y);
     if (!act[0]) sn.x = s.x;
     if (!act[1]) sn.y = s.y;
@@ -96,7 +109,7 @@ struct EpiResidS {
     gap.y += fabs(rr.y);
     s64[o] = sn;
     if (r < nX) {
-      const double2 is = isig[o];
+      const double2 is = p.is;
       u_new[o] = pair_gather<V>(sn.x * is.x, sn.y * is.y);
       v32[o] = make_float2((float)(rr.x * is.x), (float)(rr.y * is.y));
     }
@@ -110,11 +123,17 @@ struct EpiFinalS {
   const double2* d;
   double2* psi;
   double n;
-  __device__ __forceinline__ void row(int32_t r, int lane, V yp, const int*, double2&) const {
+  struct Pre {
+    double2 l, dd;
+  };
+  __device__ __forceinline__ Pre pre(int32_t r, int lane) const {
+    const int64_t o = (int64_t)r * 32 + lane;
+    return Pre{lam[o], d[o]};
+  }
+  __device__ __forceinline__ void row(int32_t r, int lane, V yp, const int*, double2&, const Pre& p) const {
     const int64_t o = (int64_t)r * 32 + lane;
     const double2 y = pair_value(yp);
-    const double2 l = lam[o], dd = d[o];
-    psi[o] = make_double2((l.x * y.x + dd.x) / n, (l.y * y.y + dd.y) / n);
+    psi[o] = make_double2((p.l.x * y.x + p.dd.x) / n, (p.l.y * y.y + p.dd.y) / n);
   }
 };
 
@@ -182,6 +201,7 @@ __global__ void __launch_bounds__(256) k_spmm(SpmmArgs a, const V* __restrict__ 
     int32_t r = a.chunk_row[c];
     const bool head_open = (int64_t)a.row_ptr[r] < p0;
     int64_t next_end = a.row_ptr[r + 1];
+    typename Epi::Pre pre = epi.pre(r, lane);
     bool first = true;
     V acc = zero2<V>();
     // col is padded to whole chunks with the zero entry, so groups of 8 never run short
@@ -200,11 +220,12 @@ __global__ void __launch_bounds__(256) k_spmm(SpmmArgs a, const V* __restrict__ 
           acc = add2(acc, x[i]);
           if (q + i0 + i + 1 == next_end) {  // row r ends at this nonzero (warp-uniform)
             if (first && head_open) ch[c * 32 + lane] = acc;
-            else epi.row(r, lane, acc, act, gap);
+            else epi.row(r, lane, acc, act, gap, pre);
             first = false;
             acc = zero2<V>();
             ++r;
             next_end = r < a.n_rows ? (int64_t)a.row_ptr[r + 1] : INT64_MAX;
+            if (r < a.n_rows) pre = epi.pre(r, lane);
           }
         }
       }
@@ -235,7 +256,7 @@ __global__ void __launch_bounds__(256) k_spmm_fixup(SpmmArgs a, const int32_t* _
 #pragma unroll 8
     for (int32_t k = cs; k < c; ++k) acc = add2(acc, ct[(int64_t)k * 32 + lane]);
     acc = add2(acc, ch[(int64_t)c * 32 + lane]);
-    epi.row(r, lane, acc, act, gap);
+    epi.row(r, lane, acc, act, gap, epi.pre(r, lane));
   }
   gap_fix[warp_id * a.S + 2 * lane] = gap.x;
   gap_fix[warp_id * a.S + 2 * lane + 1] = gap.y;

@@ -104,11 +104,11 @@ def train(x, t, steps=400, batch=1 << 16, lr=3e-3, seed=0, log_every=0):
     std = x.std(0).clamp_min(1e-3)
     norm = torch.cat([mean, std, t.mean().reshape(1), t.std().clamp_min(1e-3).reshape(1)]).cpu().numpy()
     model.set_params(norm=norm)
-    gen = torch.Generator(device="cpu").manual_seed(seed + 1)
+    gen = torch.Generator(device=x.device).manual_seed(seed + 1)  # minibatch rows drawn on the device
     losses = []
     n = x.shape[0]
     for k in range(steps):
-        idx = torch.randint(0, n, (min(batch, n),), generator=gen).to(x.device)
+        idx = torch.randint(0, n, (min(batch, n),), generator=gen, device=x.device)
         xb, tb = x[idx].contiguous(), t[idx].contiguous()
         loss = model.grad(xb, tb)
         model.step(lr * (0.5 * (1 + np.cos(np.pi * k / steps))) + 1e-5)
