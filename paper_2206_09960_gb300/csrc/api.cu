@@ -81,14 +81,13 @@ void Allocator::free(void* p, size_t bytes) {
 }
 
 int64_t num_sms() {
-  static int cached = 0;
-  if (!cached) {
+  static const int cached = [] {  // once, thread-safe
     int dev = 0;
     PSI_CUDA(cudaGetDevice(&dev));
     int v = 0;
     PSI_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev));
-    cached = v > 0 ? v : 1;
-  }
+    return v > 0 ? v : 1;
+  }();
   return cached;
 }
 

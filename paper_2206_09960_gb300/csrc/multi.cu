@@ -611,12 +611,11 @@ void multi_buffers(Multi& M) {
 
 template <typename T, typename Epi>
 int multi_spmv_grid(int tiles) {
-  static int per_sm = -1;
-  if (per_sm < 0) {
+  static const int per_sm = [] {  // once, thread-safe
     int b = 0;
     PSI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_spmv<T, Epi>, kSpmvThreads, 0));
-    per_sm = b > 0 ? b : 1;
-  }
+    return b > 0 ? b : 1;
+  }();
   return spmv_blocks(per_sm, tiles);
 }
 

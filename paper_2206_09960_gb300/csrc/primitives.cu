@@ -206,11 +206,11 @@ template <typename K, bool VALS>
 void launch_scatter(const K* src, const uint32_t* vsrc, K* dst, uint32_t* vdst, int64_t n, int shift, uint32_t mask,
                     int64_t tiles, const uint32_t* offsets, cudaStream_t s) {
   const size_t dyn = (size_t)kRsTile * (sizeof(K) + (VALS ? sizeof(uint32_t) : 0));
-  static bool configured = false;
-  if (!configured) {
+  static const bool configured = [dyn] {  // once, thread-safe (concurrent builds on several streams)
     PSI_CUDA(cudaFuncSetAttribute(k_radix_scatter<K, VALS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
-    configured = true;
-  }
+    return true;
+  }();
+  (void)configured;
   k_radix_scatter<K, VALS><<<(unsigned)tiles, kRsThreads, dyn, s>>>(src, vsrc, dst, vdst, n, shift, mask, tiles,
                                                                      offsets);
   PSI_LAUNCHED();

@@ -145,12 +145,11 @@ void fill(T* x, int64_t n, T v, cudaStream_t s) {
 
 template <typename T, typename Epi>
 int spmv_grid(int32_t tiles) {
-  static int per_sm = -1;
-  if (per_sm < 0) {
+  static const int per_sm = [] {  // once, thread-safe
     int b = 0;
     PSI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_spmv<T, Epi>, kSpmvThreads, 0));
-    per_sm = b > 0 ? b : 1;
-  }
+    return b > 0 ? b : 1;
+  }();
   return spmv_blocks(per_sm, tiles);
 }
 
@@ -159,12 +158,12 @@ constexpr int32_t kHotMax = 32768;  // largest shared-memory copy of the series 
 // One block per SM of the series product with a shared-memory copy (no more blocks than
 // the tiles fill)
 int hot_series_grid(int32_t tiles) {
-  static bool configured = false;
-  if (!configured) {
+  static const bool configured = [] {  // once, thread-safe
     PSI_CUDA(cudaFuncSetAttribute(k_spmv<float, EpiSeries, kSpmvHotWarps>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(float) * kHotMax)));
-    configured = true;
-  }
+    return true;
+  }();
+  (void)configured;
   const int64_t need = ceil_div(tiles > 0 ? tiles : 1, kSpmvHotWarps);
   return (int)(need < num_sms() ? need : num_sms());
 }

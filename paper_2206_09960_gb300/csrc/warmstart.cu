@@ -821,11 +821,11 @@ psi_status psi_mlp_grad(psi_mlp* h, int64_t rows, const float* x, const float* t
   }
   try {
     Mlp& m = h->m;
-    static bool configured = false;
-    if (!configured) {
+    static const bool configured = [] {  // once, thread-safe
       PSI_CUDA(cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(GradSmem)));
-      configured = true;
-    }
+      return true;
+    }();
+    (void)configured;
     k_mlp_grad<<<m.grid, 256, sizeof(GradSmem), m.stream>>>(m.wb.get(), m.norm.get(), rows, x, target, m.part.get(),
                                                             m.loss_part.get());
     PSI_LAUNCHED();

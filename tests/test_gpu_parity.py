@@ -452,3 +452,46 @@ def test_start_vector_is_c_to_an_ulp_for_any_rates():
     out = gpu_solve(n, f[keep], l[keep], lam, mu, 1e-8, max_iter=0, precision="fp64")
     want = mu / (lam + mu)
     np.testing.assert_allclose(out["s"], want, rtol=6.7e-16, atol=0)
+
+
+def test_graphs_on_two_streams_from_two_threads():
+    """Two host threads, each with its own stream, build and solve graphs at once through the
+    C ABI (host and device inputs; the bench's end-to-end mode): every result is bit-identical
+    to the same graph solved alone."""
+    import threading
+
+    torch = _torch()
+    from paper_2206_09960_gb300 import Graph
+
+    ws = [psigen.workload("rmat", seed=31 + i, scale=15) for i in range(2)]
+    alone = [gpu_solve(w["n"], w["follower"], w["leader"], w["lam"], w["mu"], 1e-8, on_device=(i == 0))
+             for i, w in enumerate(ws)]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    got = [[], []]
+    errors = []
+
+    def lane(i):
+        try:
+            w = ws[i]
+            args = [np.ascontiguousarray(w[k]) for k in ("follower", "leader", "lam", "mu")]
+            with torch.cuda.stream(streams[i]):
+                if i == 0:
+                    args = [torch.from_numpy(a).cuda() for a in args]
+                for _ in range(3):
+                    with Graph(w["n"], *args, stream=streams[i]) as g:
+                        g.solve(1e-8, 20000)
+                        got[i].append(g.scores().cpu().numpy())
+            streams[i].synchronize()
+        except Exception as exc:
+            errors.append(exc)
+
+    threads = [threading.Thread(target=lane, args=(i,)) for i in (0, 1)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
+    for i in (0, 1):
+        assert len(got[i]) == 3
+        for psi in got[i]:
+            np.testing.assert_array_equal(psi, alone[i]["psi"])
