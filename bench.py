@@ -916,7 +916,8 @@ def main():
         import threading
 
         quiesce_s, quiesce_moved = host_quiesce()
-        e_streams = [stream, torch.cuda.Stream()]
+        e_streams = [torch.cuda.Stream(), torch.cuda.Stream()]  # not the legacy default stream, which
+        # would wait for (and hold up) the other one
         e_out = [(ids_h, vals_h), (torch.empty(100, dtype=torch.int32).pin_memory(),
                                    torch.empty(100, dtype=torch.float64).pin_memory())]
 
