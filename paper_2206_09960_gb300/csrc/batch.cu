@@ -231,6 +231,7 @@ struct BatchHook final : BuildHook {
   const double* muS;
   explicit BatchHook(Batch& bb, const double* l, const double* m) : b(bb), lamS(l), muS(m) {}
 
+  bool follower_csr() const override { return true; }  // one product per scenario over it
   void on_follower_csr(Graph& g, const FollowerCsr& fc) override { form(g, &fc); }
 
   void form(Graph& g, const FollowerCsr* fc) {

@@ -755,7 +755,7 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
   DBuf<int32_t> li;
   // sigma and beta of a single graph as exact sums (leader_sums.cuh) when the rates allow:
   // formed from the keys half-way through the sort, no follower-grouped CSR
-  const bool exact = hook == nullptr && nu > 0 && m > 0 && m < ((int64_t)1 << 31) &&
+  const bool exact = (hook == nullptr || !hook->follower_csr()) && nu > 0 && m > 0 && m < ((int64_t)1 << 31) &&
                      exact_sums_apply(erange[0], erange[1]);
   ExactLeaderSums xs;
   DBuf<double> lam_i(al, (size_t)n), mu_i(al, (size_t)n);
@@ -906,13 +906,14 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
     }
     k_leader_counts<<<grid_for(n_f), 256, 0, s>>>(rp_f.get(), n_f, g.nX, g.nR, g.n_leaders.get());
     PSI_LAUNCHED();
-    if (hook) {
+    if (hook && hook->follower_csr()) {
       FollowerCsr fc{rp_f.get(), reinterpret_cast<const int32_t*>(ls), &sch, n_f, mc};
       hook->on_follower_csr(g, fc);
     }
   } else {
     li.release();
   }
+  if (hook) hook->on_leader_sums(g, sigma.get(), beta.get());
 
   phases.next("psi build 5: constants");
   // ---- 5. per-user constants

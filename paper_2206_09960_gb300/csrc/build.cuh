@@ -37,7 +37,12 @@ struct FollowerCsr {
 
 struct BuildHook {
   virtual ~BuildHook() = default;
-  virtual void on_follower_csr(Graph& g, const FollowerCsr& fc) = 0;
+  // whether on_follower_csr needs the follower-grouped CSR, which is then always built (the
+  // exact leader sums of a single graph do without it)
+  virtual bool follower_csr() const { return false; }
+  virtual void on_follower_csr(Graph&, const FollowerCsr&) {}
+  // sigma and beta of every user (internal order, device), once formed
+  virtual void on_leader_sums(Graph&, const double* /*sigma*/, const double* /*beta*/) {}
   // device array of a group id (< 1024) per input user, or nullptr: users of one group stay
   // contiguous inside each class of the renumbering
   virtual const int32_t* user_group() const { return nullptr; }

@@ -367,14 +367,6 @@ __global__ void k_group_bnorm(const double* __restrict__ sigma, const double* __
   }
 }
 
-__global__ void k_permute_f64(const double* __restrict__ in, const int32_t* __restrict__ perm, int64_t n, double* out) {
-  MGRID_STRIDE(k, n) out[k] = in[perm[k]];
-}
-
-__global__ void k_pair_weights(const double* __restrict__ lam, const double* __restrict__ mu, int64_t n, D2* w) {
-  MGRID_STRIDE(k, n + 1) w[k] = k < n ? D2(lam[k] + mu[k], lam[k]) : D2(0.0, 0.0);
-}
-
 // gathered index space: X at [0, nX), U at [nX, nX + nU) (user j + nR)
 template <typename T>
 __global__ void k_to_gathered(T* dst, const T* __restrict__ s, const T* __restrict__ isig, int32_t nX, int32_t nR,
@@ -456,31 +448,15 @@ struct Multi {
   bool tuned = false;
 };
 
-// Per-graph ||B||_inf from sigma and beta, formed while the follower-grouped CSR exists.
+// Per-graph ||B||_inf from the build's sigma and beta.
 struct MultiHook final : BuildHook {
   Multi& mg;
   const int32_t* group_in;
-  const double* lam_in;  // input order, device
-  const double* mu_in;
-  MultiHook(Multi& m, const int32_t* gr, const double* l, const double* u) : mg(m), group_in(gr), lam_in(l), mu_in(u) {}
+  MultiHook(Multi& m, const int32_t* gr) : mg(m), group_in(gr) {}
   const int32_t* user_group() const override { return group_in; }
-  void on_follower_csr(Graph& g, const FollowerCsr& fc) override {
-    Allocator& al = g.al;
-    cudaStream_t s = g.stream;
+  void on_leader_sums(Graph& g, const double* sigma, const double* beta) override {
     const int64_t n = g.n;
-    DBuf<double> lam(al, (size_t)n), mu(al, (size_t)n), sig(al, (size_t)n), bet(al, (size_t)n);
-    DBuf<D2> w(al, (size_t)n + 1);
-    k_permute_f64<<<mgrid(n), 256, 0, s>>>(lam_in, g.perm.get(), n, lam.get());
-    PSI_LAUNCHED();
-    k_permute_f64<<<mgrid(n), 256, 0, s>>>(mu_in, g.perm.get(), n, mu.get());
-    PSI_LAUNCHED();
-    k_pair_weights<<<mgrid(n + 1), 256, 0, s>>>(lam.get(), mu.get(), n, w.get());
-    PSI_LAUNCHED();
-    PSI_CUDA(cudaMemsetAsync(sig.get(), 0, sizeof(double) * n, s));
-    PSI_CUDA(cudaMemsetAsync(bet.get(), 0, sizeof(double) * n, s));
-    run_store_product(fc.row_ptr, fc.col, *fc.sched, fc.n_rows, fc.m, w.get(), EpiStore2{sig.get(), bet.get(), g.nX, g.nR},
-                      al, s);
-    k_group_bnorm<<<mgrid(n), 256, 0, s>>>(sig.get(), bet.get(), group_in, g.perm.get(), n, mg.bnorm_bits.get());
+    k_group_bnorm<<<mgrid(n), 256, 0, g.stream>>>(sigma, beta, group_in, g.perm.get(), n, mg.bnorm_bits.get());
     PSI_LAUNCHED();
   }
 };
@@ -1109,7 +1085,7 @@ psi_status psi_multi_create(int32_t G, const int64_t* n_g, const int64_t* m_g, c
     const double* dmu = on_device(mu, (size_t)n, mbuf_d, g.al, s);
     M.bnorm_bits.reset(g.al, (size_t)G);
     PSI_CUDA(cudaMemsetAsync(M.bnorm_bits.get(), 0, sizeof(unsigned long long) * G, s));
-    MultiHook hook(M, group_in.get(), dlam, dmu);
+    MultiHook hook(M, group_in.get());
     build_graph(g, n, m, uf.get(), ul.get(), dlam, dmu, &hook);
     uf.release();
     ul.release();
