@@ -753,8 +753,8 @@ void build_graph(Graph& g, int64_t n, int64_t m, const int32_t* follower, const 
   const uint64_t sentinel = ((uint64_t)1 << (bl + bf)) - 1;
   int64_t mu_count = 0;
   DBuf<int32_t> li;
-  // sigma and beta of a single graph as exact sums (leader_sums.cuh) when the rates allow:
-  // formed from the keys half-way through the sort, no follower-grouped CSR
+  // sigma and beta as exact sums (leader_sums.cuh) when the rates allow and no hook needs the
+  // follower-grouped CSR: formed from the keys half-way through the sort, no such CSR built
   const bool exact = (hook == nullptr || !hook->follower_csr()) && nu > 0 && m > 0 && m < ((int64_t)1 << 31) &&
                      exact_sums_apply(erange[0], erange[1]);
   ExactLeaderSums xs;

@@ -1,4 +1,4 @@
-// leader_sums.cu -- exact sigma and beta sums of the single-graph build (leader_sums.cuh).
+// leader_sums.cu -- exact sigma and beta sums of the graph build (leader_sums.cuh).
 #include "leader_sums.cuh"
 #include "primitives.cuh"
 

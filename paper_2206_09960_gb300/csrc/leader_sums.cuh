@@ -1,6 +1,6 @@
 // leader_sums.cuh -- sigma_j = sum_{l in L(j)} (lambda_l + mu_l) and beta_j = sum_{l in L(j)}
-// lambda_l (Sec. II: the denominators of a_ji and b_ji) as exact sums, for the single-graph
-// build.
+// lambda_l (Sec. II: the denominators of a_ji and b_ji) as exact sums, for the builds of single
+// graphs and of multi-graph objects.
 //
 // Every nonzero rate is m * 2^(e - 1075) with a 53-bit integer m and biased exponent e.  When
 // all rates of the graph have exponents in [ebase, ebase + kFixedSpan], a rate divided by
