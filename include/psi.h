@@ -158,9 +158,8 @@ typedef struct psi_graph_stats {
  * of user i (n entries, FP64).  opt may be NULL (defaults).  m may be 0.
  * sigma_j and beta_j = sum_{l in L(j)} lambda_l are exact sums rounded once to FP64 when
  * the binary exponents of all nonzero rates lie within 40 of the smallest and none is
- * subnormal (they
- * then do not depend on the order of the edges); otherwise they are float-pair sums (about
- * 48 bits; FP64 sums with PSI_FP64).
+ * subnormal (they then do not depend on the order of the edges); otherwise they are
+ * float-pair sums (about 48 bits; FP64 sums with PSI_FP64).
  * Errors: INVALID_ARG, OUT_OF_RANGE_ID, SELF_LOOP, BAD_RATE, OOM, CUDA; *out is NULL then.
  */
 psi_status psi_graph_create(int64_t n, int64_t m, const int32_t* follower, const int32_t* leader,
