@@ -75,3 +75,21 @@ def test_edge_order_does_not_change_results(precision):
     np.testing.assert_array_equal(a, b)
     np.testing.assert_array_equal(a, c)
     assert ia["iters"] == ib["iters"] == ic["iters"]
+
+
+@pytest.mark.parametrize("top,tiny", [(2.0 ** 40, 0.0), (2.0 ** 41, 0.0), (1.0, 1e-310)])
+def test_leader_sums_at_the_edges_of_the_exact_range(top, tiny):
+    """Rates whose binary exponents span exactly 40 (exact sums), 41 (the product), and a
+    subnormal rate (the product): each against the oracle."""
+    w = psigen.workload("chunglu", seed=24, scale=13)
+    n = w["n"]
+    u = psigen.uniform(24, 11, n)
+    lam = np.where(u < 0.5, 1.0, top)   # exponents 0 and log2(top)
+    mu = np.where(u < 0.25, top, 1.0)
+    if tiny:
+        lam[::97] = tiny  # subnormal posting rates
+    ref = oracle.solve(n, w["follower"], w["leader"], lam, mu, eps=0.0, to_floor=True)
+    psi, info, st = _solve(n, w["follower"], w["leader"], lam, mu)
+    assert info["converged"]
+    assert st["m_unique"] == ref["m_unique"]
+    assert rel_l1(psi, ref["psi"]) <= 1e-12
