@@ -37,9 +37,9 @@ METRIC = "Power-ψ time-to-L1<1e-8 and GTEPS/iter at N=2^25; % of HBM peak"
 FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes per launch of the FP32 series step (k_spmv + fix-up) from one ncu capture,
 # valid only while the kernel sources hash to `sha`.
-NCU_TRAFFIC = {"sha": "a79666bafee8b9b9", "bytes_per_launch": 2466689006,
-               "note": "k_spmv<float,EpiSeries,32> (tile 1024, 28672 entries in shared memory) DRAM read + write on "
-                       "R-MAT scale 23 (one --set full capture: 623.5 MB = 0.940 x the kernel's own bytes), scaled "
+NCU_TRAFFIC = {"sha": "284f5319779e3082", "bytes_per_launch": 2462346414,
+               "note": "k_spmv<float,EpiSeries,32> (tile 2048, 28672 entries in shared memory) DRAM read + write on "
+                       "R-MAT scale 23 (one --set full capture: 622.4 MB = 0.938 x the kernel's own bytes), scaled "
                        "to the scale-25 launch by its kernel bytes (2.624 GB)"}
 KERNEL_SOURCES = ["paper_2206_09960_gb300/csrc/spmv.cuh", "paper_2206_09960_gb300/csrc/common.cuh"]
 CPU_SAMPLE_SCALE = 20
