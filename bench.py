@@ -728,6 +728,29 @@ def run_warmstart(args, n_train=200, eval_scale=23, train_steps=1500):
         psi_warm = g.scores().cpu().numpy()
         g.solve(args.eps, 100000)
         psi_cold = g.scores().cpu().numpy()
+    # resuming from the solved iterate after every rate moves by ~1% (multiplicative
+    # LogNormal(0, 0.01) noise): the start the library also offers (psi_get_iterate -> init_s)
+    rng = np.random.default_rng(7778)
+    lam2 = w["lam"] * np.exp(0.01 * rng.standard_normal(w["n"]))
+    mu2 = w["mu"] * np.exp(0.01 * rng.standard_normal(w["n"]))
+    with psi.Graph(w["n"], *args_d, stream=stream) as g:
+        g.solve(args.eps, 100000)
+        s_prev = g.iterate()
+    args_p = [args_d[0], args_d[1], torch.from_numpy(lam2).cuda(), torch.from_numpy(mu2).cuda()]
+    with psi.Graph(w["n"], *args_p, stream=stream) as g:
+        for name in ("changed_cold", "changed_resume"):
+            ts, its = [], []
+            for rep in range(args.warmup + args.steps):
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                info = g.solve(args.eps, 100000, s_prev if name == "changed_resume" else None)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if rep >= args.warmup:
+                    ts.append(e0.elapsed_time(e1) / 1e3)
+                    its.append(info["iters"])
+            res[name] = (statistics.mean(ts), its[-1], info["converged"])
     clk = clocks.stop()
     rel = float(np.abs(psi_warm - psi_cold).sum() / np.abs(psi_cold).sum())
     # the network on tensor cores: one forward pass over the held-out graph's rows and one
@@ -763,7 +786,11 @@ def run_warmstart(args, n_train=200, eval_scale=23, train_steps=1500):
                        "eps": args.eps, "train_rows": int(x.shape[0]), "train_steps": train_steps},
             "cold_s": res["cold"][0], "cold_iters": res["cold"][1], "warm_s": res["warm"][0],
             "warm_iters": res["warm"][1], "converged": [res["cold"][2], res["warm"][2]],
-            "psi_rel_l1_warm_vs_cold": rel, "loss_first": float(np.mean(losses[:10])),
+            "psi_rel_l1_warm_vs_cold": rel,
+            "rates_changed_1pct": {"cold_s": res["changed_cold"][0], "cold_iters": res["changed_cold"][1],
+                                   "resume_s": res["changed_resume"][0], "resume_iters": res["changed_resume"][1],
+                                   "converged": [res["changed_cold"][2], res["changed_resume"][2]]},
+            "loss_first": float(np.mean(losses[:10])),
             "loss_last": float(np.mean(losses[-50:])), "data_s": t_data, "train_s": t_train, "clocks": clk,
             "roofline": net}
     print(json.dumps(line), flush=True)
