@@ -93,3 +93,21 @@ def test_leader_sums_at_the_edges_of_the_exact_range(top, tiny):
     assert info["converged"]
     assert st["m_unique"] == ref["m_unique"]
     assert rel_l1(psi, ref["psi"]) <= 1e-12
+
+
+@pytest.mark.parametrize("lo,hi", [(1e-3, 1e3), (1e-10, 1e10)])
+def test_one_edge_repeated_many_times(lo, hi):
+    """200,000 copies of one follow edge beside a sparse graph: the repeats span whole warps
+    and blocks of the duplicate merge and are subtracted from the exact sums in one run per
+    warp (exact path), or merged before the follower sort (product path)."""
+    w = psigen.workload("poisson1000", seed=25, scale=3000)
+    n = w["n"]
+    f = np.concatenate([w["follower"], np.full(200_000, 7, np.int32), w["follower"][:50]])
+    l = np.concatenate([w["leader"], np.full(200_000, 11, np.int32), w["leader"][:50]])
+    lam = _log_uniform(n, lo, hi, 25, psigen.STREAM_LAMBDA)
+    mu = _log_uniform(n, lo, hi, 25, psigen.STREAM_MU)
+    ref = oracle.solve(n, f, l, lam, mu, eps=0.0, to_floor=True)
+    psi, info, st = _solve(n, f, l, lam, mu)
+    assert info["converged"]
+    assert st["m_unique"] == ref["m_unique"] and st["m_input"] == f.size
+    assert rel_l1(psi, ref["psi"]) <= 1e-12
