@@ -225,18 +225,25 @@ psi_status psi_pagerank(psi_graph* g, double alpha, double eps, int32_t max_iter
                         psi_solve_info* info);
 
 /*
- * psi_power_nf -- Power-NF (Algorithm 1), the method Power-psi replaces, for small graphs
- * (n <= 4096): for every origin user i, the newsfeed vector of Eq. 8, p_i <- A p_i + b_i from
- * p_i = b_i, until ||p_i^t - p_i^{t-1}||_1 <= eps (each origin on its own test; a gap of 1
- * before the first step) or max_iter steps; then q_i = C p_i + d_i (Eq. 7) and
- * psi_i = (1/N) sum_n q_i^(n) (Eq. 1), in FP64.  All origins step together as the columns
- * of an n x n matrix.  psi_out: n FP64 values in input order, host or device (may be
- * NULL).  info (may be NULL): iters = the most steps any origin took, spmv_launches = the
- * matrix-vector products of Algorithm 1 (steps summed over origins), gap_s_l1 = the largest
- * last gap, converged, ms.  The handle's psi scores are left as they were.
- * Returns OK, NOT_CONVERGED (psi still written) or an error (INVALID_ARG for n > 4096).
+ * psi_power_nf -- Power-NF (Algorithm 1), the method Power-psi replaces: for every origin
+ * user i, the newsfeed vector of Eq. 8, p_i <- A p_i + b_i from p_i = b_i, until
+ * ||p_i^t - p_i^{t-1}||_1 <= eps (each origin on its own test; a gap of 1 before the first
+ * step) or max_iter steps; then q_i = C p_i + d_i (Eq. 7) and psi_i = (1/N) sum_n q_i^(n)
+ * (Eq. 1), in FP64.  Origins are stepped together in passes, as the columns of a matrix
+ * with one row per user that has leaders (users without leaders have p = 0; origins without
+ * followers have p_i = 0 and psi_i = d_i / N).  origins_per_pass: origins per pass, 0 to
+ * take as many as a quarter of the free device memory holds (6 to 32 GiB of pass state,
+ * two FP64 matrices); results do not depend on it.  The cost is that of about N Power-psi
+ * solves.  psi_out: n FP64 values in input
+ * order, host or device (may be NULL).  info (may be NULL): iters = the most steps any
+ * origin took, spmv_launches = the matrix-vector products of Algorithm 1 (steps summed over
+ * origins, saturating at INT32_MAX), gap_s_l1 = the largest last gap, converged, ms.  The
+ * handle's psi scores are left as they were.
+ * Returns OK, NOT_CONVERGED (psi still written) or an error (INVALID_ARG for more than 2^20
+ * users with leaders, a negative origins_per_pass, NaN eps or a negative max_iter).
  */
-psi_status psi_power_nf(psi_graph* g, double eps, int32_t max_iter, double* psi_out, psi_solve_info* info);
+psi_status psi_power_nf(psi_graph* g, double eps, int32_t max_iter, int32_t origins_per_pass, double* psi_out,
+                        psi_solve_info* info);
 
 /* ------------------------------------------------------------------------------------
  * Scenario batches: S sets of activity rates (lambda, mu) on one follower graph, solved

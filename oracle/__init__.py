@@ -81,6 +81,8 @@ def _load():
             lib.orc_power_psi.argtypes = [p, dbl, i32, i32, i64, i32, p, p, p, p, ctypes.POINTER(Info)]
             lib.orc_power_nf.restype = i32
             lib.orc_power_nf.argtypes = [p, dbl, i64, p, ctypes.POINTER(i64)]
+            lib.orc_power_nf_origins.restype = i32
+            lib.orc_power_nf_origins.argtypes = [p, dbl, i64, p, i64, p, ctypes.POINTER(i64)]
             lib.orc_newsfeed_mass.restype = i64
             lib.orc_newsfeed_mass.argtypes = [p, i64, p]
             lib.orc_pagerank.restype = i64
@@ -204,11 +206,21 @@ class Model:
             out["gaps"] = hist[: info.iters].copy()
         return out
 
-    def power_nf(self, eps, max_iter=100000):
-        """Algorithm 1 for every origin.  Returns (psi, matvecs)."""
-        psi = np.empty(self.n)
+    def power_nf(self, eps, max_iter=100000, origins=None):
+        """Algorithm 1 for every origin, or for the listed origins (input ids) only: each
+        origin is its own problem, so a subset gives the same values.  Returns (psi,
+        matvecs), psi[q] the score of the q-th origin."""
         mv = ctypes.c_int64(0)
-        self._lib.orc_power_nf(self._h, float(eps), int(max_iter), _p(psi), ctypes.byref(mv))
+        if origins is None:
+            psi = np.empty(self.n)
+            self._lib.orc_power_nf(self._h, float(eps), int(max_iter), _p(psi), ctypes.byref(mv))
+            return psi, mv.value
+        ids = np.ascontiguousarray(origins, np.int64)
+        psi = np.empty(ids.size)
+        st = self._lib.orc_power_nf_origins(self._h, float(eps), int(max_iter), _p(ids), ids.size, _p(psi),
+                                            ctypes.byref(mv))
+        if st not in (0, 7):  # OK, or not converged within max_iter
+            raise OracleError(st)
         return psi, mv.value
 
     def newsfeed_mass(self, max_iter=100000):

@@ -322,52 +322,75 @@ int32_t orc_power_psi(const orc_model* g, double eps, int32_t tol_mode, int32_t 
 }
 
 /*
- * Power-NF, Algorithm 1, for every origin i: p_i <- b_i; while gap > eps
+ * Power-NF, Algorithm 1, for one origin i: p_i <- b_i; while gap > eps
  * { p_old <- p_i; p_i <- A p_old + b_i; gap <- ||p_i - p_old||_1 }; then
- * q_i = C p_i + d_i (Eq. 7) and psi_i = (1/N) sum_n q_i^(n) (Eq. 1).
- * Counts matrix-vector products in *matvecs.  Meant for small N.
+ * q_i = C p_i + d_i (Eq. 7) and psi_i = (1/N) sum_n q_i^(n) (Eq. 1).  p, po, bi are
+ * scratch vectors of n entries; adds the matrix-vector products to *mv and returns 1 if
+ * the origin met its test.
  */
-int32_t orc_power_nf(const orc_model* g, double eps, int64_t max_iter, double* psi_out,
-                     int64_t* matvecs) {
+static int nf_origin(const orc_model* g, int64_t i, double eps, int64_t max_iter, double* p, double* po,
+                     double* bi, double* psi_i, int64_t* mv) {
   const int64_t n = g->n;
-  double* p = (double*)malloc(sizeof(double) * (size_t)n);
-  double* po = (double*)malloc(sizeof(double) * (size_t)n);
-  double* bi = (double*)malloc(sizeof(double) * (size_t)n);
+  /* b_i: column i of B, entries b_ji for the followers j of i */
+  for (int64_t j = 0; j < n; ++j) bi[j] = 0.0;
+  for (int64_t e = g->colptr[i]; e < g->colptr[i + 1]; ++e) bi[g->follower[e]] = g->b[e];
+  for (int64_t j = 0; j < n; ++j) p[j] = bi[j];
+  double gap = 1.0;
+  int64_t t = 0;
+  while (gap > eps && t < max_iter) {
+    memcpy(po, p, sizeof(double) * (size_t)n);
+    for (int64_t j = 0; j < n; ++j) { /* (A p_old)_j = sum_{k in L(j)} a_jk p_old_k */
+      double acc = 0.0;
+      for (int64_t e = g->rowptr[j]; e < g->rowptr[j + 1]; ++e) acc += g->a_row[e] * po[g->leader[e]];
+      p[j] = acc + bi[j];
+    }
+    double acc = 0.0;
+    for (int64_t j = 0; j < n; ++j) acc += fabs(p[j] - po[j]);
+    gap = acc;
+    ++t;
+    ++*mv;
+  }
+  /* q_i^(n) = c_n p_i^(n) + d_i 1{n = i};  psi_i = mean over n */
+  double q = 0.0;
+  for (int64_t j = 0; j < n; ++j) q += g->c[j] * p[j];
+  q += g->d[i];
+  *psi_i = q / (double)n;
+  return gap <= eps;
+}
+
+/*
+ * Power-NF (Algorithm 1) for the origins listed in origins[0..count) (input ids), or for
+ * every origin in order when origins is NULL (count is then ignored): psi_out[q] is the
+ * score of the q-th origin.  Each origin is an independent problem in Algorithm 1, so a
+ * subset gives the same values as the full run.  Counts matrix-vector products in
+ * *matvecs.  Meant for small N, or for a few origins of a larger graph.
+ */
+int32_t orc_power_nf_origins(const orc_model* g, double eps, int64_t max_iter, const int64_t* origins,
+                             int64_t count, double* psi_out, int64_t* matvecs) {
+  const int64_t n = g->n;
+  if (!origins) count = n;
+  double* p = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  double* po = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  double* bi = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
   if (!p || !po || !bi) { free(p); free(po); free(bi); return ORC_ERR_NOMEM; }
   int64_t mv = 0;
   int32_t st = ORC_OK;
-  for (int64_t i = 0; i < n; ++i) {
-    /* b_i: column i of B, entries b_ji for the followers j of i */
-    for (int64_t j = 0; j < n; ++j) bi[j] = 0.0;
-    for (int64_t e = g->colptr[i]; e < g->colptr[i + 1]; ++e) bi[g->follower[e]] = g->b[e];
-    for (int64_t j = 0; j < n; ++j) p[j] = bi[j];
-    double gap = 1.0;
-    int64_t t = 0;
-    while (gap > eps && t < max_iter) {
-      memcpy(po, p, sizeof(double) * (size_t)n);
-      for (int64_t j = 0; j < n; ++j) { /* (A p_old)_j = sum_{k in L(j)} a_jk p_old_k */
-        double acc = 0.0;
-        for (int64_t e = g->rowptr[j]; e < g->rowptr[j + 1]; ++e) acc += g->a_row[e] * po[g->leader[e]];
-        p[j] = acc + bi[j];
-      }
-      double acc = 0.0;
-      for (int64_t j = 0; j < n; ++j) acc += fabs(p[j] - po[j]);
-      gap = acc;
-      ++t;
-      ++mv;
-    }
-    if (gap > eps) st = ORC_NOT_CONVERGED;
-    /* q_i^(n) = c_n p_i^(n) + d_i 1{n = i};  psi_i = mean over n */
-    double q = 0.0;
-    for (int64_t j = 0; j < n; ++j) q += g->c[j] * p[j];
-    q += g->d[i];
-    psi_out[i] = q / (double)n;
+  for (int64_t q = 0; q < count; ++q) {
+    const int64_t i = origins ? origins[q] : q;
+    if (i < 0 || i >= n) { st = ORC_ERR_ID; break; }
+    if (!nf_origin(g, i, eps, max_iter, p, po, bi, &psi_out[q], &mv)) st = ORC_NOT_CONVERGED;
   }
   if (matvecs) *matvecs = mv;
   free(p);
   free(po);
   free(bi);
   return st;
+}
+
+/* Power-NF (Algorithm 1) for every origin: psi_out[i] for i = 0..n-1. */
+int32_t orc_power_nf(const orc_model* g, double eps, int64_t max_iter, double* psi_out,
+                     int64_t* matvecs) {
+  return orc_power_nf_origins(g, eps, max_iter, NULL, 0, psi_out, matvecs);
 }
 
 /*

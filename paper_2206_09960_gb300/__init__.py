@@ -144,16 +144,17 @@ class Graph:
         d["status"] = B.status_name(st)
         return out, d
 
-    def power_nf(self, eps, max_iter=10000, out=None):
-        """Power-NF (Algorithm 1) for every origin of this graph (at most 4096 users): returns
-        (psi in input order, info dict; iters = the most steps of an origin, spmv_launches =
-        the matrix-vector products summed over origins).  The graph's psi scores are left
-        as they were."""
+    def power_nf(self, eps, max_iter=10000, out=None, origins_per_pass=0):
+        """Power-NF (Algorithm 1) for every origin of this graph (at most 2^20 users with
+        leaders), ``origins_per_pass`` origins at a time (0: as many as a quarter of the free
+        device memory holds, 6 to 32 GiB): returns (psi in input order, info dict; iters =
+        the most steps of an origin, spmv_launches = the matrix-vector products summed over
+        origins).  The graph's psi scores are left as they were."""
         import torch
 
         if out is None:
             out = torch.empty(self.n, dtype=torch.float64, device="cuda")
-        st, d = B.psi_power_nf(self._h, eps, max_iter, _ptr(out))
+        st, d = B.psi_power_nf(self._h, eps, max_iter, origins_per_pass, _ptr(out))
         d["status"] = B.status_name(st)
         return out, d
 

@@ -133,7 +133,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.psi_trim_memory.restype = i32
         lib.psi_pagerank.argtypes = [vp, dbl, dbl, i32, vp, vp]
         lib.psi_pagerank.restype = i32
-        lib.psi_power_nf.argtypes = [vp, dbl, i32, vp, vp]
+        lib.psi_power_nf.argtypes = [vp, dbl, i32, i32, vp, vp]
         lib.psi_power_nf.restype = i32
         lib.psi_multi_create.argtypes = [i32, vp, vp, vp, vp, vp, vp, ctypes.POINTER(psi_options),
                                          ctypes.POINTER(vp)]
@@ -273,9 +273,9 @@ def psi_batch_destroy(h):
     load().psi_batch_destroy(h)
 
 
-def psi_power_nf(h, eps, max_iter, out_ptr):
+def psi_power_nf(h, eps, max_iter, origins_per_pass, out_ptr):
     info = psi_solve_info()
-    st = load().psi_power_nf(h, float(eps), int(max_iter), out_ptr, ctypes.byref(info))
+    st = load().psi_power_nf(h, float(eps), int(max_iter), int(origins_per_pass), out_ptr, ctypes.byref(info))
     _check(st, allow=(PSI_OK, PSI_ERR_NOT_CONVERGED))
     return st, info.as_dict()
 

@@ -284,14 +284,15 @@ psi_status psi_pagerank(psi_graph* g, double alpha, double eps, int32_t max_iter
   return result;
 }
 
-psi_status psi_power_nf(psi_graph* g, double eps, int32_t max_iter, double* psi_out, psi_solve_info* info) {
+psi_status psi_power_nf(psi_graph* g, double eps, int32_t max_iter, int32_t origins_per_pass, double* psi_out,
+                        psi_solve_info* info) {
   psi::NvtxRange nvtx_range("psi_power_nf");
   if (!g) {
     psi::set_last_error("graph is NULL");
     return PSI_ERR_INVALID_ARG;
   }
   psi_status result = PSI_OK;
-  psi_status st = psi::guarded([&] { result = psi::power_nf(g->g, eps, max_iter, psi_out, info); });
+  psi_status st = psi::guarded([&] { result = psi::power_nf(g->g, eps, max_iter, origins_per_pass, psi_out, info); });
   if (st != PSI_OK) return st;
   if (result == PSI_ERR_NOT_CONVERGED) psi::set_last_error("max_iter reached before every origin met its test");
   return result;

@@ -24,7 +24,8 @@ struct SolveTarget {
 SolveConsts graph_consts(const Graph& g);
 // Power-NF (Algorithm 1) for every origin at once, small graphs (powernf.cu); psi_out in
 // input order (host or device)
-psi_status power_nf(Graph& g, double eps, int32_t max_iter, double* psi_out, psi_solve_info* info);
+psi_status power_nf(Graph& g, double eps, int32_t max_iter, int32_t origins_per_pass, double* psi_out,
+                    psi_solve_info* info);
 // PageRank power method (Eq. 22) on the graph's follower structure (pagerank.cu)
 psi_status pagerank(Graph& g, double alpha, double eps, int32_t max_iter, double* pi_out, psi_solve_info* info);
 psi_status solve_with(Graph& g, const SolveConsts& K, const SolveTarget& T, double eps, int32_t max_iter,

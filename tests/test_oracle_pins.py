@@ -308,6 +308,25 @@ def test_power_nf_matches_power_psi_and_costs_more():
     assert mv > 20 * ps["iters"]
 
 
+def test_power_nf_on_listed_origins_is_the_full_run():
+    """Algorithm 1 treats each origin on its own: the oracle's origin-list form gives the full
+    run's values for those origins, in the listed order (repeats allowed), and the step
+    counts add up; an origin outside [0, n) is refused."""
+    rng = np.random.default_rng(19)
+    n = 150
+    f, l = _random_graph(n, 700, 20)
+    lam, mu = rng.uniform(0.0, 1, n), rng.uniform(0.1, 1, n)
+    with oracle.Model(n, f, l, lam, mu) as g:
+        full, mv = g.power_nf(1e-13)
+        ids = np.array([149, 0, 7, 7, 63])
+        sub, mv_sub = g.power_nf(1e-13, origins=ids)
+        halves = [g.power_nf(1e-13, origins=np.arange(a, b))[1] for a, b in ((0, 75), (75, n))]
+        with pytest.raises(oracle.OracleError):
+            g.power_nf(1e-13, origins=np.array([n]))
+    np.testing.assert_array_equal(sub, full[ids])
+    assert sum(halves) == mv and 0 < mv_sub < mv
+
+
 def test_poisson1000_direct_solve_agrees_with_power_psi():
     """The small FP64 workload: the direct solve of all N wall systems (one LU with N
     right-hand sides) and Algorithm 2 at eps = 1e-12 agree."""
