@@ -622,14 +622,20 @@ def run_pagerank(args, alpha=0.85, eps=1e-9):
 # another machine and the real graphs: context only).
 TABLE3 = [("dblp", 12_591, 49_743, 17.805, 0.029), ("hepph", 34_546, 421_578, 272.358, 0.622),
           ("facebook", 63_731, 817_035, 1764.226, 0.307), ("twitter", 465_017, 834_797, 14526.039, 0.634)]
+# and its Table IV times with homogeneous rates (lambda = 0.15, mu = 0.85): PageRank's power
+# method, Power-NF and Power-psi
+TABLE4 = {"dblp": (0.023, 20.775, 0.034), "hepph": (0.361, 360.769, 0.908), "facebook": (0.308, 2253.302, 0.454),
+          "twitter": (0.584, 17411.146, 0.806)}
 
 
 def run_powernf(args, eps=1e-9, sample=64):
-    """The paper's Table III on stand-ins of its four graphs: Chung-Lu (gamma = 2.1) graphs
-    with the same node and edge-draw counts and rates U(0, 1) (Sec. V's heterogeneous case).
-    Power-NF (Algorithm 1, every origin, per-origin p-tolerance eps) against Power-psi
-    (Algorithm 2, FP64, s-tolerance eps) on the same graph handle, solve times only, and
-    the largest psi difference between the two.  The oracle's Algorithm 1 runs on a few
+    """The paper's Tables III and IV on stand-ins of its four graphs: Chung-Lu (gamma = 2.1)
+    graphs with the same node and edge-draw counts and rates U(0, 1) (Sec. V's heterogeneous
+    case), then the same graphs with lambda = 0.15, mu = 0.85 (the homogeneous case, with
+    PageRank's power method at alpha = 0.85 and pi-tolerance eps beside).  Power-NF
+    (Algorithm 1, every origin, per-origin p-tolerance eps) against Power-psi (Algorithm 2,
+    FP64, s-tolerance eps) on the same graph handle, solve times only, and the largest psi
+    difference between the two.  The oracle's Algorithm 1 runs on a few
     origins of every graph (parity, one by one), and on `sample` random origins of the
     largest for the CPU baseline."""
     import numpy as np
@@ -658,7 +664,7 @@ def run_powernf(args, eps=1e-9, sample=64):
 
     clocks = Clocks(torch.cuda.current_device())
     clocks.start()
-    rows = []
+    rows, hom_rows = [], []
     cpu = None
     for name, n, draws, paper_nf, paper_psi in TABLE3:
         f, l = psigen.chung_lu_graph(n, 2.1, draws, args.seed)
@@ -692,6 +698,21 @@ def run_powernf(args, eps=1e-9, sample=64):
                                  f"the {name} stand-in, scaled by {n}/{sample}",
                        "measured_s": t_s, "scaled_by": n / sample}
         parity = float(np.max(np.abs(nf_host[top] - ref) / np.maximum(np.abs(ref), 1.0 / n)))
+        # Table IV: the same graph with homogeneous rates, where psi is PageRank with alpha = 0.85
+        hom = [torch.full((n,), v, dtype=torch.float64, device="cuda") for v in (0.15, 0.85)]
+        with psi.Graph(n, dev[0], dev[1], *hom, precision="fp64", tol_mode="s_abs", stream=stream) as g:
+            h_nf, (h_nf_psi, h_nf_info) = timed(lambda: g.power_nf(eps, 100000), 1, 0)
+            h_ps, h_pinfo = timed(lambda: g.solve(eps, 100000), args.steps, args.warmup)
+            h_pr, (h_pi, h_prinfo) = timed(lambda: g.pagerank(0.85, eps, 100000), args.steps, args.warmup)
+            h_psi = g.scores()
+            h_diff = float((h_psi - h_pi).abs().sum() / h_pi.abs().sum())
+            h_nfdiff = float(((h_nf_psi - h_psi).abs() / h_psi.abs().clamp_min(1.0 / n)).max())
+        hom_rows.append({"workload": f"{name}_standin_homogeneous_0.15_0.85", "pagerank_s": h_pr,
+                         "pagerank_iters": h_prinfo["iters"], "power_nf_s": h_nf,
+                         "power_nf_matvecs": h_nf_info["spmv_launches"], "power_psi_s": h_ps,
+                         "power_psi_iters": h_pinfo["iters"], "psi_vs_pagerank_rel_l1": h_diff,
+                         "max_rel_psi_diff_nf_vs_psi": h_nfdiff,
+                         "paper_cpu_s": dict(zip(("pagerank", "power_nf", "power_psi"), TABLE4[name]))})
         rows.append({"workload": f"{name}_standin_chunglu_gamma2.1_n{n}_draws{draws}_uniform0-1", "n": n,
                      "edges_drawn": draws, "edges_unique": st["m_unique"], "users_with_leaders": st["n_gathered"],
                      "users_with_followers": st["n_rows"],
@@ -706,7 +727,7 @@ def run_powernf(args, eps=1e-9, sample=64):
             "higher_is_better": False, "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "+".join(r["workload"] for r in rows), "eps": eps,
                        "tolerance": "per-origin ||p_t - p_t-1||_1 (Power-NF), ||s_t - s_t-1||_1 (Power-psi)"},
-            "cases": rows, "clocks": clk}
+            "cases": rows, "cases_homogeneous": hom_rows, "clocks": clk}
     if cpu is not None:
         line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)
