@@ -227,6 +227,8 @@ struct Graph {
   DBuf<float> u32a, u32b, u32c;// gathered FP32 vectors [n+1]
   DBuf<double> psi64;          // psi, internal order
   DBuf<double> carry_head, carry_tail, gap_part, gap_fix;
+  DBuf<double> gap_tile;       // per-tile gaps of the product ([num_tiles])
+  DBuf<int32_t> tile_ctr;      // the product's tile claims {claimed, warps done}
   DBuf<DevState> state;
   DevState* host_state = nullptr;  // pinned mirror
   bool solved = false;

@@ -198,6 +198,7 @@ constexpr int64_t kTuneMinNnz = (int64_t)1 << 22;  // smaller graphs keep the fi
 float time_series_step(Graph& g, const Schedule& sc, int32_t hot, cudaStream_t s) {
   Allocator& al = g.al;
   DBuf<float> ch(al, (size_t)sc.tiles), ct(al, (size_t)sc.tiles);
+  DBuf<double> gt(al, (size_t)sc.tiles);
   SpmvArgs a{};
   a.row_ptr = g.row_ptr.get();
   a.col = g.col.get();
@@ -209,6 +210,8 @@ float time_series_step(Graph& g, const Schedule& sc, int32_t hot, cudaStream_t s
   a.m = g.m_unique;
   a.state = g.state.get();
   a.gap_part = g.gap_part.get();
+  a.tile_ctr = g.tile_ctr.get();
+  a.gap_tile = gt.get();
   a.carry_head = ch.get();
   a.carry_tail = ct.get();
   FixArgs f{};
@@ -221,6 +224,8 @@ float time_series_step(Graph& g, const Schedule& sc, int32_t hot, cudaStream_t s
   f.gap_fix = g.gap_fix.get();
   f.carry_head = ch.get();
   f.carry_tail = ct.get();
+  f.gap_tile = gt.get();
+  f.gap_tiles = sc.tiles;
   // scratch output: the series term goes to u32b, the sums to s64 (both initialised by the
   // solve that follows)
   EpiSeries epi{g.mu32.get(), g.isig32.get(), g.s64.get(), g.u32b.get(), g.nX};
@@ -232,10 +237,9 @@ float time_series_step(Graph& g, const Schedule& sc, int32_t hot, cudaStream_t s
       k_spmv<float, EpiSeries><<<spmv_grid<float, EpiSeries>(sc.tiles), kSpmvThreads, 0, s>>>(a, g.u32a.get(), epi);
     }
     PSI_LAUNCHED();
-    if (sc.num_fix > 0) {
-      k_fixup<float, EpiSeries><<<fix_blocks(sc.num_fix), kFixThreads, 0, s>>>(f, epi);
-      PSI_LAUNCHED();
-    }
+    // the fix-up also adds the per-tile gaps, so it runs on every step
+    k_fixup<float, EpiSeries><<<fix_blocks(std::max(sc.num_fix, sc.tiles)), kFixThreads, 0, s>>>(f, epi);
+    PSI_LAUNCHED();
   };
   cudaEvent_t e0, e1;
   PSI_CUDA(cudaEventCreate(&e0));
@@ -260,6 +264,7 @@ void apply_schedule(Graph& g, Schedule&& sc) {
   g.fix_tile = std::move(sc.fix_tile);
   g.carry_head.reset(g.al, (size_t)(g.num_tiles > 0 ? g.num_tiles : 1));
   g.carry_tail.reset(g.al, (size_t)(g.num_tiles > 0 ? g.num_tiles : 1));
+  if (g.allocated_iter) g.gap_tile.reset(g.al, (size_t)(g.num_tiles > 0 ? g.num_tiles : 1));
 }
 
 void autotune_series(Graph& g, cudaStream_t s) {
@@ -358,6 +363,11 @@ struct Stepper {
     a.m = g.m_unique;
     a.state = g.state.get();
     a.gap_part = g.gap_part.get();
+    // FP32 products claim their tiles at run time (their gaps then reach k_finalize through
+    // the fix-up's fixed slices); the 8- and 16-byte products keep the fixed stride
+    constexpr bool claims = sizeof(T) == 4;
+    a.tile_ctr = claims ? g.tile_ctr.get() : nullptr;
+    a.gap_tile = claims ? g.gap_tile.get() : nullptr;
     a.carry_head = g.carry_head.get();
     a.carry_tail = g.carry_tail.get();
     int grid = 0, fgrid = 0;
@@ -383,7 +393,9 @@ struct Stepper {
         PSI_LAUNCHED();
       }
     }
-    if (g.num_fix > 0) {
+    // the fix-up closes rows that span tiles and, after claimed tiles, adds the product's
+    // per-tile gaps in fixed slices (no per-block gap then has a fixed order)
+    if (claims ? g.num_tiles > 0 : g.num_fix > 0) {
       FixArgs f{};
       f.row_ptr = g.row_ptr.get();
       f.tile_row = g.tile_row.get();
@@ -394,7 +406,9 @@ struct Stepper {
       f.gap_fix = g.gap_fix.get();
       f.carry_head = g.carry_head.get();
       f.carry_tail = g.carry_tail.get();
-      fgrid = fix_blocks(g.num_fix);
+      f.gap_tile = claims ? g.gap_tile.get() : nullptr;
+      f.gap_tiles = claims ? g.num_tiles : 0;
+      fgrid = fix_blocks(claims ? std::max(g.num_fix, g.num_tiles) : g.num_fix);
       k_fixup<T, Epi><<<fgrid, kFixThreads, 0, s>>>(f, epi);
       PSI_LAUNCHED();
     }
@@ -404,7 +418,7 @@ struct Stepper {
       ev.push_back(e1);
       ev_phase.push_back(phase_step);
     }
-    k_finalize<<<1, 1024, 0, s>>>(g.state.get(), g.gap_part.get(), grid, g.gap_fix.get(), fgrid);
+    k_finalize<<<1, 1024, 0, s>>>(g.state.get(), g.gap_part.get(), claims ? 0 : grid, g.gap_fix.get(), fgrid);
     PSI_LAUNCHED();
     ++phase_step;
     ++launches;
@@ -493,6 +507,9 @@ void ensure_iteration_buffers(Graph& g) {
   g.carry_tail.reset(al, nt);
   g.gap_part.reset(al, (size_t)num_sms() * 32);
   g.gap_fix.reset(al, (size_t)num_sms() * 8);
+  g.gap_tile.reset(al, nt);
+  g.tile_ctr.reset(al, 2);
+  PSI_CUDA(cudaMemsetAsync(g.tile_ctr.get(), 0, 2 * sizeof(int32_t), g.stream));
   g.state.reset(al, 1);
   if (!g.host_state) PSI_CUDA(cudaMallocHost((void**)&g.host_state, 2 * sizeof(DevState)));
   g.allocated_iter = true;

@@ -280,9 +280,13 @@ struct SpmvArgs {
   int32_t num_tiles;
   int32_t hot;            // entries u[0, hot) staged in the block's shared memory (0: none)
   int32_t n_rows;
+  int32_t* tile_ctr;      // tiles claimed at run time (4-byte sums only): {tiles claimed, warps
+                          // done}, zero between launches (the last warp resets them); nullptr:
+                          // a fixed stride
   int64_t m;
   const DevState* state;  // skip the step when state->done
-  double* gap_part;       // [gridDim.x]
+  double* gap_part;       // [gridDim.x] (fixed stride)
+  double* gap_tile;       // [num_tiles] the gap of each tile (claimed tiles)
   void* carry_head;       // [num_tiles] T
   void* carry_tail;       // [num_tiles] T
 };
@@ -297,6 +301,8 @@ struct FixArgs {
   double* gap_fix;        // [gridDim.x]
   const void* carry_head;
   const void* carry_tail;
+  const double* gap_tile; // the product's per-tile gaps, added in fixed slices (gap_tiles > 0)
+  int32_t gap_tiles;
 };
 
 // An epilogue may declare `static constexpr bool kTileSkip = true` and a member
@@ -343,7 +349,12 @@ constexpr int spmv_min_blocks() {
 // (one block per SM: the copy takes most of the SM's shared memory).
 constexpr int kSpmvHotWarps = 32;
 
-// One warp per tile; the warps of all blocks walk the tiles with a grid-wide stride.  A
+// One warp per tile.  With a.tile_ctr (FP32 sums), each warp takes its first two tiles by a grid-wide
+// stride and claims every later one from a counter (the claim for the tile after next is
+// issued when a tile starts and read when it ends, so its latency hides under the tile);
+// SMs that run faster take more tiles, and the tile's gap is written per tile (a.gap_tile,
+// a fixed lane tree) so that its sum keeps an order fixed by the graph.  Without it the
+// warps walk the tiles with a grid-wide stride and leave a per-block gap.  A
 // tile's row ends are first marked in a bitmap in shared memory (bit q: nonzero nnz0 + q is
 // the last one of its row) from the tile's slice of row_ptr.  Every row has at least one
 // nonzero, so the k-th row end of the tile belongs to row tile_row[tile] + k.  Each step
@@ -419,7 +430,11 @@ __global__ void __launch_bounds__(WARPS * 32, WARPS == kSpmvWarps ? spmv_min_blo
     }
   };
 
+  // claims only in the 4-byte products: the 8- and 16-byte sums need the registers
+  constexpr bool kClaims = !kSkip && sizeof(T) == 4;
+  const bool dyn = kClaims && a.tile_ctr != nullptr;
   int32_t tile = next_tile();
+  int32_t nxt = kClaims ? next_tile() : 0;  // with claims the next tile is known a tile ahead
   // software pipeline: the values of the next step are in flight while a step is reduced,
   // and the column indices of the step after it, so its gathers issue without waiting
   T xn[kSpmvItems];
@@ -436,7 +451,9 @@ __global__ void __launch_bounds__(WARPS * 32, WARPS == kSpmvWarps ? spmv_min_blo
     const int32_t nnz0 = tile * a.tile;  // < m < 2^31
     const int32_t r0 = a.tile_row[tile];
     const int32_t nr = a.tile_row[tile + 1] - r0 + 1;  // rows touching the tile
-    const int32_t next = next_tile();
+    const int32_t next = kClaims ? nxt : next_tile();
+    int32_t claim = a.num_tiles;
+    if (dyn && lane == 0 && next < a.num_tiles) claim = 2 * stride + atomicAdd(a.tile_ctr, 1);
     for (int w = lane; w < words; w += 32) ends[w] = 0u;
     __syncwarp();
     const bool head_open = ld_stream(a.row_ptr + r0, pol_s) < nnz0;  // row r0 began earlier
@@ -509,7 +526,29 @@ __global__ void __launch_bounds__(WARPS * 32, WARPS == kSpmvWarps ? spmv_min_blo
     }
     if (lane == 0) carry_tail[tile] = open;  // the sum after the tile's last row end
     __syncwarp();  // the bitmap is rewritten for the next tile
+    if constexpr (kClaims) {
+      if (dyn) {
+        // the tile's gap, summed over the lanes in a fixed tree: the same whichever warp ran it
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) gap += __shfl_xor_sync(0xffffffffu, gap, o);
+        if (lane == 0) a.gap_tile[tile] = gap;
+        gap = 0.0;
+        const int32_t nn = __shfl_sync(0xffffffffu, claim, 0);
+        nxt = (next < a.num_tiles && nn < a.num_tiles) ? nn : a.num_tiles;
+      } else {
+        nxt = next_tile();
+      }
+    }
     tile = next;
+  }
+  if (dyn && lane == 0) {
+    // every claim of this warp is made before it counts itself done; the last warp to finish
+    // leaves both counters at zero for the next launch
+    __threadfence();
+    if (atomicAdd(a.tile_ctr + 1, 1) == stride - 1) {
+      atomicExch(a.tile_ctr, 0);
+      atomicExch(a.tile_ctr + 1, 0);
+    }
   }
   // per-CTA gap partial, fixed order
 #pragma unroll
@@ -586,6 +625,11 @@ __global__ void __launch_bounds__(kFixThreads) k_fixup(FixArgs a, Epi epi) {
       for (int o = 16; o > 0; o >>= 1) acc = acc + shfl_xor_t(acc, o);
       if (lane == 0) epi.row(rl, acc + ch[kl], gap, pol_s, pol_k);
     }
+  }
+  if (a.gap_tiles > 0) {  // this block's fixed slice of the product's per-tile gaps
+    const int32_t per = (int32_t)ceil_div(a.gap_tiles, gridDim.x);
+    const int32_t t1 = min(a.gap_tiles, (int32_t)blockIdx.x * per + per);
+    for (int32_t t = (int32_t)blockIdx.x * per + threadIdx.x; t < t1; t += kFixThreads) gap += a.gap_tile[t];
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) gap += __shfl_xor_sync(0xffffffffu, gap, o);
