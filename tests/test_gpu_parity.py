@@ -495,3 +495,29 @@ def test_graphs_on_two_streams_from_two_threads():
         assert len(got[i]) == 3
         for psi in got[i]:
             np.testing.assert_array_equal(psi, alone[i]["psi"])
+
+
+@pytest.mark.parametrize("tuned", [True, False])
+def test_claimed_tiles_are_bit_reproducible(tuned):
+    """At R-MAT scale 20 the FP32 series product has far more tiles than two per warp, so most
+    tiles are claimed at run time and land on different warps from run to run; each tile's gap
+    is summed on its own and the tiles' gaps in fixed slices, so repeated solves (and a
+    permuted edge order) give the same bits, step counts and gaps.  Both launch shapes: the
+    32-warp blocks with the shared-memory copy and the 8-warp blocks, tiles of 512."""
+    torch = _torch()
+    w = psigen.workload("rmat", seed=33, scale=20)
+    n, f, l = w["n"], w["follower"], w["leader"]
+    kw = {"spmv_tile": 512, "spmv_hot": 28672} if tuned else {"spmv_tile": 512, "autotune": 0, "spmv_hot": 0}
+    runs = [gpu_solve(n, f, l, w["lam"], w["mu"], 1e-8, **kw) for _ in range(3)]
+    order = psigen.permutation(f.size, 33, 4)
+    runs.append(gpu_solve(n, f[order], l[order], w["lam"], w["mu"], 1e-8, **kw))
+    st = runs[0]["stats"]
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    warps = sms * (32 if st["spmv_hot"] > 0 else 5 * 8)
+    assert st["m_unique"] / st["spmv_tile"] > 4 * warps  # most tiles are claimed
+    assert tuned == (st["spmv_hot"] > 0)
+    for r in runs[1:]:
+        np.testing.assert_array_equal(r["psi"], runs[0]["psi"])
+        np.testing.assert_array_equal(r["ids"], runs[0]["ids"])
+        assert r["info"]["iters"] == runs[0]["info"]["iters"]
+        assert r["info"]["gap_s_l1"] == runs[0]["info"]["gap_s_l1"]
