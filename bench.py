@@ -408,7 +408,7 @@ def run_batch(args, S=64, plain_sample=8):
     peak, peak_kind = measured_peaks()
     roofline = {"bound": "hbm", "achieved": alg / step_ms / 1e6, "peak": peak, "unit": "GB/s",
                 "frac": alg / step_ms / 1e6 / peak, "traffic": None, "peak_kind": peak_kind,
-                "kernel": "k_spmm<float2,EpiSeriesS> + fix-up (batched FP32 series step)",
+                "kernel": "k_spmm_claims<EpiSeriesS> + fix-up (batched FP32 series step, chunks claimed at run time)",
                 "alg_bytes_per_launch": alg, "avg_launch_ms": step_ms, "launches_timed": pinfo[0]["spmv_timed"]}
     t_plain_all = t_plain * S / plain_sample
     solve_batch = infos[0]["ms"] / 1e3

@@ -220,6 +220,8 @@ struct Batch {
   DBuf<float2> carry_head, carry_tail;
   DBuf<double2> carry_head64, carry_tail64;
   DBuf<double> gap_part, gap_fix;
+  DBuf<double> gap_chunk;      // [chunks][S] per-chunk gaps of the FP32 product
+  DBuf<int32_t> chunk_ctr;     // its chunk claims {claimed, warps done}
   int grid = 0, fgrid = 0;
   bool solved = false;
 };
@@ -334,12 +336,15 @@ void batch_buffers(Batch& b) {
   b.carry_head64.reset(al, nc * 32);
   b.carry_tail64.reset(al, nc * 32);
   int per_sm = 0;
-  PSI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmm<float2, EpiSeriesS>, 256, 0));
+  PSI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmm_claims<EpiSeriesS>, 256, 0));
   b.grid = (int)num_sms() * (per_sm > 0 ? per_sm : 1);
   b.fgrid = (int)num_sms() * 2;
 
   b.gap_part.reset(al, (size_t)b.grid * 8 * kSp);
   b.gap_fix.reset(al, (size_t)b.fgrid * 8 * kSp);
+  b.gap_chunk.reset(al, nc * kSp);
+  b.chunk_ctr.reset(al, 2);
+  PSI_CUDA(cudaMemsetAsync(b.chunk_ctr.get(), 0, 2 * sizeof(int32_t), g.stream));
 }
 
 SpmmArgs spmm_args(Batch& b) {
@@ -362,18 +367,26 @@ SpmmArgs spmm_args(Batch& b) {
   return a;
 }
 
-// one step for every active scenario: product, fix-up, per-scenario stop tests
+// one step for every active scenario: product, fix-up, per-scenario stop tests.  The FP32
+// product claims its chunks at run time; its gaps then reach k_b_finalize through the
+// fix-up, which adds the per-chunk gaps in fixed slices and so runs on every such step.
 template <typename V, typename Epi>
 void batch_step(Batch& b, const V* u, const Epi& epi) {
   cudaStream_t s = b.g.stream;
   SpmmArgs a = spmm_args(b);
+  constexpr bool claims = std::is_same<V, float2>::value;
+  if (claims) {
+    a.chunk_ctr = b.chunk_ctr.get();
+    a.gap_chunk = b.gap_chunk.get();
+  }
   int ngp = 0, ngf = 0;
   if (a.num_chunks > 0) {
-    k_spmm<V, Epi><<<b.grid, 256, 0, s>>>(a, u, epi);
+    if constexpr (claims) k_spmm_claims<Epi><<<b.grid, 256, 0, s>>>(a, u, epi);
+    else k_spmm<V, Epi><<<b.grid, 256, 0, s>>>(a, u, epi);
     PSI_LAUNCHED();
-    ngp = b.grid * 8;
+    ngp = claims ? 0 : b.grid * 8;
   }
-  if (b.sched.num_fix > 0) {
+  if (b.sched.num_fix > 0 || (claims && a.num_chunks > 0)) {
     k_spmm_fixup<V, Epi><<<b.fgrid, 256, 0, s>>>(a, b.sched.fix_tile.get(), b.sched.num_fix, b.gap_fix.get(), epi);
     PSI_LAUNCHED();
     ngf = b.fgrid * 8;

@@ -13,6 +13,8 @@
 // they have met their stop test.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "df.cuh"
 
@@ -31,7 +33,10 @@ struct SpmmArgs {
   int32_t S;                   // padded scenario count (64)
   const int32_t* active;       // [S]: 1 while a scenario still steps
   const int32_t* done;         // nonzero: no scenario steps, skip the launch
-  double* gap_part;            // [warps][S]
+  double* gap_part;            // [warps][S] (fixed stride)
+  int32_t* chunk_ctr;          // chunks claimed at run time (FP32 products): {claimed, warps
+                               // done}, zero between launches; nullptr: a fixed stride
+  double* gap_chunk;           // [num_chunks][S] the gaps of each chunk (claimed chunks)
   float2* carry_head;          // [num_chunks][S/2] (FP32 products)
   float2* carry_tail;
   double2* carry_head64;       // FP64 products
@@ -183,19 +188,30 @@ __device__ __forceinline__ DF2* carry_of<DF2>(const SpmmArgs& a, bool head) {  /
 }
 
 // V = float2 (FP32 gathers) or DF2 (float-pair gathers); u is [gathered + 1][S/2] pairs.
+// With a.chunk_ctr (FP32 only) each warp takes its first two chunks by a grid-wide stride
+// and claims every later one from a counter (the claim for the chunk after next issued when
+// a chunk starts, read when it ends); each chunk's gaps go to a.gap_chunk and the fix-up
+// adds them in fixed slices, so the sums keep an order fixed by the graph.
 template <typename V, typename Epi>
-__global__ void __launch_bounds__(256) k_spmm(SpmmArgs a, const V* __restrict__ u, Epi epi) {
+__device__ __forceinline__ void spmm_run(const SpmmArgs& a, const V* __restrict__ u, const Epi& epi) {
   if (*a.done) return;
   const int lane = threadIdx.x & 31;
   const int64_t warp_id = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  constexpr bool kClaims = std::is_same<V, float2>::value;
+  const bool dyn = kClaims && a.chunk_ctr != nullptr;
   const uint64_t pol_s = policy_evict_first();
   const uint64_t pol_k = policy_evict_last();
   const int act[2] = {a.active[2 * lane], a.active[2 * lane + 1]};
   V* ch = carry_of<V>(a, true);
   V* ct = carry_of<V>(a, false);
   double2 gap = make_double2(0.0, 0.0);
-  for (int64_t c = warp_id; c < a.num_chunks; c += n_warps) {
+  int64_t nxt = warp_id + n_warps;  // the next chunk (known a chunk ahead with claims)
+  for (int64_t c = warp_id; c < a.num_chunks;) {
+    int32_t claim = a.num_chunks;
+    if constexpr (kClaims) {
+      if (dyn && lane == 0 && nxt < a.num_chunks) claim = (int32_t)(2 * n_warps) + atomicAdd(a.chunk_ctr, 1);
+    }
     const int64_t p0 = c * kSpmmChunk;
     const int64_t p1 = p0 + kSpmmChunk < a.m ? p0 + kSpmmChunk : a.m;
     int32_t r = a.chunk_row[c];
@@ -231,9 +247,45 @@ __global__ void __launch_bounds__(256) k_spmm(SpmmArgs a, const V* __restrict__ 
       }
     }
     ct[c * 32 + lane] = acc;  // the part of a row that continues into the next chunk
+    if constexpr (kClaims) {
+      if (dyn) {
+        a.gap_chunk[c * a.S + 2 * lane] = gap.x;
+        a.gap_chunk[c * a.S + 2 * lane + 1] = gap.y;
+        gap = make_double2(0.0, 0.0);
+        const int32_t nn = __shfl_sync(0xffffffffu, claim, 0);
+        c = nxt;
+        nxt = (nxt < a.num_chunks && nn < a.num_chunks) ? nn : a.num_chunks;
+      } else {
+        c += n_warps;
+      }
+    } else {
+      (void)claim;
+      c += n_warps;
+    }
+  }
+  if (kClaims && dyn && lane == 0) {
+    // every claim of this warp is made before it counts itself done; the last warp to finish
+    // leaves both counters at zero for the next launch
+    __threadfence();
+    if (atomicAdd(a.chunk_ctr + 1, 1) == (int32_t)n_warps - 1) {
+      atomicExch(a.chunk_ctr, 0);
+      atomicExch(a.chunk_ctr + 1, 0);
+    }
   }
   a.gap_part[warp_id * a.S + 2 * lane] = gap.x;
   a.gap_part[warp_id * a.S + 2 * lane + 1] = gap.y;
+}
+
+// The product with a fixed stride (the 8- and 16-byte sums take the registers they need).
+template <typename V, typename Epi>
+__global__ void __launch_bounds__(256) k_spmm(SpmmArgs a, const V* __restrict__ u, Epi epi) {
+  spmm_run<V, Epi>(a, u, epi);
+}
+
+// The FP32 product with chunk claims, held to 64 registers (four blocks per SM).
+template <typename Epi>
+__global__ void __launch_bounds__(256, 4) k_spmm_claims(SpmmArgs a, const float2* __restrict__ u, Epi epi) {
+  spmm_run<float2, Epi>(a, u, epi);
 }
 
 // Rows that began in an earlier chunk: y = carries of the chunks in order + head partial.
@@ -257,6 +309,14 @@ __global__ void __launch_bounds__(256) k_spmm_fixup(SpmmArgs a, const int32_t* _
     for (int32_t k = cs; k < c; ++k) acc = add2(acc, ct[(int64_t)k * 32 + lane]);
     acc = add2(acc, ch[(int64_t)c * 32 + lane]);
     epi.row(r, lane, acc, act, gap, epi.pre(r, lane));
+  }
+  if (a.gap_chunk) {  // this warp's fixed slice of the product's per-chunk gaps, in order
+    const int64_t per = (a.num_chunks + n_warps - 1) / n_warps;
+    const int64_t c1 = min((int64_t)a.num_chunks, warp_id * per + per);
+    for (int64_t c = warp_id * per; c < c1; ++c) {
+      gap.x += a.gap_chunk[c * a.S + 2 * lane];
+      gap.y += a.gap_chunk[c * a.S + 2 * lane + 1];
+    }
   }
   gap_fix[warp_id * a.S + 2 * lane] = gap.x;
   gap_fix[warp_id * a.S + 2 * lane + 1] = gap.y;
