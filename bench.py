@@ -1016,8 +1016,12 @@ def main():
 
         for i in (0, 1):  # warm-up of both lanes
             host_step(i)
+        def device_allocs():
+            return torch.cuda.memory_stats().get("num_device_alloc", 0)
+
         # sequential: the steps one after another on one stream
         barrier()
+        na_seq = device_allocs()
         t0 = time.perf_counter()
         seq_walls, seq_builds = [], []
         for _ in range(args.steps):
@@ -1026,6 +1030,7 @@ def main():
             seq_builds.append(b_)
         barrier()
         seq_s = max_over_ranks((time.perf_counter() - t0) / args.steps)
+        na_seq = device_allocs() - na_seq
         # two in flight
         walls = [[], []]
         builds = [[], []]
@@ -1050,6 +1055,7 @@ def main():
             t_.join()
         torch.cuda.synchronize()
         barrier()
+        na_fl = device_allocs()
         t0 = time.perf_counter()
         threads = [threading.Thread(target=lane, args=(i,)) for i in (0, 1)]
         for t_ in threads:
@@ -1061,11 +1067,14 @@ def main():
             raise errors[0]
         barrier()
         e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps)
+        na_fl = device_allocs() - na_fl
         h2d_gbs = pinned_h2d_gbs(f_h, f_d, stream)
         placement = host_placement(f_h)
         ms_ = torch.cuda.memory_stats()
         alloc_stats = {k: ms_.get(k) for k in ("num_alloc_retries", "num_device_alloc", "num_device_free")}
         alloc_stats["reserved_gib"] = round(torch.cuda.memory_reserved() / 2**30, 1)
+        # new device segments taken while the timed steps ran (a cudaMalloc there is timed)
+        alloc_stats["device_allocs_in_timed_steps"] = {"sequential": na_seq, "in_flight": na_fl}
         e2e = {"value": ws * m0 / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(2 * 4 * m0 + 2 * 8 * n),
                "d2h_bytes_per_step": int(100 * (4 + 8)), "s_per_step": e2e_s, "in_flight": 2,
                "h2d_gbs": h2d_gbs, "host_buffers": placement,
