@@ -315,7 +315,9 @@ psi_status power_nf(Graph& g, double eps, int32_t max_iter, int32_t origins_per_
     const int64_t fit = budget / (int64_t)(sizeof(double) * (2 * std::max<int64_t>(nG, 1) + nb + nseg));
     C = std::min<int64_t>(C, std::max<int64_t>(kNfThreads, fit / kNfThreads * kNfThreads));
   }
-  C = std::max<int64_t>(C, 1);
+  // the step and product grids take a pass's origins in their y dimension (at most 65535
+  // blocks of kNfThreads)
+  C = std::max<int64_t>(std::min<int64_t>(C, int64_t(65535) * kNfThreads), 1);
 
   const size_t state = (size_t)(std::max<int64_t>(nG, 1) * C);
   const size_t hn = (size_t)std::max<int64_t>(nr, 1);
