@@ -1,5 +1,6 @@
 """The C ABI library builds, loads and exports every symbol include/psi.h declares; the
-ctypes structs match the C layout; host-side argument checks need no GPU."""
+binding's argument lists and the ctypes structs match the header; host-side argument
+checks need no GPU."""
 import ctypes
 import os
 import re
@@ -35,6 +36,44 @@ def test_every_declared_symbol_is_exported(lib):
     for n in names:
         assert n in exported, n
         assert hasattr(lib, n)
+
+
+def _declarations():
+    """(name, [parameter text]) of every function include/psi.h declares."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    out = []
+    for name, params in re.findall(r"\b(psi_[a-z_]+)\s*\(([^;{}]*?)\)\s*;", text, flags=re.S):
+        p = params.strip()
+        out.append((name, [] if p in ("", "void") else [x.strip() for x in p.split(",")]))
+    return out
+
+
+def _kind_of_c(param):
+    if "*" in param:
+        return "ptr"
+    base = param.split()[-2] if len(param.split()) > 1 else param
+    return {"int64_t": "i64", "uint64_t": "u64", "int32_t": "i32", "psi_status": "i32", "int": "i32",
+            "double": "f64", "float": "f32"}[base]
+
+
+def _kind_of_ctypes(t):
+    if t in (ctypes.c_void_p, ctypes.c_char_p) or (isinstance(t, type) and issubclass(t, ctypes._Pointer)):
+        return "ptr"
+    return {ctypes.c_int64: "i64", ctypes.c_uint64: "u64", ctypes.c_int32: "i32", ctypes.c_double: "f64",
+            ctypes.c_float: "f32"}[t]
+
+
+def test_binding_signatures_match_header(lib):
+    """Every declared function has the binding's argument list: the same number of
+    parameters, each of the same kind (64- or 32-bit integer, double, float, pointer)."""
+    decls = _declarations()
+    assert sorted(n for n, _ in decls) == _declared_functions()
+    for name, params in decls:
+        at = getattr(lib, name).argtypes
+        assert at is not None, name
+        assert [_kind_of_c(p) for p in params] == [_kind_of_ctypes(t) for t in at], name
 
 
 def test_struct_layout_matches_header(tmp_path):
