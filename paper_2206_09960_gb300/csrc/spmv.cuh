@@ -349,12 +349,12 @@ constexpr int spmv_min_blocks() {
 // (one block per SM: the copy takes most of the SM's shared memory).
 constexpr int kSpmvHotWarps = 32;
 
-// One warp per tile.  With a.tile_ctr (FP32 sums), each warp takes its first two tiles by a grid-wide
-// stride and claims every later one from a counter (the claim for the tile after next is
-// issued when a tile starts and read when it ends, so its latency hides under the tile);
-// SMs that run faster take more tiles, and the tile's gap is written per tile (a.gap_tile,
-// a fixed lane tree) so that its sum keeps an order fixed by the graph.  Without it the
-// warps walk the tiles with a grid-wide stride and leave a per-block gap.  A
+// One warp per tile.  With a.tile_ctr (FP32 sums), each warp takes its first two tiles by a
+// grid-wide stride and claims every later one from a counter (the claim for the tile after
+// next is issued when a tile starts and read when it ends, so its latency hides under the
+// tile); SMs that run faster take more tiles, and the tile's gap is written per tile
+// (a.gap_tile, a fixed lane tree) so that its sum keeps an order fixed by the graph.
+// Without it the warps walk the tiles with a grid-wide stride and leave a per-block gap.  A
 // tile's row ends are first marked in a bitmap in shared memory (bit q: nonzero nnz0 + q is
 // the last one of its row) from the tile's slice of row_ptr.  Every row has at least one
 // nonzero, so the k-th row end of the tile belongs to row tile_row[tile] + k.  Each step
